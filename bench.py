@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 H(curl) AMG: time to a 1e-8 relative residual (setup + PCG solve) on a
+synthetic coefficient-jump workload, the achieved HBM bandwidth of the dominant V-cycle kernel,
+and the CPU oracle beside it.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--precision f64|f32|bf16]
+
+A step is one pass of the whole path on one system: amgh_setup (graph steps, local harmonic-
+extension solves, Galerkin products, smoother blocks) and amgh_pcg_solve to ||r|| <= 1e-8 ||r0||,
+with A, G and f already in device memory.  Under torchrun every rank solves its own copy
+(replicas: the path has no data exchange between independent systems).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 rel residual; V-cycle HBM GB/s vs 8 TB/s; FP64 vs mixed/learned"
+WORKLOAD = "hex64_checker"
+WORKLOAD_DESC = ("unit-cube 64^3 hex mesh, lowest-order Nedelec (762,048 edge DoFs), alpha on an 8^3 "
+                 "checkerboard of blocks {1, 1e4}, beta = 1e-2, f ~ U(-1,1) seed 1, x0 = 0, tol 1e-8")
+SAMPLE = "hex16_checker"   # bounded CPU sample of the same workload family (10,800 DoFs)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def traffic_for(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "solve_kernels.cu"), "rb").read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("sha") == sha:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(gpu_iters=None):
+    """Oracle setup + PCG on the 16^3 member of the workload family, scaled to the 64^3 workload
+    by the DoF ratio (both are O(n) per iteration) and by the iteration ratio."""
+    import workloads as W
+    from oracle import amg as O
+    s = W.make_config(SAMPLE)
+    full_n = 3 * 64 * 63 * 63
+    t0 = time.perf_counter()
+    H = O.setup(s["A"], s["G"], coarse_size=100)
+    _, it, _ = O.pcg(H, s["f"], tol=1e-8, maxit=1000)
+    t = time.perf_counter() - t0
+    scale = full_n / s["ndof"]
+    if gpu_iters:
+        scale *= gpu_iters / max(it, 1)
+    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": "%s (%d DoFs): oracle setup + PCG to 1e-8 took %.2f s in %d iterations; scaled by "
+                      "DoFs %d/%d%s" % (SAMPLE, s["ndof"], t, it, full_n, s["ndof"],
+                                        " and iterations %d/%d" % (gpu_iters, it) if gpu_iters else ""),
+            "sample_seconds": t, "sample_iters": it}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample()
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample())
+    wall = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "sample": SAMPLE},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2602_23613_gb300 import build, amgh
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    amgh.load()
+    prec = {"f64": amgh.AMGH_F64, "f32": amgh.AMGH_F32, "bf16": amgh.AMGH_BF16}[args.precision]
+    prob = W.make_config(args.workload)
+    A, G, f = prob["A"], prob["G"], prob["f"]
+    n = prob["ndof"]
+    dev = torch.device("cuda", local_rank)
+
+    def dcsr(M):
+        return (torch.tensor(M.indptr.astype(np.int32), device=dev), torch.tensor(M.indices.astype(np.int32), device=dev),
+                torch.tensor(M.data.astype(np.float64), device=dev), M.shape)
+
+    Ad, Gd = dcsr(A), dcsr(G)
+    fd = torch.tensor(f, device=dev)
+    xd = torch.zeros(n, dtype=torch.float64, device=dev)
+    stats = {}
+
+    def step(profile):
+        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        if profile:
+            amgh.amgh_profile(h, 1, "schwarz", 0)
+        xd.zero_()
+        t0 = time.perf_counter()
+        it, rel, ok = amgh.amgh_pcg_solve(h, fd, xd, 1e-8, 2000)
+        solve_s = time.perf_counter() - t0
+        info = amgh.amgh_info(h)
+        ks = amgh.amgh_kernel_stats(h) if profile else None
+        amgh.amgh_destroy(h)
+        return dict(iters=it, relres=rel, ok=ok, solve_s=solve_s, info=info, ks=ks)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    lib = amgh.load()
+    l0 = lib.amgh_launch_count(None)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    t0 = time.perf_counter()
+    res = [step(True) for _ in range(args.steps)]
+    ev1.record()
+    barrier()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    gpu_launches = lib.amgh_launch_count(None) - l0
+    dev_ms = ev0.elapsed_time(ev1)
+    t_step = max(dev_ms / 1000.0, wall) / args.steps
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    ks_launch = sum(r["ks"]["launches"] for r in res)
+    ks_ms = sum(r["ks"]["total_ms"] for r in res)
+    ks_bytes = sum(r["ks"]["algorithmic_bytes"] for r in res)
+    achieved = ks_bytes / (ks_ms / 1000.0) / 1e9 if ks_ms > 0 else None
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    traffic = traffic_for("schwarz", args.workload)
+    last = res[-1]
+
+    # end to end through the same API with host buffers (copies inside the timed region)
+    fh = np.ascontiguousarray(f)
+    xh = np.zeros(n)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h = amgh.amgh_setup(A, G, precision=prec)
+        xh[:] = 0.0
+        amgh.amgh_pcg_solve(h, fh, xh, 1e-8, 2000)
+        amgh.amgh_destroy(h)
+    barrier()
+    e2e = (time.perf_counter() - t0) / e2e_steps
+    csr_bytes = lambda M: 4 * (M.shape[0] + 1) + 12 * M.nnz
+    h2d = csr_bytes(A) + csr_bytes(G) + 8 * n + 8 * n
+    d2h = 8 * n
+
+    if rank != 0:
+        return 0
+    cpu = oracle_sample(gpu_iters=last["iters"])
+    info = last["info"]
+    line = {
+        "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "n_dofs": n, "nnz": int(A.nnz),
+                   "precision": args.precision, "tol": 1e-8,
+                   "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
+                   "levels": info["n"], "op_complexity": round(info["op_complexity"], 4)},
+        "pcg_iters": last["iters"], "relres": last["relres"], "converged": last["ok"],
+        "solve_ms": 1000 * statistics.mean(r["solve_s"] for r in res),
+        "setup_host_ms": info["setup_host_ms"], "setup_device_ms": info["setup_device_ms"],
+        "vcycles_per_s": last["iters"] / statistics.mean(r["solve_s"] for r in res),
+        "roofline": {"bound": "hbm", "kernel": "schwarz colour sweep, finest level", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                     "peak_source": "measured" if pk else "fallback",
+                     "traffic": traffic, "launches": ks_launch,
+                     "algorithmic_bytes_per_launch": ks_bytes / ks_launch if ks_launch else None,
+                     "ms_per_launch": ks_ms / ks_launch if ks_launch else None},
+        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(gpu_launches), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            dist.init_process_group("gloo")
+        else:
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,198 @@
+/*
+ * amgh: GB300 (sm_103a) library for the fully algebraic H(curl) algebraic multigrid of
+ * Shen, Brannick, Falgout, Kahl, Schroder, "Nodal Coarsening and Sparse Ideal Interpolation for
+ * H(curl) Problems in Algebraic Multigrid".
+ *
+ * Problem (Section 2, Eq. curl): the SPD edge-element system A u = f with A = A^s(mu) + beta A^m,
+ * and the discrete gradient G (signed node incidence, de Rham: ker A^s = range G, Eq. deRham).
+ * The setup needs only A and G (Section 4): augmentG (Alg. 1), nodal coarsening of the dual
+ * operator G~^T A G~ (Alg. 2), matching of fine edges into coarse edges along distance-two
+ * nodal paths (Alg. 3), sparse ideal interpolation P_app by interior harmonic extension
+ * (Eq. sparseP), G_c = R G I_C (Eq. Gc) and the Galerkin operator A_c = P^T A P (Eq. tl),
+ * recursively.  The solve (Section 5) is a V-cycle with one pre- and one post-step of the OSS-l1
+ * smoother (symmetrised multiplicative Schwarz on node-star blocks, then l1-Jacobi), used alone or
+ * as the preconditioner of conjugate gradients to a relative residual tolerance.
+ *
+ * Conventions for every entry point:
+ *  - Indices are 0-based int32; matrices are CSR with strictly ascending columns in each row.
+ *  - "device pointer" means memory of the GPU the handle was created on; "host pointer" means
+ *    ordinary or pinned host memory.  Where an argument may be either, the library detects the
+ *    kind with cudaPointerGetAttributes and copies host data through its own device buffers.
+ *  - All work is enqueued on the handle's stream: amgh_params.stream, or when that is NULL a
+ *    blocking stream the handle creates (ordered with the legacy default stream); an entry point
+ *    returns after the work it enqueued has completed.
+ *  - Every entry point returns an amgh_status and never aborts the process; amgh_last_error()
+ *    gives a one-line message for the last failure of the handle (or of a failed setup when the
+ *    handle argument is NULL).  After AMGH_ERR_CUDA the handle should be destroyed.
+ *  - The handle owns all device memory it allocates (cudaMalloc at setup); the caller owns every
+ *    buffer it passes in.  Handles are not thread-safe: use one handle per host thread.
+ */
+#ifndef AMGH_H
+#define AMGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMGH_OK = 0,
+    AMGH_ERR_INVALID_ARG = 1,   /* malformed input or argument out of range                    */
+    AMGH_ERR_NOT_SPD = 2,       /* a Cholesky factorisation met a non-positive pivot            */
+    AMGH_ERR_NOT_CONVERGED = 3, /* the solver reached maxit before the tolerance                */
+    AMGH_ERR_CUDA = 4,          /* a CUDA runtime call failed                                   */
+    AMGH_ERR_OOM = 5,           /* device or host allocation failed                             */
+    AMGH_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                           */
+    AMGH_ERR_SETUP_STALL = 7,   /* the finest level produced no coarse edge                     */
+    AMGH_ERR_UNSUPPORTED = 8    /* valid input outside the limits of this build (e.g. block size) */
+} amgh_status;
+
+typedef struct amgh_ctx* amgh_handle;
+
+/* A CSR matrix: nrows x ncols, nnz stored entries.  row_ptr has nrows+1 entries with
+ * row_ptr[0] = 0 and row_ptr[nrows] = nnz; col and val have nnz entries.  on_device = 1 when the
+ * three arrays are device pointers, 0 when they are host pointers. */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double* val;
+    int on_device;
+} amgh_csr;
+
+/* storage precision of the V-cycle (hierarchy matrices, interpolation, block inverses, l1
+ * diagonal and V-cycle vectors); FP64 keeps everything in double, F32 stores float and
+ * accumulates in float, BF16 stores bfloat16 values and accumulates in float. */
+enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
+
+/* interior extension of the coarse variables (Eq. sparseP): exact local solves on each coarse
+ * edge's patch, or the weights predicted by a trained network (amgh_mlp_*) on the same pattern */
+enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1 };
+
+typedef struct {
+    int max_levels;       /* at most this many levels, finest included (Section 5: 20)          */
+    int coarse_size;      /* stop coarsening once a level has <= coarse_size DoFs (Sec. 5: 32)  */
+    int precision;        /* AMGH_F64 | AMGH_F32 | AMGH_BF16                                    */
+    int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED                            */
+    int ring;             /* rings of interior A-neighbours in a truncated patch (>= 1)        */
+    int p_max;            /* largest patch of one local harmonic extension (<= 256)            */
+    double theta;         /* strength-of-connection threshold of the nodal C/F split (0.25)    */
+    double stall_ratio;   /* stop when n_coarse > stall_ratio * n (0.9)                         */
+    void* stream;         /* cudaStream_t for all work of the handle; NULL = a private stream   */
+} amgh_params;
+
+/* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
+ * theta 0.25, stall_ratio 0.9, stream NULL. */
+void amgh_default_params(amgh_params* p);
+
+/* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,
+ * every row holds at most two entries equal to +-1, two entries of opposite sign; a row with one
+ * entry is an edge touching the eliminated boundary, a row with none an interior edge joining two
+ * boundary nodes).  Section 4
+ * (Alg. 1-3, Eq. sparseP, Eq. Gc) recursed per Section 5's limits.  A and G are deep-copied; the
+ * caller may free them on return.  Errors: INVALID_ARG for malformed CSR, non-square A, a G row
+ * with more than 2 entries, an entry other than +-1, or a two-entry row whose entries share a sign;
+ * NOT_SPD when a local or coarsest factorisation fails; SETUP_STALL when level 0 has no coarse
+ * edge; UNSUPPORTED for a smoother block larger than 32 DoFs or a coarsest level larger than
+ * 2048 DoFs. On failure *out is NULL. */
+amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
+                       amgh_handle* out);
+
+/* Host-only variant of amgh_setup for inspecting the graph steps of the finest level without a
+ * GPU: runs Alg. 1-3, the patch construction of Eq. sparseP, the symbolic Galerkin pattern and
+ * the smoother stars and colouring of level 0 on the host and makes no CUDA call (A and G must be
+ * host CSR).  On the returned handle only amgh_level_structure(h, 0, ...), amgh_level_matrix(h,
+ * 0, which) (which = 1 returns P's pattern with the exterior +-1 and zeros elsewhere; which = 3
+ * returns the symbolic pattern of P^T A P with zero values), amgh_last_error and amgh_destroy are
+ * valid; every other call returns INVALID_ARG.  Errors as amgh_setup. */
+amgh_status amgh_setup_host_structure(const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
+                                      amgh_handle* out);
+
+/* z = B r, one V-cycle (Eq. tl applied recursively: zero initial guess, OSS-l1 pre-step,
+ * residual restriction P^T, coarse correction, prolongation P, OSS-l1 post-step; dense Cholesky
+ * on the coarsest level).  r and z: n doubles, host or device pointers (both of the same kind),
+ * may not alias. */
+amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z);
+
+/* Preconditioned conjugate gradients (Section 5) on the finest A with the V-cycle as the
+ * preconditioner: stops when ||f - A x_k||_2 (as updated by the recurrence) <= tol ||f - A x_0||_2
+ * or after maxit iterations.  x holds x_0 on entry and the solution on return; f and x are n
+ * doubles, host or device (same kind).  With an FP32/BF16 hierarchy the outer loop is flexible
+ * CG (beta = <z_k+1, r_k+1 - r_k> / <z_k, r_k>) with FP64 vectors, SpMV and dots.  iters and
+ * relres (may be NULL) receive the iteration count and the final relative residual.
+ * Returns NOT_CONVERGED (with x, iters, relres filled) when maxit is reached. */
+amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit,
+                           int* iters, double* relres);
+
+/* Stand-alone V-cycle iteration x <- x + B (f - A x) (Section 5, "AMG" counts), same stopping
+ * rule and argument conventions as amgh_pcg_solve, on the true residual. */
+amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit,
+                           int* iters, double* relres);
+
+typedef struct {
+    int levels;
+    int64_t n[32];        /* DoFs per level                                                    */
+    int64_t nnz[32];      /* stored entries of A_l                                             */
+    int64_t nnz_p[32];    /* stored entries of P_l (0 on the coarsest level)                   */
+    int ncolours[32];     /* smoother colours per level (0 on the coarsest level)             */
+    int max_block[32];    /* largest smoother block per level                                  */
+    int max_patch[32];    /* largest interpolation patch per level                             */
+    double op_complexity; /* sum nnz(A_l) / nnz(A_0)                                           */
+    double grid_complexity; /* sum n_l / n_0                                                    */
+    double setup_host_ms; /* host graph steps (Alg. 1-3, patterns, colouring)                 */
+    double setup_device_ms; /* device numerics (patch solves, Galerkin product, inverses)       */
+} amgh_hier_info;
+
+/* Hierarchy statistics (levels, sizes, complexities as defined in Section 5, setup time split). */
+amgh_status amgh_info(amgh_handle h, amgh_hier_info* info);
+
+/* Structural outputs of the setup on level l (0 <= l < levels-1), into host arrays.  Any pointer
+ * may be NULL to skip it; sizes are those reported by the query form: call first with all
+ * pointers NULL to obtain the counts.
+ *   ncoarse_nodes / cf_state: length n_nodes_aug = columns of G~ (Alg. 1): state 1 = C, 2 = F
+ *   coarse_edges: 7 ints per coarse edge in creation order: DoF1, s1, DoF2, s2, i, k, j (Alg. 3)
+ *   coarse_nodes: the kept columns of R G (Eq. Gc), ascending
+ *   patch_ptr / patch_idx: CSR of the sorted patch of every coarse edge (Eq. sparseP)
+ *   colour: smoother colour of every star (one star per column of G_l) */
+amgh_status amgh_level_structure(amgh_handle h, int l, int64_t* n_nodes_aug, int64_t* n_edges,
+                                 int64_t* n_coarse_nodes, int64_t* patch_nnz, int64_t* n_stars,
+                                 int8_t* cf_state, int32_t* coarse_edges, int32_t* coarse_nodes,
+                                 int32_t* patch_ptr, int32_t* patch_idx, int32_t* colour);
+
+/* Copy a level matrix to host CSR arrays (FP64 values as computed on the device).
+ * which = 0: A_l (n_l x n_l); 1: P_l (n_l x n_{l+1}); 2: G_l (n_l x m_l); 3: the symbolic pattern
+ * of P_l^T A_l P_l with the device values of A_{l+1} (zeros on a structure-only handle).
+ * Query form: pass row_ptr = col = val = NULL to receive nrows, ncols, nnz only. */
+amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, int64_t* ncols,
+                              int64_t* nnz, int32_t* row_ptr, int32_t* col, double* val);
+
+/* Single steps of the V-cycle on level l, for testing the kernels one by one.  Device pointers
+ * of n_l (or n_{l+1}) doubles.  op = 0: y = A_l x;  1: y = f - A_l x;  2: x <- OSS-l1 pre-step
+ * (x in/out, f the right-hand side);  3: x <- OSS-l1 post-step;  4: y = P_l^T x (restriction);
+ * 5: y <- y + P_l x (prolongation);  6: y = A_L^{-1} x on the coarsest level L (l ignored). */
+amgh_status amgh_level_apply(amgh_handle h, int l, int op, const double* f, const double* x,
+                             double* y);
+
+/* Kernel timing, for the roofline: when enabled the library brackets every launch of the
+ * kernels of class `kind` on level `level` with CUDA events on its stream.  kind: 0 Schwarz
+ * colour sweep, 1 l1-Jacobi, 2 residual, 3 restriction, 4 prolongation, 5 coarsest solve,
+ * 6 outer SpMV.  amgh_kernel_stats returns the number of bracketed launches, their summed
+ * duration (ms) and the algorithmic bytes they moved (sum over launches of the bytes each launch
+ * must read and write once: matrix values and indices, block inverses, vectors). */
+amgh_status amgh_profile(amgh_handle h, int enable, int kind, int level);
+amgh_status amgh_kernel_stats(amgh_handle h, int64_t* launches, double* total_ms,
+                              double* algorithmic_bytes);
+
+/* Number of kernels the library has launched in this process, over all handles (a CUDA-graph
+ * replay counts every kernel it runs); the handle argument may be NULL. */
+int64_t amgh_launch_count(amgh_handle h);
+
+const char* amgh_last_error(amgh_handle h);
+void amgh_destroy(amgh_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMGH_H */

@@ -1,0 +1,288 @@
+"""Python binding of libamgh (argument marshalling only; every step runs in the library).
+
+Functions carry the names of the C entry points declared in include/amgh.h.  Matrices are passed
+as scipy CSR matrices (host) or as (row_ptr, col, val, shape) tuples of CUDA torch tensors
+(device); vectors as numpy arrays (host) or torch tensors (host or CUDA).  The library must have
+been built (``paper_2602_23613_gb300.build.build()``); there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+AMGH_OK, AMGH_ERR_INVALID_ARG, AMGH_ERR_NOT_SPD, AMGH_ERR_NOT_CONVERGED = 0, 1, 2, 3
+AMGH_ERR_CUDA, AMGH_ERR_OOM, AMGH_ERR_TIMEOUT, AMGH_ERR_SETUP_STALL, AMGH_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
+AMGH_F64, AMGH_F32, AMGH_BF16 = 0, 1, 2
+AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED = 0, 1
+KIND = {"schwarz": 0, "l1": 1, "residual": 2, "restrict": 3, "prolong": 4, "coarse": 5, "spmv": 6}
+
+
+class amgh_csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("on_device", ctypes.c_int)]
+
+
+class amgh_params(ctypes.Structure):
+    _fields_ = [("max_levels", ctypes.c_int), ("coarse_size", ctypes.c_int), ("precision", ctypes.c_int),
+                ("interp", ctypes.c_int), ("ring", ctypes.c_int), ("p_max", ctypes.c_int),
+                ("theta", ctypes.c_double), ("stall_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+
+
+class amgh_hier_info(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("n", ctypes.c_int64 * 32), ("nnz", ctypes.c_int64 * 32),
+                ("nnz_p", ctypes.c_int64 * 32), ("ncolours", ctypes.c_int * 32), ("max_block", ctypes.c_int * 32),
+                ("max_patch", ctypes.c_int * 32), ("op_complexity", ctypes.c_double),
+                ("grid_complexity", ctypes.c_double), ("setup_host_ms", ctypes.c_double),
+                ("setup_device_ms", ctypes.c_double)]
+
+
+_LIB = None
+EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve", "amgh_amg_solve", "amgh_info",
+           "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
+           "amgh_launch_count", "amgh_last_error", "amgh_destroy"]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load():
+    """Load libamgh.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libamgh.so is not built (%s); run paper_2602_23613_gb300.build.build()" % path)
+    L = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    L.amgh_default_params.argtypes = [ctypes.POINTER(amgh_params)]
+    L.amgh_default_params.restype = None
+    L.amgh_setup.argtypes = [ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_params), ctypes.POINTER(P)]
+    L.amgh_setup_host_structure.argtypes = L.amgh_setup.argtypes
+    L.amgh_vcycle.argtypes = [P, P, P]
+    L.amgh_pcg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_amg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_info.argtypes = [P, ctypes.POINTER(amgh_hier_info)]
+    L.amgh_level_structure.argtypes = [P, I] + [ctypes.POINTER(I64)] * 5 + [P] * 6
+    L.amgh_level_matrix.argtypes = [P, I, I] + [ctypes.POINTER(I64)] * 3 + [P, P, P]
+    L.amgh_level_apply.argtypes = [P, I, I, P, P, P]
+    L.amgh_profile.argtypes = [P, I, I, I]
+    L.amgh_kernel_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]
+    L.amgh_launch_count.argtypes = [P]
+    L.amgh_launch_count.restype = I64
+    L.amgh_last_error.argtypes = [P]
+    L.amgh_last_error.restype = ctypes.c_char_p
+    L.amgh_destroy.argtypes = [P]
+    L.amgh_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("amgh_default_params", "amgh_launch_count", "amgh_last_error", "amgh_destroy"):
+            getattr(L, name).restype = I
+    _LIB = L
+    return L
+
+
+class AmghError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("amgh status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _check(st, h=None):
+    if st != AMGH_OK:
+        msg = load().amgh_last_error(h).decode(errors="replace")
+        raise AmghError(st, msg)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _vec_ptr(x, keep):
+    """Pointer of a float64 vector (numpy, or torch host/CUDA), contiguous, kept alive in keep."""
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("vectors must be contiguous float64")
+        return x.data_ptr()
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _csr(M, keep):
+    c = amgh_csr()
+    if isinstance(M, tuple):           # (row_ptr, col, val, (nrows, ncols)) of CUDA torch tensors
+        rp, ci, va, shape = M
+        c.nrows, c.ncols, c.nnz = shape[0], shape[1], int(ci.numel())
+        c.row_ptr, c.col, c.val, c.on_device = rp.data_ptr(), ci.data_ptr(), va.data_ptr(), 1 if rp.is_cuda else 0
+        keep.extend([rp, ci, va])
+        return c
+    import scipy.sparse as sp
+    M = sp.csr_matrix(M)
+    M.sort_indices()
+    rp = np.ascontiguousarray(M.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(M.indices, dtype=np.int32)
+    va = np.ascontiguousarray(M.data, dtype=np.float64)
+    keep.extend([rp, ci, va])
+    c.nrows, c.ncols, c.nnz = M.shape[0], M.shape[1], M.nnz
+    c.row_ptr, c.col, c.val, c.on_device = rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0
+    return c
+
+
+class Handle:
+    """Owns an amgh_handle; destroyed with amgh_destroy."""
+
+    def __init__(self, ptr, n):
+        self.ptr = ptr
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            load().amgh_destroy(self.ptr)
+            self.ptr = None
+
+
+def amgh_default_params():
+    p = amgh_params()
+    load().amgh_default_params(ctypes.byref(p))
+    return p
+
+
+def amgh_setup(A, G, params=None, **kw):
+    """Build the hierarchy for (A, G); keyword arguments override fields of amgh_params."""
+    L = load()
+    p = params if params is not None else amgh_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    keep = []
+    a, g = _csr(A, keep), _csr(G, keep)
+    out = ctypes.c_void_p()
+    _check(L.amgh_setup(ctypes.byref(a), ctypes.byref(g), ctypes.byref(p), ctypes.byref(out)))
+    return Handle(out.value, a.nrows)
+
+
+def amgh_setup_host_structure(A, G, params=None, **kw):
+    """Level-0 graph steps on the host only (no GPU needed); see include/amgh.h."""
+    L = load()
+    p = params if params is not None else amgh_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    keep = []
+    a, g = _csr(A, keep), _csr(G, keep)
+    out = ctypes.c_void_p()
+    _check(L.amgh_setup_host_structure(ctypes.byref(a), ctypes.byref(g), ctypes.byref(p), ctypes.byref(out)))
+    return Handle(out.value, a.nrows)
+
+
+def amgh_vcycle(h, r, z):
+    keep = []
+    _check(load().amgh_vcycle(h.ptr, _vec_ptr(r, keep), _z_ptr(z)), h.ptr)
+
+
+def _z_ptr(z):
+    if _is_torch(z):
+        import torch
+        if z.dtype != torch.float64 or not z.is_contiguous():
+            raise TypeError("output vectors must be contiguous float64")
+        return z.data_ptr()
+    if not (isinstance(z, np.ndarray) and z.dtype == np.float64 and z.flags.c_contiguous and z.flags.writeable):
+        raise TypeError("output vectors must be writeable contiguous float64 arrays")
+    return z.ctypes.data
+
+
+def _solve(fn, h, f, x, tol, maxit):
+    keep = []
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = fn(h.ptr, _vec_ptr(f, keep), _z_ptr(x), tol, maxit, ctypes.byref(it), ctypes.byref(rel))
+    if st not in (AMGH_OK, AMGH_ERR_NOT_CONVERGED):
+        _check(st, h.ptr)
+    return it.value, rel.value, st == AMGH_OK
+
+
+def amgh_pcg_solve(h, f, x, tol=1e-8, maxit=500):
+    """PCG with the V-cycle; x holds x0 on entry.  Returns (iterations, relres, converged)."""
+    return _solve(load().amgh_pcg_solve, h, f, x, tol, maxit)
+
+
+def amgh_amg_solve(h, f, x, tol=1e-8, maxit=500):
+    """Stand-alone V-cycle iteration.  Returns (iterations, relres, converged)."""
+    return _solve(load().amgh_amg_solve, h, f, x, tol, maxit)
+
+
+def amgh_info(h):
+    info = amgh_hier_info()
+    _check(load().amgh_info(h.ptr, ctypes.byref(info)), h.ptr)
+    L = info.levels
+    return dict(levels=L, n=list(info.n[:L]), nnz=list(info.nnz[:L]), nnz_p=list(info.nnz_p[:L]),
+                ncolours=list(info.ncolours[:L]), max_block=list(info.max_block[:L]),
+                max_patch=list(info.max_patch[:L]), op_complexity=info.op_complexity,
+                grid_complexity=info.grid_complexity, setup_host_ms=info.setup_host_ms,
+                setup_device_ms=info.setup_device_ms)
+
+
+def amgh_level_structure(h, l):
+    """Structural outputs of level l as numpy arrays (see include/amgh.h)."""
+    Lb = load()
+    cnt = [ctypes.c_int64(0) for _ in range(5)]
+    nul = [None] * 6
+    _check(Lb.amgh_level_structure(h.ptr, l, *[ctypes.byref(c) for c in cnt], *nul), h.ptr)
+    nna, ne, ncn, pnz, ns = [c.value for c in cnt]
+    cf = np.zeros(nna, np.int8)
+    edges = np.zeros((ne, 7), np.int32)
+    cnodes = np.zeros(ncn, np.int32)
+    pptr = np.zeros(ne + 1, np.int32)
+    pidx = np.zeros(pnz, np.int32)
+    col = np.zeros(ns, np.int32)
+    _check(Lb.amgh_level_structure(h.ptr, l, *[ctypes.byref(c) for c in cnt], cf.ctypes.data, edges.ctypes.data,
+                                   cnodes.ctypes.data, pptr.ctypes.data, pidx.ctypes.data, col.ctypes.data), h.ptr)
+    return dict(cf_state=cf, edges=edges, coarse_nodes=cnodes, patch_ptr=pptr, patch_idx=pidx, colour=col)
+
+
+def amgh_level_matrix(h, l, which):
+    """Level matrix as scipy CSR: which = 0 A_l, 1 P_l, 2 G_l, 3 P_l^T A_l P_l (symbolic pattern)."""
+    import scipy.sparse as sp
+    Lb = load()
+    nr, nc, nz = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(Lb.amgh_level_matrix(h.ptr, l, which, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nz),
+                                None, None, None), h.ptr)
+    rp = np.zeros(nr.value + 1, np.int32)
+    ci = np.zeros(nz.value, np.int32)
+    va = np.zeros(nz.value, np.float64)
+    _check(Lb.amgh_level_matrix(h.ptr, l, which, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nz),
+                                rp.ctypes.data, ci.ctypes.data, va.ctypes.data), h.ptr)
+    return sp.csr_matrix((va, ci, rp), shape=(nr.value, nc.value))
+
+
+def amgh_level_apply(h, l, op, f, x, y):
+    """One V-cycle step on level l with CUDA float64 tensors (see include/amgh.h for op)."""
+    _check(load().amgh_level_apply(h.ptr, l, op, f.data_ptr() if f is not None else None, x.data_ptr(),
+                                   y.data_ptr()), h.ptr)
+
+
+def amgh_profile(h, enable, kind="schwarz", level=0):
+    _check(load().amgh_profile(h.ptr, int(enable), KIND.get(kind, kind), level), h.ptr)
+
+
+def amgh_kernel_stats(h):
+    n, ms, by = ctypes.c_int64(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().amgh_kernel_stats(h.ptr, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)), h.ptr)
+    return dict(launches=n.value, total_ms=ms.value, algorithmic_bytes=by.value)
+
+
+def amgh_launch_count(h):
+    return int(load().amgh_launch_count(h.ptr))
+
+
+def amgh_last_error(h=None):
+    return load().amgh_last_error(h.ptr if h is not None else None).decode(errors="replace")
+
+
+def amgh_destroy(h):
+    if h.ptr:
+        load().amgh_destroy(h.ptr)
+        h.ptr = None

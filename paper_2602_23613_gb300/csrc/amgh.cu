@@ -1,0 +1,1057 @@
+// libamgh: setup driver, V-cycle engine, Krylov solvers and the C-ABI entry points.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <type_traits>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "engine.cuh"
+
+namespace amgh {
+
+std::atomic<int64_t>& launch_counter() {
+    static std::atomic<int64_t> c{0};
+    return c;
+}
+
+struct StatusError {
+    amgh_status st;
+    std::string msg;
+};
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static void upload_csr(const HostCSR& h, DevCSR& d, cudaStream_t s, bool values) {
+    d.nrows = h.nrows;
+    d.ncols = h.ncols;
+    d.nnz = h.nnz();
+    d.ptr.upload(h.ptr, s);
+    d.idx.upload(h.idx, s);
+    if (values) d.val.upload(h.val, s);
+    else d.val.alloc(d.nnz);
+}
+
+// slice pointers of a 32-row SELL for the rows of a host pattern (or for listed rows)
+static std::vector<int64_t> sell_slices(const HostCSR& M, const std::vector<int32_t>* rows) {
+    const int64_t nrows = rows ? (int64_t)rows->size() : M.nrows;
+    const int64_t ns = (nrows + 31) / 32;
+    std::vector<int64_t> sp(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        int w = 0;
+        for (int64_t q = 32 * s; q < std::min<int64_t>(nrows, 32 * s + 32); ++q) {
+            int r = rows ? (*rows)[q] : (int)q;
+            if (r >= 0) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+        }
+        sp[s + 1] = sp[s] + 32 * (int64_t)w;
+    }
+    return sp;
+}
+
+template <class V>
+static void build_sell(const HostCSR& pat, const DevCSR& dev, Sell<V>& S, cudaStream_t s) {
+    auto sp = sell_slices(pat, nullptr);
+    S.nrows = pat.nrows;
+    S.nslices = (int)(sp.size() - 1);
+    S.stored = sp.back();
+    S.slice_ptr.upload(sp, s);
+    S.col.alloc(S.stored);
+    S.val.alloc(S.stored);
+    launch_sell_fill<V>(dev, S, s);
+}
+
+template <class V, class T>
+struct Engine : EngineBase {
+    std::vector<LevelDev<V, T>> L;
+    std::vector<int> ncol;
+    int nlev = 0, nL = 0;
+    DevArray<T> cinv;
+    DevArray<double> io_in, io_out;   // FP64 staging when T != double
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool prof_in_graph = false;
+    int prof_gen = -1;
+    int64_t launches_vc = 0;
+
+    ~Engine() override { release_graph(); }
+
+    double* in64() override {
+        if constexpr (std::is_same<T, double>::value) return L[0].f.p;
+        else return io_in.p;
+    }
+    double* out64() override {
+        if constexpr (std::is_same<T, double>::value) return L[0].x.p;
+        else return io_out.p;
+    }
+
+    template <class F>
+    void timed(int kind, int level, double bytes, cudaStream_t s, F&& fn) {
+        if (prof && prof->match(kind, level)) {
+            auto ev = prof->next();
+            prof->bytes_used.resize(prof->used);
+            prof->bytes_used[prof->used - 1] = bytes;
+            prof->record(ev.first, s);
+            fn();
+            prof->record(ev.second, s);
+        } else {
+            fn();
+        }
+    }
+
+    static std::vector<int> colour_sequence(int nc) {
+        std::vector<int> seq;
+        for (int c = 0; c < nc; ++c) seq.push_back(c);
+        for (int c = nc - 2; c >= 0; --c) seq.push_back(c);
+        return seq;
+    }
+
+    // bytes one pass over a SELL matrix must move: values + column indices of the stored
+    // (non-padding) entries, plus row pointers (4 B per row), plus the vectors it reads and writes
+    double bytes_sell(const Sell<V>& A, int64_t nnz, int vec_rw) const {
+        return (double)nnz * (sizeof(V) + 4) + 4.0 * A.nrows + (double)vec_rw * sizeof(T) * A.nrows;
+    }
+
+    std::vector<int64_t> nnzA, nnzP, sm_nnz, sm_inv;   // per level: algorithmic counts
+
+    void smooth_pre(int l, cudaStream_t s, int64_t& cnt) {
+        auto& d = L[l];
+        for (int c : colour_sequence(ncol[l])) {
+            const double by = (double)sm_nnz_col[l][c] * (sizeof(V) + 4) + (double)sm_inv_col[l][c] * sizeof(V) +
+                              3.0 * sizeof(T) * sm_rows_col[l][c];
+            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_colour<V, T>(d.sm, c, d.f.p, d.x.p, s); });
+            cnt++;
+        }
+        timed(K_L1, l, bytes_sell(d.A, nnzA[l], 4), s,
+              [&] { launch_sell<V, T>(SELL_L1, d.A, d.x.p, d.f.p, d.l1inv.p, d.y.p, s); });
+        cnt++;
+    }
+    void smooth_post(int l, cudaStream_t s, int64_t& cnt) {
+        auto& d = L[l];
+        timed(K_L1, l, bytes_sell(d.A, nnzA[l], 4), s,
+              [&] { launch_sell<V, T>(SELL_L1, d.A, d.y.p, d.f.p, d.l1inv.p, d.x.p, s); });
+        cnt++;
+        for (int c : colour_sequence(ncol[l])) {
+            const double by = (double)sm_nnz_col[l][c] * (sizeof(V) + 4) + (double)sm_inv_col[l][c] * sizeof(V) +
+                              3.0 * sizeof(T) * sm_rows_col[l][c];
+            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_colour<V, T>(d.sm, c, d.f.p, d.x.p, s); });
+            cnt++;
+        }
+    }
+    std::vector<std::vector<int64_t>> sm_nnz_col, sm_inv_col, sm_rows_col;
+
+    int64_t core(cudaStream_t s) {
+        int64_t cnt = 0;
+        if constexpr (!std::is_same<T, double>::value) {
+            launch_convert<T>(io_in.p, L[0].f.p, L[0].n, s);
+            cnt++;
+        }
+        for (int l = 0; l + 1 < nlev; ++l) {
+            auto& d = L[l];
+            d.x.zero(s);
+            smooth_pre(l, s, cnt);
+            // after the pre-step the iterate lives in y
+            timed(K_RESID, l, bytes_sell(d.A, nnzA[l], 3), s,
+                  [&] { launch_sell<V, T>(SELL_RESID, d.A, d.y.p, d.f.p, nullptr, d.r.p, s); });
+            cnt++;
+            timed(K_RESTRICT, l, bytes_sell(d.PT, nnzP[l], 0) + sizeof(T) * (double)(d.n + L[l + 1].n), s,
+                  [&] { launch_sell<V, T>(SELL_AX, d.PT, d.r.p, nullptr, nullptr, L[l + 1].f.p, s); });
+            cnt++;
+        }
+        timed(K_COARSE, nlev - 1, (double)nL * nL * sizeof(T), s,
+              [&] { launch_coarse_apply<T>(cinv.p, nL, L[nlev - 1].f.p, L[nlev - 1].x.p, s); });
+        cnt++;
+        for (int l = nlev - 2; l >= 0; --l) {
+            auto& d = L[l];
+            timed(K_PROLONG, l, bytes_sell(d.P, nnzP[l], 2) + sizeof(T) * (double)L[l + 1].n, s,
+                  [&] { launch_sell<V, T>(SELL_ADD, d.P, L[l + 1].x.p, nullptr, nullptr, d.y.p, s); });
+            cnt++;
+            smooth_post(l, s, cnt);
+        }
+        if constexpr (!std::is_same<T, double>::value) {
+            launch_to_double<T>(L[0].x.p, io_out.p, L[0].n, s);
+            cnt++;
+        }
+        return cnt;
+    }
+
+    int64_t vcycle(cudaStream_t s) override {
+        const bool want_prof = prof && prof->enabled;
+        if (!gexec || want_prof != prof_in_graph || (want_prof && prof_gen != prof->gen)) capture(s);
+        AMGH_CUDA(cudaGraphLaunch(gexec, s));
+        launch_counter().fetch_add(launches_vc);
+        return launches_vc;
+    }
+
+    void capture(cudaStream_t s) override {
+        release_graph();
+        prof_in_graph = prof && prof->enabled;
+        prof_gen = prof ? prof->gen : -1;
+        if (prof) { prof->used = 0; prof->capturing = true; }
+        const int64_t before = launch_counter().load();   // capturing launches nothing
+        AMGH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int64_t cnt = 0;
+        try {
+            cnt = core(s);
+        } catch (...) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(s, &g);
+            if (g) cudaGraphDestroy(g);
+            if (prof) prof->capturing = false;
+            throw;
+        }
+        AMGH_CUDA(cudaStreamEndCapture(s, &graph));
+        launch_counter().store(before);
+        if (prof) { prof->capturing = false; prof_pairs = prof->used; prof->used = 0; }
+        AMGH_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+        launches_vc = cnt;
+    }
+
+    void release_graph() override {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
+
+    void level_apply(int l, int op, const double* f, const double* x, double* y, cudaStream_t s) override {
+        if (op == 6) l = nlev - 1;
+        if (l < 0 || l >= nlev || (op != 6 && l == nlev - 1))
+            throw StatusError{AMGH_ERR_INVALID_ARG, "level out of range for this operation"};
+        auto& d = L[l];
+        const int n = d.n;
+        auto to_T = [&](const double* src, T* dst, int64_t cnt) { launch_convert<T>(src, dst, cnt, s); };
+        auto from_T = [&](const T* src, double* dst, int64_t cnt) { launch_to_double<T>(src, dst, cnt, s); };
+        switch (op) {
+            case 0:
+            case 1:
+                to_T(x, d.x.p, n);
+                if (op == 1) to_T(f, d.f.p, n);
+                launch_sell<V, T>(op == 0 ? SELL_AX : SELL_RESID, d.A, d.x.p, d.f.p, nullptr, d.r.p, s);
+                from_T(d.r.p, y, n);
+                break;
+            case 2: {   // pre-step from iterate x: result in y
+                int64_t c = 0;
+                to_T(x, d.x.p, n);
+                to_T(f, d.f.p, n);
+                smooth_pre(l, s, c);
+                from_T(d.y.p, y, n);
+                break;
+            }
+            case 3: {   // post-step from iterate x
+                int64_t c = 0;
+                to_T(x, d.y.p, n);
+                to_T(f, d.f.p, n);
+                smooth_post(l, s, c);
+                from_T(d.x.p, y, n);
+                break;
+            }
+            case 4: {
+                auto& c = L[l + 1];
+                to_T(x, d.r.p, n);
+                launch_sell<V, T>(SELL_AX, d.PT, d.r.p, nullptr, nullptr, c.f.p, s);
+                from_T(c.f.p, y, c.n);
+                break;
+            }
+            case 5: {
+                auto& c = L[l + 1];
+                to_T(x, c.x.p, c.n);
+                to_T(y, d.y.p, n);
+                launch_sell<V, T>(SELL_ADD, d.P, c.x.p, nullptr, nullptr, d.y.p, s);
+                from_T(d.y.p, y, n);
+                break;
+            }
+            case 6:
+                to_T(x, d.f.p, n);
+                launch_coarse_apply<T>(cinv.p, nL, d.f.p, d.x.p, s);
+                from_T(d.x.p, y, n);
+                break;
+            default:
+                throw StatusError{AMGH_ERR_INVALID_ARG, "unknown level operation"};
+        }
+    }
+};
+
+std::unique_ptr<EngineBase> new_engine(int precision) {
+    if (precision == AMGH_F64) return std::unique_ptr<EngineBase>(new Engine<double, double>());
+    if (precision == AMGH_F32) return std::unique_ptr<EngineBase>(new Engine<float, float>());
+    return std::unique_ptr<EngineBase>(new Engine<__nv_bfloat16, float>());
+}
+
+}  // namespace amgh
+
+using namespace amgh;
+
+struct amgh_ctx {
+    amgh_params prm{};
+    cudaStream_t s = nullptr;
+    std::string err;
+    std::vector<LevelHost> hl;
+    std::vector<DevCSR> A64, P64, PT64;
+    DevArray<double> cinv64;
+    std::unique_ptr<EngineBase> eng;
+    Sell<double> A0;   // outer FP64 SpMV
+    int64_t nnzA0 = 0;
+    DevArray<double> kp, kq, kro, partial, scal, stage_f, stage_x;
+    double* hscal = nullptr;
+    DevArray<int> errflag;
+    Profiler prof;
+    int64_t launches = 0;
+    double host_ms = 0, dev_ms = 0;
+    bool vc_pending = false;          // a V-cycle ran since the last harvest of its event pairs
+    std::vector<int> max_patch;
+    bool own_stream = false;
+    bool structure_only = false;
+    ~amgh_ctx() {
+        eng.reset();
+        if (hscal) cudaFreeHost(hscal);
+        if (own_stream && s) cudaStreamDestroy(s);
+    }
+};
+
+static thread_local std::string g_setup_error;
+
+namespace amgh {
+
+template <class V, class T>
+static void build_engine(amgh_ctx* h, Engine<V, T>* e) {
+    cudaStream_t s = h->s;
+    const int nlev = (int)h->hl.size();
+    e->nlev = nlev;
+    e->L.resize(nlev);
+    e->ncol.assign(nlev, 0);
+    e->nnzA.assign(nlev, 0);
+    e->nnzP.assign(nlev, 0);
+    e->sm_nnz_col.assign(nlev, {});
+    e->sm_inv_col.assign(nlev, {});
+    e->sm_rows_col.assign(nlev, {});
+    for (int l = 0; l < nlev; ++l) {
+        auto& d = e->L[l];
+        const LevelHost& hl = h->hl[l];
+        d.n = hl.A.nrows;
+        d.f.alloc(d.n);
+        d.x.alloc(d.n);
+        d.y.alloc(d.n);
+        d.r.alloc(d.n);
+        d.f.zero(s);
+        d.x.zero(s);
+        d.y.zero(s);
+        d.r.zero(s);
+        if (l == nlev - 1) break;
+        e->nnzA[l] = hl.A.nnz();
+        e->nnzP[l] = hl.cz.P.nnz();
+        build_sell<V>(hl.A, h->A64[l], d.A, s);
+        d.l1inv.alloc(d.n);
+        launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
+        // smoother
+        const StarLayout& st = hl.stars;
+        auto& sm = d.sm;
+        sm.ncolours = st.ncolours;
+        sm.nwarps = (int)(st.slot_row.size() / 32);
+        sm.bmax = std::max(1, st.max_block);
+        sm.colour_warp_begin = st.colour_warp_begin;
+        e->ncol[l] = st.ncolours;
+        sm.slot_row.upload(st.slot_row, s);
+        sm.slot_base.upload(st.slot_base, s);
+        sm.slot_bsize.upload(st.slot_bsize, s);
+        auto sp = sell_slices(hl.A, &st.slot_row);
+        sm.rows.nrows = (int)st.slot_row.size();
+        sm.rows.nslices = sm.nwarps;
+        sm.rows.stored = sp.back();
+        sm.rows.slice_ptr.upload(sp, s);
+        sm.rows.col.alloc(sm.rows.stored);
+        sm.rows.val.alloc(sm.rows.stored);
+        launch_slot_fill<V>(h->A64[l], sm.slot_row.p, sm.rows, s);
+        sm.inv.alloc((size_t)sm.nwarps * 32 * sm.bmax);
+        sm.inv.zero(s);
+        std::vector<int32_t> star_warp(st.nstars, 0), star_base(st.nstars, 0);
+        for (size_t q = 0; q < st.slot_row.size(); ++q)
+            if (st.slot_star[q] >= 0 && st.slot_pos[q] == 0) {
+                star_warp[st.slot_star[q]] = (int32_t)(q / 32);
+                star_base[st.slot_star[q]] = (int32_t)(q % 32);
+            }
+        DevArray<int32_t> dsp, dsi, dsw, dsb;
+        dsp.upload(st.star_ptr, s);
+        dsi.upload(st.star_idx, s);
+        dsw.upload(star_warp, s);
+        dsb.upload(star_base, s);
+        launch_star_inverse<V>(h->A64[l], st.nstars, dsp.p, dsi.p, dsw.p, dsb.p, sm.bmax, sm.inv.p, h->errflag.p, s);
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        // per-colour algorithmic counts
+        e->sm_nnz_col[l].assign(st.ncolours, 0);
+        e->sm_inv_col[l].assign(st.ncolours, 0);
+        e->sm_rows_col[l].assign(st.ncolours, 0);
+        for (int c = 0; c < st.ncolours; ++c)
+            for (int w = st.colour_warp_begin[c]; w < st.colour_warp_begin[c + 1]; ++w)
+                for (int q = 0; q < 32; ++q) {
+                    int r = st.slot_row[(size_t)w * 32 + q];
+                    if (r < 0) continue;
+                    e->sm_nnz_col[l][c] += hl.A.ptr[r + 1] - hl.A.ptr[r];
+                    e->sm_inv_col[l][c] += st.slot_bsize[(size_t)w * 32 + q];
+                    e->sm_rows_col[l][c] += 1;
+                }
+        // transfers
+        build_sell<V>(hl.cz.P, h->P64[l], d.P, s);
+        build_sell<V>(hl.cz.PT, h->PT64[l], d.PT, s);
+    }
+    e->nL = h->hl.back().A.nrows;
+    e->cinv.alloc((size_t)e->nL * e->nL);
+    launch_convert<T>(h->cinv64.p, e->cinv.p, (int64_t)e->nL * e->nL, s);
+    if constexpr (!std::is_same<T, double>::value) {
+        e->io_in.alloc(e->L[0].n);
+        e->io_out.alloc(e->L[0].n);
+    }
+    AMGH_CUDA(cudaStreamSynchronize(s));
+}
+
+static void check_flag(amgh_ctx* h, const char* what) {
+    int flag = 0;
+    AMGH_CUDA(cudaMemcpyAsync(&flag, h->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+    if (flag) throw StatusError{AMGH_ERR_NOT_SPD, std::string("non-positive pivot in ") + what};
+}
+
+static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false) {
+    if (!M || !M->row_ptr || (M->nnz > 0 && (!M->col || !M->val)))
+        throw StatusError{AMGH_ERR_INVALID_ARG, "null CSR pointer"};
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0 || M->nrows >= INT32_MAX || M->ncols >= INT32_MAX ||
+        M->nnz >= INT32_MAX)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "CSR dimensions out of range"};
+    HostCSR h;
+    h.nrows = (int)M->nrows;
+    h.ncols = (int)M->ncols;
+    h.ptr.resize(h.nrows + 1);
+    h.idx.resize(M->nnz);
+    h.val.resize(M->nnz);
+    if (!M->on_device) {
+        std::memcpy(h.ptr.data(), M->row_ptr, sizeof(int32_t) * (h.nrows + 1));
+        if (M->nnz) {
+            std::memcpy(h.idx.data(), M->col, sizeof(int32_t) * M->nnz);
+            std::memcpy(h.val.data(), M->val, sizeof(double) * M->nnz);
+        }
+    } else {
+        if (host_only) throw StatusError{AMGH_ERR_INVALID_ARG, "host CSR required"};
+        AMGH_CUDA(cudaMemcpyAsync(h.ptr.data(), M->row_ptr, sizeof(int32_t) * (h.nrows + 1), cudaMemcpyDeviceToHost, s));
+        if (M->nnz) {
+            AMGH_CUDA(cudaMemcpyAsync(h.idx.data(), M->col, sizeof(int32_t) * M->nnz, cudaMemcpyDeviceToHost, s));
+            AMGH_CUDA(cudaMemcpyAsync(h.val.data(), M->val, sizeof(double) * M->nnz, cudaMemcpyDeviceToHost, s));
+        }
+        AMGH_CUDA(cudaStreamSynchronize(s));
+    }
+    if (h.ptr[h.nrows] != M->nnz) throw StatusError{AMGH_ERR_INVALID_ARG, "row_ptr[nrows] != nnz"};
+    return h;
+}
+
+static void check_params(const amgh_params& prm) {
+    if (prm.max_levels < 1 || prm.max_levels > 32 || prm.coarse_size < 1 || prm.ring < 1 || prm.p_max < 1 ||
+        prm.p_max > 256 || prm.precision < 0 || prm.precision > 2 || !(prm.theta >= 0.0 && prm.theta <= 1.0) ||
+        !(prm.stall_ratio > 0.0))
+        throw StatusError{AMGH_ERR_INVALID_ARG, "parameter out of range"};
+    if (prm.interp != AMGH_INTERP_LOCAL)
+        throw StatusError{AMGH_ERR_UNSUPPORTED, "only exact local interpolation is available through amgh_setup"};
+}
+
+static void check_inputs(const HostCSR& A, const HostCSR& G) {
+    std::string e = check_csr(A, true);
+    if (e.empty()) e = check_csr(G, false);
+    if (e.empty() && G.nrows != A.nrows) e = "G must have as many rows as A";
+    if (e.empty()) e = check_gradient(G);
+    if (!e.empty()) throw StatusError{AMGH_ERR_INVALID_ARG, e};
+    if (A.nrows == 0) throw StatusError{AMGH_ERR_INVALID_ARG, "empty system"};
+}
+
+static int host_threads() {
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = std::max(1, std::min(omp_get_max_threads(), 32));
+#endif
+    return nthreads;
+}
+
+static Params graph_params(const amgh_params& prm) {
+    Params gp;
+    gp.theta = prm.theta;
+    gp.ring = prm.ring;
+    gp.p_max = prm.p_max;
+    return gp;
+}
+
+// level 0 graph steps only, on the host (structure-only handle)
+static void host_structure_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
+    check_params(h->prm);
+    HostCSR A = to_host(Ain, nullptr, true);
+    HostCSR G = to_host(Gin, nullptr, true);
+    check_inputs(A, G);
+    h->structure_only = true;
+    h->hl.emplace_back();
+    LevelHost& cur = h->hl.back();
+    cur.A = std::move(A);
+    cur.G = std::move(G);
+    std::string msg = coarsen_level(cur.A, cur.G, graph_params(h->prm), cur.cz, host_threads());
+    if (!msg.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, msg};
+    if (cur.cz.edges.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, "the finest level produced no coarse edge"};
+    msg = build_stars(cur.A, cur.G, cur.stars);
+    if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+}
+
+static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
+    cudaStream_t s = h->s;
+    const auto& prm = h->prm;
+    check_params(prm);
+    HostCSR A = to_host(Ain, s);
+    HostCSR G = to_host(Gin, s);
+    check_inputs(A, G);
+    const int nthreads = host_threads();
+    Params gp = graph_params(prm);
+    h->errflag.alloc(1);
+    h->errflag.zero(s);
+    DevCSR dA;
+    upload_csr(A, dA, s, true);
+    for (int l = 0;; ++l) {
+        h->hl.emplace_back();
+        LevelHost& cur = h->hl.back();
+        cur.A = std::move(A);
+        cur.G = std::move(G);
+        h->A64.push_back(std::move(dA));
+        const int n = cur.A.nrows;
+        bool coarsest = n <= prm.coarse_size || l + 1 >= prm.max_levels;
+        double t0 = now_ms();
+        if (!coarsest) {
+            std::string msg = coarsen_level(cur.A, cur.G, gp, cur.cz, nthreads);
+            if (!msg.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, msg};
+            const int nc = (int)cur.cz.edges.size();
+            if (nc == 0 || (double)nc > prm.stall_ratio * n) {
+                if (l == 0) throw StatusError{AMGH_ERR_SETUP_STALL, "the finest level produced no usable coarse level"};
+                coarsest = true;
+                cur.cz = Coarsening();
+            }
+        }
+        if (!coarsest) {
+            std::string msg = build_stars(cur.A, cur.G, cur.stars);
+            if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+        }
+        h->host_ms += now_ms() - t0;
+        if (coarsest) break;
+        t0 = now_ms();
+        Coarsening& cz = cur.cz;
+        const int nc = (int)cz.edges.size();
+        h->P64.emplace_back();
+        h->PT64.emplace_back();
+        DevCSR& P = h->P64.back();
+        DevCSR& PT = h->PT64.back();
+        upload_csr(cz.P, P, s, true);
+        upload_csr(cz.PT, PT, s, true);
+        std::vector<int32_t> e4(4 * (size_t)nc);
+        int maxp = 0;
+        for (int c = 0; c < nc; ++c) {
+            e4[4 * c] = cz.edges[c].d1;
+            e4[4 * c + 1] = cz.edges[c].s1;
+            e4[4 * c + 2] = cz.edges[c].d2;
+            e4[4 * c + 3] = cz.edges[c].s2;
+            maxp = std::max(maxp, cz.patch_ptr[c + 1] - cz.patch_ptr[c]);
+        }
+        h->max_patch.push_back(maxp);
+        {
+            DevArray<int32_t> de4, dpp, dpi;
+            DevArray<int64_t> dpos, dpost;
+            de4.upload(e4, s);
+            dpp.upload(cz.patch_ptr, s);
+            dpi.upload(cz.patch_idx, s);
+            dpos.upload(cz.patch_pos_P, s);
+            dpost.upload(cz.patch_pos_PT, s);
+            launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
+                               h->errflag.p, s);
+            check_flag(h, "a local harmonic-extension solve");
+        }
+        DevCSR AP, Ac;
+        upload_csr(cz.AP, AP, s, false);
+        launch_ap_numeric(h->A64[l], P, AP, s);
+        upload_csr(cz.Ac, Ac, s, false);
+        launch_ac_numeric(PT, AP, Ac, s);
+        HostCSR An = cz.Ac;   // pattern of the next level
+        An.val.resize(An.nnz());
+        AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * An.nnz(), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        h->dev_ms += now_ms() - t0;
+        A = std::move(An);
+        G = cz.Gc;
+        G.val = cz.Gc.val;
+        dA = std::move(Ac);
+    }
+    const int nL = h->hl.back().A.nrows;
+    if (nL > 2048) throw StatusError{AMGH_ERR_UNSUPPORTED, "coarsest level larger than 2048 DoFs"};
+    double t0 = now_ms();
+    {
+        DevArray<double> work;
+        work.alloc((size_t)nL * nL);
+        h->cinv64.alloc((size_t)nL * nL);
+        launch_coarse_inverse(h->A64.back(), h->cinv64.p, work.p, h->errflag.p, s);
+        check_flag(h, "the coarsest factorisation");
+    }
+    h->eng = new_engine(prm.precision);
+    h->eng->prof = &h->prof;
+    if (prm.precision == AMGH_F64) build_engine(h, static_cast<Engine<double, double>*>(h->eng.get()));
+    else if (prm.precision == AMGH_F32) build_engine(h, static_cast<Engine<float, float>*>(h->eng.get()));
+    else build_engine(h, static_cast<Engine<__nv_bfloat16, float>*>(h->eng.get()));
+    check_flag(h, "a smoother block");
+    build_sell<double>(h->hl[0].A, h->A64[0], h->A0, s);
+    h->nnzA0 = h->hl[0].A.nnz();
+    const int64_t n0 = h->hl[0].A.nrows;
+    h->kp.alloc(n0);
+    h->kq.alloc(n0);
+    h->kro.alloc(n0);
+    h->partial.alloc(2 * RED_BLOCKS);
+    h->scal.alloc(S_COUNT);
+    h->scal.zero(s);
+    AMGH_CUDA(cudaMallocHost(&h->hscal, sizeof(double) * S_COUNT));
+    h->eng->capture(s);
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    h->dev_ms += now_ms() - t0;
+}
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static double read_scalar(amgh_ctx* h, int slot) {
+    AMGH_CUDA(cudaMemcpyAsync(h->hscal, h->scal.p, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+    return h->hscal[slot];
+}
+
+// accumulate kernel timings after a stream sync: the V-cycle graph's event pairs (recorded by
+// its last launch) and, for the outer SpMV class, the pairs recorded eagerly since the last call
+static void harvest(amgh_ctx* h) {
+    if (!h->prof.enabled) { h->vc_pending = false; return; }
+    if (h->vc_pending) {
+        if (h->eng->prof_pairs) h->prof.harvest(h->eng->prof_pairs);
+        h->vc_pending = false;
+    }
+    if (h->prof.kind == K_SPMV) {
+        if (h->prof.used) h->prof.harvest(h->prof.used);
+        h->prof.used = 0;
+    }
+}
+
+// V-cycle on the engine's FP64 buffers; profiling pairs are harvested by the caller after a sync
+static void run_vcycle(amgh_ctx* h) {
+    h->launches += h->eng->vcycle(h->s);
+    h->vc_pending = true;
+}
+
+struct Staged {
+    const double* f;
+    double* x;
+};
+
+static Staged stage_in(amgh_ctx* h, const double* f, double* x, bool copy_x) {
+    const int64_t n = h->hl[0].A.nrows;
+    bool df = is_device_ptr(f), dx = is_device_ptr(x);
+    if (df != dx) throw StatusError{AMGH_ERR_INVALID_ARG, "f and x must both be host or both be device pointers"};
+    if (df) return {f, x};
+    if (h->stage_f.n != (size_t)n) { h->stage_f.alloc(n); h->stage_x.alloc(n); }
+    AMGH_CUDA(cudaMemcpyAsync(h->stage_f.p, f, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+    if (copy_x) AMGH_CUDA(cudaMemcpyAsync(h->stage_x.p, x, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+    return {h->stage_f.p, h->stage_x.p};
+}
+
+static void stage_out(amgh_ctx* h, const Staged& st, double* x) {
+    const int64_t n = h->hl[0].A.nrows;
+    if (st.x != x) AMGH_CUDA(cudaMemcpyAsync(x, st.x, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+}
+
+template <class F>
+static void outer_spmv_timed(amgh_ctx* h, F&& fn) {
+    if (h->prof.match(K_SPMV, 0)) {
+        auto ev = h->prof.next();
+        h->prof.bytes_used.resize(h->prof.used);
+        h->prof.bytes_used[h->prof.used - 1] = (double)h->nnzA0 * 12.0 + 4.0 * h->A0.nrows + 16.0 * h->A0.nrows;
+        h->prof.record(ev.first, h->s);
+        fn();
+        h->prof.record(ev.second, h->s);
+    } else {
+        fn();
+    }
+}
+
+static amgh_status pcg_impl(amgh_ctx* h, const double* f_in, double* x_in, double tol, int maxit, int* iters,
+                            double* relres) {
+    if (maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
+    cudaStream_t s = h->s;
+    const int64_t n = h->hl[0].A.nrows;
+    const bool flexible = h->prm.precision != AMGH_F64;
+    Staged st = stage_in(h, f_in, x_in, true);
+    const double* f = st.f;
+    double* x = st.x;
+    double* r = h->eng->in64();
+    double* z = h->eng->out64();
+    double* p = h->kp.p;
+    double* q = h->kq.p;
+    h->prof.used = 0;
+    outer_spmv_timed(h, [&] { launch_sell<double, double>(SELL_RESID, h->A0, x, f, nullptr, r, s); });
+    launch_dot(n, r, r, h->partial.p, s);
+    launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, s);
+    h->launches += 3;
+    const double r0 = std::sqrt(read_scalar(h, S_TMP));
+    harvest(h);
+    h->prof.used = 0;
+    int it = 0;
+    double rel = 0.0;
+    amgh_status status = AMGH_OK;
+    if (r0 > 0.0) {
+        run_vcycle(h);
+        launch_dot2(n, r, z, nullptr, h->partial.p, s);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_RZ, s);
+        AMGH_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        h->launches += 2;
+        rel = 1.0;
+        bool conv = false;
+        for (it = 1; it <= maxit; ++it) {
+            outer_spmv_timed(h, [&] { launch_spmv_dot(h->A0, p, q, h->partial.p, s); });
+            launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_ALPHA, s);
+            launch_cg_update(n, x, r, flexible ? h->kro.p : nullptr, p, q, h->scal.p, h->partial.p, s);
+            launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, s);
+            h->launches += 4;
+            const double rr = read_scalar(h, S_TMP);
+            harvest(h);
+            h->prof.used = 0;
+            rel = std::sqrt(rr) / r0;
+            if (!(rel == rel)) throw StatusError{AMGH_ERR_NOT_CONVERGED, "residual became NaN"};
+            if (rel <= tol) { conv = true; break; }
+            run_vcycle(h);
+            launch_dot2(n, r, z, flexible ? h->kro.p : nullptr, h->partial.p, s);
+            launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, flexible ? SC_BETA_FCG : SC_BETA_CG, s);
+            launch_p_update(n, p, z, h->scal.p, s);
+            h->launches += 3;
+        }
+        if (!conv) { it = maxit; status = AMGH_ERR_NOT_CONVERGED; }
+    }
+    stage_out(h, st, x_in);
+    harvest(h);
+    h->prof.used = 0;
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (status != AMGH_OK) h->err = "PCG reached maxit before the tolerance";
+    return status;
+}
+
+static amgh_status amg_impl(amgh_ctx* h, const double* f_in, double* x_in, double tol, int maxit, int* iters,
+                            double* relres) {
+    if (maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
+    cudaStream_t s = h->s;
+    const int64_t n = h->hl[0].A.nrows;
+    Staged st = stage_in(h, f_in, x_in, true);
+    double* r = h->eng->in64();
+    double* z = h->eng->out64();
+    h->prof.used = 0;
+    double r0 = 0.0, rel = 0.0;
+    int it = 0;
+    amgh_status status = AMGH_OK;
+    for (it = 0; it <= maxit; ++it) {
+        outer_spmv_timed(h, [&] { launch_sell<double, double>(SELL_RESID, h->A0, st.x, st.f, nullptr, r, s); });
+        launch_dot(n, r, r, h->partial.p, s);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, s);
+        h->launches += 3;
+        const double nr = std::sqrt(read_scalar(h, S_TMP));
+        harvest(h);
+        h->prof.used = 0;
+        if (it == 0) r0 = nr;
+        rel = r0 > 0 ? nr / r0 : 0.0;
+        if (r0 == 0.0 || rel <= tol) break;
+        if (it == maxit) { status = AMGH_ERR_NOT_CONVERGED; break; }
+        run_vcycle(h);
+        launch_axpy1(n, st.x, z, s);
+        h->launches += 1;
+    }
+    stage_out(h, st, x_in);
+    harvest(h);
+    h->prof.used = 0;
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (status != AMGH_OK) h->err = "stand-alone V-cycle iteration reached maxit before the tolerance";
+    return status;
+}
+
+}  // namespace amgh
+
+// =============================================================================================
+// C-ABI
+// =============================================================================================
+template <class F>
+static amgh_status guarded(amgh_ctx* h, F&& fn) {
+    try {
+        return fn();
+    } catch (const StatusError& e) {
+        if (h) h->err = e.msg;
+        else g_setup_error = e.msg;
+        return e.st;
+    } catch (const CudaError& e) {
+        std::string m = std::string("CUDA error ") + cudaGetErrorString(e.code) + " in " + e.where;
+        if (h) h->err = m;
+        else g_setup_error = m;
+        return AMGH_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        if (h) h->err = "host allocation failed";
+        else g_setup_error = "host allocation failed";
+        return AMGH_ERR_OOM;
+    } catch (const std::exception& e) {
+        if (h) h->err = e.what();
+        else g_setup_error = e.what();
+        return AMGH_ERR_INVALID_ARG;
+    }
+}
+
+extern "C" {
+
+void amgh_default_params(amgh_params* p) {
+    if (!p) return;
+    p->max_levels = 20;
+    p->coarse_size = 100;
+    p->precision = AMGH_F64;
+    p->interp = AMGH_INTERP_LOCAL;
+    p->ring = 1;
+    p->p_max = 128;
+    p->theta = 0.25;
+    p->stall_ratio = 0.9;
+    p->stream = nullptr;
+}
+
+amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params, amgh_handle* out) {
+    if (!out) return AMGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    amgh_ctx* h = nullptr;
+    try {
+        h = new amgh_ctx();
+    } catch (...) {
+        g_setup_error = "host allocation failed";
+        return AMGH_ERR_OOM;
+    }
+    if (params) h->prm = *params;
+    else amgh_default_params(&h->prm);
+    h->s = (cudaStream_t)h->prm.stream;
+    amgh_status st = guarded(h, [&] {
+        if (!h->s) {
+            // a blocking stream of our own: ordered with the legacy default stream, capturable
+            AMGH_CUDA(cudaStreamCreate(&h->s));
+            h->own_stream = true;
+        }
+        setup_impl(h, A, G);
+        return AMGH_OK;
+    });
+    if (st != AMGH_OK) {
+        g_setup_error = h->err;
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AMGH_OK;
+}
+
+amgh_status amgh_setup_host_structure(const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
+                                      amgh_handle* out) {
+    if (!out) return AMGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    amgh_ctx* h = nullptr;
+    try {
+        h = new amgh_ctx();
+    } catch (...) {
+        g_setup_error = "host allocation failed";
+        return AMGH_ERR_OOM;
+    }
+    if (params) h->prm = *params;
+    else amgh_default_params(&h->prm);
+    amgh_status st = guarded(h, [&] {
+        host_structure_impl(h, A, G);
+        return AMGH_OK;
+    });
+    if (st != AMGH_OK) {
+        g_setup_error = h->err;
+        delete h;
+        return st;
+    }
+    *out = h;
+    return AMGH_OK;
+}
+
+amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z) {
+    if (!h || !r || !z || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const int64_t n = h->hl[0].A.nrows;
+        bool dr = is_device_ptr(r), dz = is_device_ptr(z);
+        if (dr != dz) throw StatusError{AMGH_ERR_INVALID_ARG, "r and z must both be host or both be device pointers"};
+        auto kind_in = dr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        auto kind_out = dr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        h->prof.used = 0;
+        AMGH_CUDA(cudaMemcpyAsync(h->eng->in64(), r, sizeof(double) * n, kind_in, h->s));
+        run_vcycle(h);
+        AMGH_CUDA(cudaMemcpyAsync(z, h->eng->out64(), sizeof(double) * n, kind_out, h->s));
+        AMGH_CUDA(cudaStreamSynchronize(h->s));
+        harvest(h);
+        h->prof.used = 0;
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
+                           double* relres) {
+    if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] { return pcg_impl(h, f, x, tol, maxit, iters, relres); });
+}
+
+amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
+                           double* relres) {
+    if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] { return amg_impl(h, f, x, tol, maxit, iters, relres); });
+}
+
+amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
+    if (!h || !info || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        std::memset(info, 0, sizeof(*info));
+        const int nlev = (int)h->hl.size();
+        info->levels = nlev;
+        double nnz0 = (double)h->hl[0].A.nnz(), n0 = (double)h->hl[0].A.nrows, so = 0, sg = 0;
+        for (int l = 0; l < nlev && l < 32; ++l) {
+            const auto& L = h->hl[l];
+            info->n[l] = L.A.nrows;
+            info->nnz[l] = L.A.nnz();
+            info->nnz_p[l] = L.cz.P.nnz();
+            info->ncolours[l] = L.stars.ncolours;
+            info->max_block[l] = L.stars.max_block;
+            info->max_patch[l] = l < (int)h->max_patch.size() ? h->max_patch[l] : 0;
+            so += L.A.nnz();
+            sg += L.A.nrows;
+        }
+        info->op_complexity = so / nnz0;
+        info->grid_complexity = sg / n0;
+        info->setup_host_ms = h->host_ms;
+        info->setup_device_ms = h->dev_ms;
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_level_structure(amgh_handle h, int l, int64_t* n_nodes_aug, int64_t* n_edges,
+                                 int64_t* n_coarse_nodes, int64_t* patch_nnz, int64_t* n_stars, int8_t* cf_state,
+                                 int32_t* coarse_edges, int32_t* coarse_nodes, int32_t* patch_ptr, int32_t* patch_idx,
+                                 int32_t* colour) {
+    if (!h || l < 0 || l >= (int)h->hl.size() || (!h->structure_only && l + 1 >= (int)h->hl.size()))
+        return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const auto& L = h->hl[l];
+        const auto& cz = L.cz;
+        if (n_nodes_aug) *n_nodes_aug = (int64_t)cz.state.size();
+        if (n_edges) *n_edges = (int64_t)cz.edges.size();
+        if (n_coarse_nodes) *n_coarse_nodes = (int64_t)cz.coarse_nodes.size();
+        if (patch_nnz) *patch_nnz = (int64_t)cz.patch_idx.size();
+        if (n_stars) *n_stars = L.stars.nstars;
+        if (cf_state) std::memcpy(cf_state, cz.state.data(), cz.state.size());
+        if (coarse_edges)
+            for (size_t c = 0; c < cz.edges.size(); ++c) {
+                const auto& e = cz.edges[c];
+                int32_t v[7] = {e.d1, e.s1, e.d2, e.s2, e.i, e.k, e.j};
+                std::memcpy(coarse_edges + 7 * c, v, sizeof(v));
+            }
+        if (coarse_nodes) std::memcpy(coarse_nodes, cz.coarse_nodes.data(), cz.coarse_nodes.size() * 4);
+        if (patch_ptr) std::memcpy(patch_ptr, cz.patch_ptr.data(), cz.patch_ptr.size() * 4);
+        if (patch_idx) std::memcpy(patch_idx, cz.patch_idx.data(), cz.patch_idx.size() * 4);
+        if (colour) std::memcpy(colour, L.stars.colour.data(), L.stars.colour.size() * 4);
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, int64_t* ncols, int64_t* nnz,
+                              int32_t* row_ptr, int32_t* col, double* val) {
+    if (!h || l < 0 || l >= (int)h->hl.size() || which < 0 || which > 3) return AMGH_ERR_INVALID_ARG;
+    const bool has_coarse = h->structure_only || l + 1 < (int)h->hl.size();
+    if ((which == 1 || which == 3) && !has_coarse) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const auto& L = h->hl[l];
+        const HostCSR& M = which == 0 ? L.A : (which == 1 ? L.cz.P : (which == 2 ? L.G : L.cz.Ac));
+        if (nrows) *nrows = M.nrows;
+        if (ncols) *ncols = M.ncols;
+        if (nnz) *nnz = M.nnz();
+        if (row_ptr) std::memcpy(row_ptr, M.ptr.data(), M.ptr.size() * 4);
+        if (col) std::memcpy(col, M.idx.data(), M.idx.size() * 4);
+        if (val) {
+            if (which == 2 || (h->structure_only && which != 3)) {
+                std::memcpy(val, M.val.data(), M.val.size() * 8);
+            } else if (h->structure_only) {
+                std::memset(val, 0, sizeof(double) * M.nnz());
+            } else {
+                const DevCSR& D = which == 0 ? h->A64[l] : (which == 1 ? h->P64[l] : h->A64[l + 1]);
+                AMGH_CUDA(cudaMemcpyAsync(val, D.val.p, sizeof(double) * D.nnz, cudaMemcpyDeviceToHost, h->s));
+                AMGH_CUDA(cudaStreamSynchronize(h->s));
+            }
+        }
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_level_apply(amgh_handle h, int l, int op, const double* f, const double* x, double* y) {
+    if (!h || !x || !y || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    if ((op == 1 || op == 2 || op == 3) && !f) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const bool was = h->prof.enabled;
+        h->prof.enabled = false;   // single steps are never timed
+        try {
+            h->eng->level_apply(l, op, f, x, y, h->s);
+        } catch (...) {
+            h->prof.enabled = was;
+            throw;
+        }
+        h->prof.enabled = was;
+        AMGH_CUDA(cudaStreamSynchronize(h->s));
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_profile(amgh_handle h, int enable, int kind, int level) {
+    if (!h || kind < 0 || kind > 6 || level < 0 || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        h->prof.enabled = enable != 0;
+        h->prof.gen++;
+        h->prof.kind = kind;
+        h->prof.level = level;
+        h->prof.launches = 0;
+        h->prof.total_ms = 0;
+        h->prof.bytes = 0;
+        h->prof.used = 0;
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_kernel_stats(amgh_handle h, int64_t* launches, double* total_ms, double* algorithmic_bytes) {
+    if (!h) return AMGH_ERR_INVALID_ARG;
+    if (launches) *launches = h->prof.launches;
+    if (total_ms) *total_ms = h->prof.total_ms;
+    if (algorithmic_bytes) *algorithmic_bytes = h->prof.bytes;
+    return AMGH_OK;
+}
+
+int64_t amgh_launch_count(amgh_handle) { return launch_counter().load(); }
+
+const char* amgh_last_error(amgh_handle h) {
+    if (!h) return g_setup_error.c_str();
+    return h->err.c_str();
+}
+
+void amgh_destroy(amgh_handle h) {
+    if (!h) return;
+    if (!h->structure_only) cudaStreamSynchronize(h->s);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,629 @@
+// Host graph steps of the algebraic H(curl) coarsening (Section 4): Alg. 1 (augment G),
+// the nodal graph of the dual operator and Alg. 2 (nodal C/F splitting), Alg. 3 (pairing fine
+// edges along distance-two nodal paths), Eq. Gc (coarse gradient), the patches of the local
+// interior harmonic extension (Eq. sparseP), the symbolic Galerkin patterns, and the node-star
+// blocks and colouring of the OSS-l1 smoother (Section 5).
+#include "host_graph.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <queue>
+#include <utility>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace amgh {
+
+namespace {
+
+inline int thread_id() {
+#ifdef _OPENMP
+    return omp_get_thread_num();
+#else
+    return 0;
+#endif
+}
+
+inline bool has(const HostCSR& M, int r, int c) {
+    auto b = M.idx.begin() + M.ptr[r], e = M.idx.begin() + M.ptr[r + 1];
+    return std::binary_search(b, e, c);
+}
+
+// Build CSR from per-row sorted vectors
+HostCSR from_rows(int nrows, int ncols, const std::vector<std::vector<int32_t>>& rows) {
+    HostCSR M;
+    M.nrows = nrows;
+    M.ncols = ncols;
+    M.ptr.assign(nrows + 1, 0);
+    for (int r = 0; r < nrows; ++r) M.ptr[r + 1] = M.ptr[r] + (int32_t)rows[r].size();
+    M.idx.resize(M.ptr[nrows]);
+    for (int r = 0; r < nrows; ++r) std::copy(rows[r].begin(), rows[r].end(), M.idx.begin() + M.ptr[r]);
+    return M;
+}
+
+// Symbolic product row by row: out row r = union over t in X row r of Y row X.idx[t].
+HostCSR symbolic_rows(const HostCSR& X, const HostCSR& Y, int nthreads) {
+    HostCSR M;
+    M.nrows = X.nrows;
+    M.ncols = Y.ncols;
+    M.ptr.assign(X.nrows + 1, 0);
+    std::vector<std::vector<int32_t>> mark(nthreads, std::vector<int32_t>(Y.ncols, -1));
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int r = 0; r < X.nrows; ++r) {
+        auto& mk = mark[thread_id()];
+        int32_t cnt = 0;
+        for (int32_t t = X.ptr[r]; t < X.ptr[r + 1]; ++t) {
+            int32_t y = X.idx[t];
+            for (int32_t u = Y.ptr[y]; u < Y.ptr[y + 1]; ++u) {
+                int32_t c = Y.idx[u];
+                if (mk[c] != r) { mk[c] = r; ++cnt; }
+            }
+        }
+        M.ptr[r + 1] = cnt;
+    }
+    for (int r = 0; r < X.nrows; ++r) M.ptr[r + 1] += M.ptr[r];
+    M.idx.resize(M.ptr[X.nrows]);
+    for (auto& mk : mark) std::fill(mk.begin(), mk.end(), -1);
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int r = 0; r < X.nrows; ++r) {
+        auto& mk = mark[thread_id()];
+        int32_t pos = M.ptr[r];
+        for (int32_t t = X.ptr[r]; t < X.ptr[r + 1]; ++t) {
+            int32_t y = X.idx[t];
+            for (int32_t u = Y.ptr[y]; u < Y.ptr[y + 1]; ++u) {
+                int32_t c = Y.idx[u];
+                if (mk[c] != r) { mk[c] = r; M.idx[pos++] = c; }
+            }
+        }
+        std::sort(M.idx.begin() + M.ptr[r], M.idx.begin() + M.ptr[r + 1]);
+    }
+    return M;
+}
+
+}  // namespace
+
+HostCSR transpose_pattern(const HostCSR& M, bool with_values) {
+    HostCSR T;
+    T.nrows = M.ncols;
+    T.ncols = M.nrows;
+    T.ptr.assign(T.nrows + 1, 0);
+    for (int32_t c : M.idx) T.ptr[c + 1]++;
+    for (int r = 0; r < T.nrows; ++r) T.ptr[r + 1] += T.ptr[r];
+    T.idx.resize(M.idx.size());
+    if (with_values) T.val.resize(M.idx.size());
+    std::vector<int32_t> cur(T.ptr.begin(), T.ptr.end() - 1);
+    for (int r = 0; r < M.nrows; ++r)
+        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+            int32_t p = cur[M.idx[e]]++;
+            T.idx[p] = r;
+            if (with_values) T.val[p] = M.val[e];
+        }
+    return T;
+}
+
+std::string check_csr(const HostCSR& M, bool square) {
+    if (M.nrows < 0 || M.ncols < 0) return "negative dimension";
+    if (square && M.nrows != M.ncols) return "matrix is not square";
+    if ((int64_t)M.ptr.size() != (int64_t)M.nrows + 1 || M.ptr[0] != 0) return "bad row_ptr";
+    for (int r = 0; r < M.nrows; ++r) {
+        if (M.ptr[r + 1] < M.ptr[r]) return "row_ptr not monotone";
+        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+            int32_t c = M.idx[e];
+            if (c < 0 || c >= M.ncols) return "column index out of range in row " + std::to_string(r);
+            if (e > M.ptr[r] && M.idx[e - 1] >= c) return "columns not strictly ascending in row " + std::to_string(r);
+        }
+    }
+    return "";
+}
+
+std::string check_gradient(const HostCSR& G) {
+    for (int r = 0; r < G.nrows; ++r) {
+        int32_t n = G.ptr[r + 1] - G.ptr[r];
+        // 0 entries: an interior edge joining two boundary nodes (e.g. a corner diagonal)
+        if (n > 2) return "G row " + std::to_string(r) + " has " + std::to_string(n) + " entries (at most 2)";
+        for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e)
+            if (G.val[e] != 1.0 && G.val[e] != -1.0) return "G entry other than +-1 in row " + std::to_string(r);
+        if (n == 2 && G.val[G.ptr[r]] == G.val[G.ptr[r] + 1]) return "G row " + std::to_string(r) + " entries share a sign";
+    }
+    return "";
+}
+
+// -------------------------------------------------------------------------------------------
+// Alg. 1: one artificial column per boundary edge-row (a row of G with one entry delta; the
+// new column holds -delta in that row).
+// -------------------------------------------------------------------------------------------
+static HostCSR augment(const HostCSR& G, int& nB) {
+    HostCSR Gt;
+    Gt.nrows = G.nrows;
+    Gt.ptr.assign(G.nrows + 1, 0);
+    nB = 0;
+    for (int r = 0; r < G.nrows; ++r) nB += (G.ptr[r + 1] - G.ptr[r] == 1);
+    Gt.ncols = G.ncols + nB;
+    Gt.idx.reserve(G.nnz() + nB);
+    Gt.val.reserve(G.nnz() + nB);
+    int b = G.ncols;
+    for (int r = 0; r < G.nrows; ++r) {
+        for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e) {
+            Gt.idx.push_back(G.idx[e]);
+            Gt.val.push_back(G.val[e]);
+        }
+        if (G.ptr[r + 1] - G.ptr[r] == 1) {
+            Gt.idx.push_back(b++);
+            Gt.val.push_back(-G.val[G.ptr[r]]);
+        }
+        Gt.ptr[r + 1] = (int32_t)Gt.idx.size();
+    }
+    return Gt;
+}
+
+// -------------------------------------------------------------------------------------------
+// Nodal graph (Section 4.1, reading of Alg. 2's "classical C/F splitting"): between gradient
+// modes (original columns of G) a Ruge-Stueben strong connection of A_G = G^T A G in either
+// direction, -a_ij >= theta max_{k != i}(-a_ik); any two columns of G~ sharing a row (edge).
+// -------------------------------------------------------------------------------------------
+static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt, const HostCSR& GtT,
+                           double theta, int nthreads, HostCSR& Minc) {
+    const int m = G.ncols, nn = Gt.ncols, ne = A.nrows;
+    HostCSR GT = transpose_pattern(G, true);   // CSC of G: rows of column i with values
+    // incidence: columns sharing a row of G~
+    std::vector<std::vector<int32_t>> inc(nn);
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads)
+    for (int a = 0; a < nn; ++a) {
+        auto& v = inc[a];
+        for (int32_t t = GtT.ptr[a]; t < GtT.ptr[a + 1]; ++t) {
+            int32_t r = GtT.idx[t];
+            for (int32_t u = Gt.ptr[r]; u < Gt.ptr[r + 1]; ++u)
+                if (Gt.idx[u] != a) v.push_back(Gt.idx[u]);
+        }
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    Minc = from_rows(nn, nn, inc);
+    // strong connections among gradient modes
+    std::vector<std::vector<int32_t>> strong(m);
+    std::vector<std::vector<int32_t>> wmark(nthreads, std::vector<int32_t>(ne, -1));
+    std::vector<std::vector<double>> w(nthreads, std::vector<double>(ne, 0.0));
+    std::vector<std::vector<int32_t>> amark(nthreads, std::vector<int32_t>(m, -1));
+    std::vector<std::vector<double>> acc(nthreads, std::vector<double>(m, 0.0));
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int i = 0; i < m; ++i) {
+        int tid = thread_id();
+        auto& wm = wmark[tid];
+        auto& wv = w[tid];
+        auto& am = amark[tid];
+        auto& av = acc[tid];
+        std::vector<int32_t> tf, tj;
+        // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
+        for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) {
+            int32_t e = GT.idx[t];
+            double ge = GT.val[t];
+            for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
+                int32_t f = A.idx[q];
+                if (wm[f] != i) { wm[f] = i; wv[f] = 0.0; tf.push_back(f); }
+                wv[f] += ge * A.val[q];
+            }
+        }
+        // row i of G^T A G
+        for (int32_t f : tf)
+            for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
+                int32_t j = G.idx[u];
+                if (am[j] != i) { am[j] = i; av[j] = 0.0; tj.push_back(j); }
+                av[j] += G.val[u] * wv[f];
+            }
+        double rowmax = -INFINITY;
+        for (int32_t j : tj)
+            if (j != i) rowmax = std::max(rowmax, -av[j]);
+        if (rowmax > 0.0) {
+            auto& s = strong[i];
+            for (int32_t j : tj)
+                if (j != i && -av[j] >= theta * rowmax) s.push_back(j);
+        }
+    }
+    // symmetrise and merge with the incidence graph
+    std::vector<std::vector<int32_t>> nb(nn);
+    for (int a = 0; a < nn; ++a) nb[a] = inc[a];
+    for (int i = 0; i < m; ++i)
+        for (int32_t j : strong[i]) {
+            nb[i].push_back(j);
+            nb[j].push_back(i);
+        }
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads)
+    for (int a = 0; a < nn; ++a) {
+        auto& v = nb[a];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    return from_rows(nn, nn, nb);
+}
+
+// -------------------------------------------------------------------------------------------
+// Alg. 2: C starts as the artificial boundary columns, their neighbours start as F, then the
+// Ruge-Stueben first pass (measure |N & U| + 2 |N & F|, largest first, ties to the smallest
+// index) splits the remaining nodes; nodes without neighbours are F.
+// -------------------------------------------------------------------------------------------
+enum : int8_t { ST_U = 0, ST_C = 1, ST_F = 2 };
+
+static void nodal_cf(const HostCSR& N, int m, std::vector<int8_t>& st) {
+    const int nn = N.nrows;
+    st.assign(nn, ST_U);
+    for (int b = m; b < nn; ++b) st[b] = ST_C;
+    for (int b = m; b < nn; ++b)
+        for (int32_t t = N.ptr[b]; t < N.ptr[b + 1]; ++t)
+            if (st[N.idx[t]] == ST_U) st[N.idx[t]] = ST_F;
+    for (int i = 0; i < nn; ++i)
+        if (st[i] == ST_U && N.ptr[i + 1] == N.ptr[i]) st[i] = ST_F;
+    std::vector<int64_t> lam(nn, 0);
+    using Key = std::pair<int64_t, int32_t>;   // (measure, -index): max-heap top is the choice
+    std::priority_queue<Key> heap;
+    for (int i = 0; i < nn; ++i) {
+        if (st[i] != ST_U) continue;
+        int64_t l = 0;
+        for (int32_t t = N.ptr[i]; t < N.ptr[i + 1]; ++t) {
+            int8_t s = st[N.idx[t]];
+            l += (s == ST_U) ? 1 : (s == ST_F ? 2 : 0);
+        }
+        lam[i] = l;
+        heap.push({l, -i});
+    }
+    std::vector<int32_t> newf;
+    while (!heap.empty()) {
+        Key top = heap.top();
+        heap.pop();
+        int32_t i = -top.second;
+        if (st[i] != ST_U || lam[i] != top.first) continue;
+        st[i] = ST_C;
+        newf.clear();
+        for (int32_t t = N.ptr[i]; t < N.ptr[i + 1]; ++t)
+            if (st[N.idx[t]] == ST_U) {
+                st[N.idx[t]] = ST_F;
+                newf.push_back(N.idx[t]);
+            }
+        for (int32_t j : newf)
+            for (int32_t t = N.ptr[j]; t < N.ptr[j + 1]; ++t) {
+                int32_t l = N.idx[t];
+                if (st[l] == ST_U) heap.push({++lam[l], -l});
+            }
+    }
+}
+
+// -------------------------------------------------------------------------------------------
+// Alg. 3, enumerated around the middle node: every pair (a, b) of coarse columns (C = c_G u B)
+// in M(k), a < b, not both artificial, not neighbours, has k as a candidate.  Sorting the triples
+// (a, b, k) visits the pairs in the order of the pair loop over C x C, and the first candidate
+// k not yet used is taken (R: smallest middle node), which reproduces Alg. 3 exactly.
+// -------------------------------------------------------------------------------------------
+static void match(const HostCSR& Gt, const HostCSR& GtT, const HostCSR& N, const HostCSR& M,
+                  const std::vector<int8_t>& st, int m, std::vector<CoarseEdge>& out) {
+    const int nn = N.nrows;
+    struct Tri { int32_t a, b, k; };
+    std::vector<Tri> tri;
+    std::vector<int32_t> cand;
+    for (int k = 0; k < nn; ++k) {
+        cand.clear();
+        for (int32_t t = M.ptr[k]; t < M.ptr[k + 1]; ++t)
+            if (st[M.idx[t]] == ST_C) cand.push_back(M.idx[t]);
+        for (size_t x = 0; x < cand.size(); ++x)
+            for (size_t y = x + 1; y < cand.size(); ++y) {
+                int32_t a = cand[x], b = cand[y];
+                if (a >= m && b >= m) continue;           // (i, j) both artificial
+                if (has(N, a, b)) continue;               // neighbours: not at distance two
+                if (!has(N, a, k) || !has(N, b, k)) continue;
+                tri.push_back({a, b, k});
+            }
+    }
+    std::sort(tri.begin(), tri.end(), [](const Tri& x, const Tri& y) {
+        if (x.a != y.a) return x.a < y.a;
+        if (x.b != y.b) return x.b < y.b;
+        return x.k < y.k;
+    });
+    std::vector<char> used(nn, 0);
+    auto edge_between = [&](int32_t u, int32_t v) -> int32_t {   // smallest row of G~ holding u and v
+        for (int32_t t = GtT.ptr[v]; t < GtT.ptr[v + 1]; ++t) {
+            int32_t r = GtT.idx[t];
+            if (Gt.ptr[r + 1] - Gt.ptr[r] == 2 && (Gt.idx[Gt.ptr[r]] == u || Gt.idx[Gt.ptr[r] + 1] == u)) return r;
+        }
+        return -1;
+    };
+    auto value_at = [&](int32_t r, int32_t c) -> int32_t {
+        for (int32_t u = Gt.ptr[r]; u < Gt.ptr[r + 1]; ++u)
+            if (Gt.idx[u] == c) return (int32_t)Gt.val[u];
+        return 0;
+    };
+    size_t p = 0;
+    while (p < tri.size()) {
+        size_t q = p;
+        while (q < tri.size() && tri[q].a == tri[p].a && tri[q].b == tri[p].b) ++q;
+        for (size_t s = p; s < q; ++s) {
+            int32_t k = tri[s].k;
+            if (used[k]) continue;
+            int32_t i = tri[s].a, j = tri[s].b;
+            int32_t d1 = edge_between(i, k), d2 = edge_between(j, k);
+            used[k] = 1;
+            out.push_back({d1, value_at(d1, k), d2, -value_at(d2, k), i, k, j});
+            break;
+        }
+        p = q;
+    }
+}
+
+std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
+                          int nthreads) {
+    const int n = A.nrows;
+    int nB = 0;
+    HostCSR Gt = augment(G, nB);
+    HostCSR GtT = transpose_pattern(Gt, false);
+    HostCSR Minc;
+    HostCSR N = nodal_graph(A, G, Gt, GtT, prm.theta, nthreads, Minc);
+    out.m = G.ncols;
+    out.nB = nB;
+    nodal_cf(N, G.ncols, out.state);
+    out.edges.clear();
+    match(Gt, GtT, N, Minc, out.state, G.ncols, out.edges);
+    const int nc = (int)out.edges.size();
+    if (nc == 0) return "";
+    for (const auto& e : out.edges)
+        if (e.d1 < 0 || e.d2 < 0) return "internal: matching found no edge for a path";
+
+    // Eq. Gc: rows e_j - e_i (or -e_i when j is artificial); keep the nonzero columns
+    std::vector<char> keep(G.ncols, 0);
+    for (const auto& e : out.edges) {
+        keep[e.i] = 1;
+        if (e.j < G.ncols) keep[e.j] = 1;
+    }
+    std::vector<int32_t> newid(G.ncols, -1);
+    out.coarse_nodes.clear();
+    for (int v = 0; v < G.ncols; ++v)
+        if (keep[v]) {
+            newid[v] = (int32_t)out.coarse_nodes.size();
+            out.coarse_nodes.push_back(v);
+        }
+    HostCSR& Gc = out.Gc;
+    Gc.nrows = nc;
+    Gc.ncols = (int)out.coarse_nodes.size();
+    Gc.ptr.assign(nc + 1, 0);
+    Gc.idx.clear();
+    Gc.val.clear();
+    for (int c = 0; c < nc; ++c) {
+        const auto& e = out.edges[c];
+        // i < j always; new ids keep the order
+        Gc.idx.push_back(newid[e.i]);
+        Gc.val.push_back(-1.0);
+        if (e.j < G.ncols) {
+            Gc.idx.push_back(newid[e.j]);
+            Gc.val.push_back(1.0);
+        }
+        Gc.ptr[c + 1] = (int32_t)Gc.idx.size();
+    }
+
+    // ---- Eq. sparseP patches: components of graph(A_II) if small enough, else rings ----------
+    std::vector<char> ext(n, 0);
+    for (const auto& e : out.edges) ext[e.d1] = ext[e.d2] = 1;
+    std::vector<int32_t> parent(n);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int32_t x) {
+        while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
+        return x;
+    };
+    for (int r = 0; r < n; ++r) {
+        if (ext[r]) continue;
+        for (int32_t t = A.ptr[r]; t < A.ptr[r + 1]; ++t) {
+            int32_t c = A.idx[t];
+            if (c > r && !ext[c]) {
+                int32_t x = find(r), y = find(c);
+                if (x != y) parent[std::max(x, y)] = std::min(x, y);
+            }
+        }
+    }
+    std::vector<int32_t> comp(n, -1), csize;
+    {
+        std::vector<int32_t> label(n, -1);
+        for (int r = 0; r < n; ++r)
+            if (!ext[r]) {
+                int32_t root = find(r);
+                if (label[root] < 0) { label[root] = (int32_t)csize.size(); csize.push_back(0); }
+                comp[r] = label[root];
+                csize[comp[r]]++;
+            }
+    }
+    std::vector<int32_t> cptr(csize.size() + 1, 0), cmem(n);
+    for (size_t c = 0; c < csize.size(); ++c) cptr[c + 1] = cptr[c] + csize[c];
+    {
+        std::vector<int32_t> cur(cptr.begin(), cptr.end() - 1);
+        for (int r = 0; r < n; ++r)
+            if (comp[r] >= 0) cmem[cur[comp[r]]++] = r;   // ascending within a component
+    }
+    std::vector<std::vector<int32_t>> patches(nc);
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+    for (int c = 0; c < nc; ++c) {
+        const auto& e = out.edges[c];
+        std::vector<int32_t> seeds;
+        for (int32_t d : {e.d1, e.d2})
+            for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t)
+                if (!ext[A.idx[t]]) seeds.push_back(A.idx[t]);
+        std::sort(seeds.begin(), seeds.end());
+        seeds.erase(std::unique(seeds.begin(), seeds.end()), seeds.end());
+        std::vector<int32_t> comps;
+        for (int32_t s : seeds) comps.push_back(comp[s]);
+        std::sort(comps.begin(), comps.end());
+        comps.erase(std::unique(comps.begin(), comps.end()), comps.end());
+        int64_t tot = 0;
+        for (int32_t q : comps) tot += csize[q];
+        auto& pt = patches[c];
+        if (tot <= prm.p_max) {
+            for (int32_t q : comps) pt.insert(pt.end(), cmem.begin() + cptr[q], cmem.begin() + cptr[q + 1]);
+        } else {
+            std::vector<int32_t> order = seeds, level = seeds;
+            std::vector<int32_t> seen = seeds;   // sorted
+            for (int r = 1; r < prm.ring && (int)order.size() < prm.p_max; ++r) {
+                std::vector<int32_t> nxt;
+                for (int32_t d : level)
+                    for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t) {
+                        int32_t x = A.idx[t];
+                        if (!ext[x] && !std::binary_search(seen.begin(), seen.end(), x)) nxt.push_back(x);
+                    }
+                std::sort(nxt.begin(), nxt.end());
+                nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
+                order.insert(order.end(), nxt.begin(), nxt.end());
+                std::vector<int32_t> merged;
+                std::merge(seen.begin(), seen.end(), nxt.begin(), nxt.end(), std::back_inserter(merged));
+                seen.swap(merged);
+                level.swap(nxt);
+            }
+            if ((int)order.size() > prm.p_max) order.resize(prm.p_max);
+            pt = order;
+        }
+        std::sort(pt.begin(), pt.end());
+    }
+    out.patch_ptr.assign(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) out.patch_ptr[c + 1] = out.patch_ptr[c] + (int32_t)patches[c].size();
+    out.patch_idx.resize(out.patch_ptr[nc]);
+    for (int c = 0; c < nc; ++c)
+        std::copy(patches[c].begin(), patches[c].end(), out.patch_idx.begin() + out.patch_ptr[c]);
+
+    // ---- patterns of P (n x nc) and P^T, with positions of every computed entry -------------
+    HostCSR& P = out.P;
+    P.nrows = n;
+    P.ncols = nc;
+    P.ptr.assign(n + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        P.ptr[out.edges[c].d1 + 1]++;
+        P.ptr[out.edges[c].d2 + 1]++;
+        for (int32_t t = out.patch_ptr[c]; t < out.patch_ptr[c + 1]; ++t) P.ptr[out.patch_idx[t] + 1]++;
+    }
+    for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
+    P.idx.assign(P.ptr[n], 0);
+    P.val.assign(P.ptr[n], 0.0);
+    out.patch_pos_P.assign(out.patch_idx.size(), 0);
+    out.ext_pos_P.assign(2 * (size_t)nc, 0);
+    {
+        std::vector<int32_t> cur(P.ptr.begin(), P.ptr.end() - 1);
+        for (int c = 0; c < nc; ++c) {   // columns visited in ascending order: rows stay sorted
+            const auto& e = out.edges[c];
+            int32_t p1 = cur[e.d1]++, p2 = cur[e.d2]++;
+            P.idx[p1] = c; P.val[p1] = e.s1; out.ext_pos_P[2 * c] = p1;
+            P.idx[p2] = c; P.val[p2] = e.s2; out.ext_pos_P[2 * c + 1] = p2;
+            for (int32_t t = out.patch_ptr[c]; t < out.patch_ptr[c + 1]; ++t) {
+                int32_t r = out.patch_idx[t];
+                int32_t pp = cur[r]++;
+                P.idx[pp] = c;
+                out.patch_pos_P[t] = pp;
+            }
+        }
+    }
+    HostCSR& PT = out.PT;
+    PT.nrows = nc;
+    PT.ncols = n;
+    PT.ptr.assign(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) PT.ptr[c + 1] = PT.ptr[c] + 2 + (out.patch_ptr[c + 1] - out.patch_ptr[c]);
+    PT.idx.assign(PT.ptr[nc], 0);
+    PT.val.assign(PT.ptr[nc], 0.0);
+    out.patch_pos_PT.assign(out.patch_idx.size(), 0);
+    out.ext_pos_PT.assign(2 * (size_t)nc, 0);
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
+    for (int c = 0; c < nc; ++c) {
+        const auto& e = out.edges[c];
+        int32_t pos = PT.ptr[c];
+        int32_t a = out.patch_ptr[c], aend = out.patch_ptr[c + 1];
+        int32_t ex[2] = {std::min(e.d1, e.d2), std::max(e.d1, e.d2)};
+        double exv[2] = {(double)(e.d1 < e.d2 ? e.s1 : e.s2), (double)(e.d1 < e.d2 ? e.s2 : e.s1)};
+        int xi = 0;
+        while (a < aend || xi < 2) {
+            if (xi < 2 && (a >= aend || ex[xi] < out.patch_idx[a])) {
+                PT.idx[pos] = ex[xi];
+                PT.val[pos] = exv[xi];
+                out.ext_pos_PT[2 * c + ((ex[xi] == e.d1) ? 0 : 1)] = pos;
+                ++xi;
+            } else {
+                PT.idx[pos] = out.patch_idx[a];
+                out.patch_pos_PT[a] = pos;
+                ++a;
+            }
+            ++pos;
+        }
+    }
+    // ---- symbolic Galerkin patterns ----------------------------------------------------------
+    out.AP = symbolic_rows(A, P, nthreads);
+    out.Ac = symbolic_rows(PT, out.AP, nthreads);
+    return "";
+}
+
+// -------------------------------------------------------------------------------------------
+// OSS-l1 smoother structure: node stars of G, greedy colouring of "an entry of A couples two
+// stars", and the warp slot layout (stars of one colour packed into 32-lane groups).
+// -------------------------------------------------------------------------------------------
+std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
+    HostCSR GT = transpose_pattern(G, false);
+    const int ns = G.ncols;
+    L.nstars = ns;
+    L.star_ptr = GT.ptr;
+    L.star_idx = GT.idx;
+    L.max_block = 0;
+    for (int j = 0; j < ns; ++j) L.max_block = std::max(L.max_block, GT.ptr[j + 1] - GT.ptr[j]);
+    if (L.max_block > 32) return "smoother star of " + std::to_string(L.max_block) + " DoFs exceeds 32";
+    L.colour.assign(ns, -1);
+    std::vector<int32_t> stamp(ns, -1);
+    std::vector<char> taken;
+    int ncol = 0;
+    std::vector<int32_t> nbrs;
+    for (int j = 0; j < ns; ++j) {
+        nbrs.clear();
+        for (int32_t t = GT.ptr[j]; t < GT.ptr[j + 1]; ++t) {
+            int32_t e = GT.idx[t];
+            for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
+                int32_t f = A.idx[q];
+                for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
+                    int32_t jj = G.idx[u];
+                    if (jj != j && stamp[jj] != j) { stamp[jj] = j; nbrs.push_back(jj); }
+                }
+            }
+        }
+        taken.assign(ncol + 1, 0);
+        for (int32_t jj : nbrs)
+            if (L.colour[jj] >= 0) taken[L.colour[jj]] = 1;
+        int c = 0;
+        while (taken[c]) ++c;
+        L.colour[j] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    L.ncolours = ncol;
+    // warp slots
+    L.colour_warp_begin.assign(ncol + 1, 0);
+    L.slot_row.clear(); L.slot_star.clear(); L.slot_base.clear(); L.slot_bsize.clear(); L.slot_pos.clear();
+    int nwarps = 0;
+    for (int c = 0; c < ncol; ++c) {
+        L.colour_warp_begin[c] = nwarps;
+        int lane = 32;   // force a new warp for the first star of the colour
+        for (int j = 0; j < ns; ++j) {
+            if (L.colour[j] != c) continue;
+            int b = GT.ptr[j + 1] - GT.ptr[j];
+            if (b == 0) continue;
+            if (lane + b > 32) {
+                // close the current warp (pad) and open a new one
+                nwarps++;
+                size_t base = (size_t)(nwarps - 1) * 32;
+                L.slot_row.resize(base + 32, -1);
+                L.slot_star.resize(base + 32, -1);
+                L.slot_base.resize(base + 32, 0);
+                L.slot_bsize.resize(base + 32, 0);
+                L.slot_pos.resize(base + 32, 0);
+                lane = 0;
+            }
+            size_t base = (size_t)(nwarps - 1) * 32;
+            for (int q = 0; q < b; ++q) {
+                L.slot_row[base + lane + q] = GT.idx[GT.ptr[j] + q];
+                L.slot_star[base + lane + q] = j;
+                L.slot_base[base + lane + q] = (int8_t)lane;
+                L.slot_bsize[base + lane + q] = (int8_t)b;
+                L.slot_pos[base + lane + q] = (int8_t)q;
+            }
+            lane += b;
+        }
+    }
+    L.colour_warp_begin[ncol] = nwarps;
+    return "";
+}
+
+}  // namespace amgh

@@ -1,0 +1,73 @@
+// Host-side graph steps of the algebraic H(curl) setup (Section 4 of the paper): pure C++,
+// O(nnz) per step, no CUDA.  Integer/pattern work only, apart from the strength test of the
+// nodal C/F splitting, which reads values of G^T A G.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace amgh {
+
+struct HostCSR {
+    int nrows = 0, ncols = 0;
+    std::vector<int32_t> ptr;   // nrows + 1
+    std::vector<int32_t> idx;   // nnz, ascending per row
+    std::vector<double> val;    // nnz (empty for a pure pattern)
+    int64_t nnz() const { return ptr.empty() ? 0 : ptr.back(); }
+};
+
+HostCSR transpose_pattern(const HostCSR& M, bool with_values);
+
+struct CoarseEdge {
+    int32_t d1, s1, d2, s2;   // fine DoFs and their +-1 signs in the row of R
+    int32_t i, k, j;          // coarse end nodes i < j and the middle node k (columns of G~)
+};
+
+struct Coarsening {
+    int m = 0, nB = 0;                   // original columns of G, artificial boundary columns
+    std::vector<int8_t> state;           // per column of G~: 1 = C, 2 = F
+    std::vector<CoarseEdge> edges;       // creation order
+    std::vector<int32_t> coarse_nodes;   // kept columns of R G, ascending
+    HostCSR Gc;                          // n_c x |coarse_nodes|, +-1
+    std::vector<int32_t> patch_ptr, patch_idx;   // sorted patch per coarse edge
+    HostCSR P;                           // pattern of P (n x n_c); val holds the exterior +-1
+    std::vector<int64_t> patch_pos_P;    // position in P.idx of every patch entry
+    HostCSR PT;                          // pattern of P^T (n_c x n)
+    std::vector<int64_t> patch_pos_PT;   // position in PT.idx of every patch entry
+    std::vector<int64_t> ext_pos_P, ext_pos_PT;   // 2 per coarse edge: (d1, c), (d2, c)
+    HostCSR AP;                          // symbolic pattern of A P
+    HostCSR Ac;                          // symbolic pattern of P^T A P
+};
+
+struct Params {
+    double theta = 0.25;
+    int ring = 1;
+    int p_max = 128;
+};
+
+// Validate G (rows with 1 or 2 entries of +-1; two entries of opposite sign).  Returns "" if ok.
+std::string check_gradient(const HostCSR& G);
+std::string check_csr(const HostCSR& M, bool square);
+
+// Alg. 1-3, Eq. sparseP patches, Eq. Gc and the symbolic Galerkin patterns for one level.
+// A must carry values (strength test).  Returns "" or an error message.
+std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
+                          int nthreads);
+
+// Smoother structure (node stars of G and their colouring) -------------------------------------
+struct StarLayout {
+    int nstars = 0, ncolours = 0, max_block = 0;
+    std::vector<int32_t> star_ptr, star_idx;   // star j = rows e with G(e, j) != 0, ascending
+    std::vector<int32_t> colour;               // per star
+    // warp slots: stars of colour c packed, without splitting, into groups of 32 lanes
+    std::vector<int32_t> colour_warp_begin;    // ncolours + 1, in warps
+    std::vector<int32_t> slot_row;             // 32 per warp: DoF row or -1
+    std::vector<int32_t> slot_star;            // 32 per warp: star id or -1
+    std::vector<int8_t> slot_base;             // lane of the star's first row
+    std::vector<int8_t> slot_bsize;            // rows of the star
+    std::vector<int8_t> slot_pos;              // position of the row in the star
+};
+
+std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& out);
+
+}  // namespace amgh

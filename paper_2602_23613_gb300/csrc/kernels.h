@@ -1,0 +1,82 @@
+// Launchers of the device kernels (defined in setup_kernels.cu and solve_kernels.cu).
+#pragma once
+#include "common.cuh"
+
+namespace amgh {
+
+// ---------------- setup numerics (FP64) ----------------------------------------------------
+// Local interior harmonic extension (Eq. sparseP): for coarse edge c with exterior pair
+// (d1, s1), (d2, s2) and sorted patch p, solve A_pp x = -(A_{p,d1} s1 + A_{p,d2} s2) by dense
+// Cholesky and scatter x into P (positions pos_P) and P^T (positions pos_PT).
+void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const int32_t* patch_ptr,
+                        const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
+                        double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s);
+
+// Galerkin product A_c = P^T (A P) on given symbolic patterns (Eq. tl), FP64, deterministic order.
+void launch_ap_numeric(const DevCSR& A, const DevCSR& P, DevCSR& AP, cudaStream_t s);
+void launch_ac_numeric(const DevCSR& PT, const DevCSR& AP, DevCSR& Ac, cudaStream_t s);
+
+// l1 row norms: out[i] = 1 / sum_j |a_ij|
+template <class T>
+void launch_l1inv(const DevCSR& A, T* out, cudaStream_t s);
+
+// SELL copy of a CSR matrix in storage type V (padding: value 0, column = own row or 0)
+template <class V>
+void launch_sell_fill(const DevCSR& M, Sell<V>& S, cudaStream_t s);
+// SELL of the smoother's slot rows (slot_row[w*32 + lane] = DoF or -1)
+template <class V>
+void launch_slot_fill(const DevCSR& A, const int32_t* slot_row, Sell<V>& S, cudaStream_t s);
+
+// Star-block inverses written in the smoother's slot layout (32 x bmax per warp, column-major).
+template <class V>
+void launch_star_inverse(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
+                         const int32_t* star_warp, const int32_t* star_base, int bmax, V* inv,
+                         int* err_flag, cudaStream_t s);
+
+// Dense inverse of the coarsest matrix (Cholesky factor, then inverse of the factor) into inv
+// (n x n, FP64, row-major); work: n*n doubles.
+void launch_coarse_inverse(const DevCSR& A, double* inv, double* work, int* err_flag, cudaStream_t s);
+
+template <class T>
+void launch_convert(const double* in, T* out, int64_t n, cudaStream_t s);
+template <class T>
+void launch_to_double(const T* in, double* out, int64_t n, cudaStream_t s);
+
+// ---------------- solve (V-cycle precision V storage, T vectors) ---------------------------
+enum SellMode { SELL_AX = 0, SELL_RESID = 1, SELL_L1 = 2, SELL_ADD = 3 };
+// MODE AX: y = A x; RESID: y = f - A x; L1: y = x + dinv (f - A x); ADD: y += A x
+template <class V, class T>
+void launch_sell(int mode, const Sell<V>& A, const T* x, const T* f, const T* dinv, T* y,
+                 cudaStream_t s);
+
+template <class V, class T>
+void launch_schwarz_colour(const Smoother<V>& S, int colour, const T* f, T* x, cudaStream_t s);
+
+template <class T>
+void launch_coarse_apply(const T* inv, int n, const T* x, T* y, cudaStream_t s);
+
+// ---------------- outer Krylov vectors (FP64) ------------------------------------------------
+constexpr int RED_BLOCKS = 608;     // 4 x 152 SMs: fixed grid => deterministic reductions
+constexpr int RED_THREADS = 256;
+// q = A p (SELL FP64) and partial sums of p.q
+void launch_spmv_dot(const Sell<double>& A, const double* p, double* q, double* partial, cudaStream_t s);
+// final reduction of RED_BLOCKS partials into scal[slot] (+ op on scalars)
+enum ScalarOp { SC_STORE = 0, SC_ALPHA = 1, SC_BETA_CG = 2, SC_BETA_FCG = 3, SC_RZ = 4 };
+void launch_reduce(const double* partial, int nvals, double* scal, int op, cudaStream_t s);
+// x += alpha p, r -= alpha q (alpha = scal[RZ]/scal[PQ]); r_old = r if r_old; partial r.r
+void launch_cg_update(int64_t n, double* x, double* r, double* r_old, const double* p, const double* q,
+                      const double* scal, double* partial, cudaStream_t s);
+// partial sums of r.z (and z.r_old when r_old != nullptr, stored in the second half)
+void launch_dot2(int64_t n, const double* r, const double* z, const double* r_old, double* partial,
+                 cudaStream_t s);
+// p = z + beta p (beta = scal[BETA])
+void launch_p_update(int64_t n, double* p, const double* z, const double* scal, cudaStream_t s);
+// generic dot partials a.b
+void launch_dot(int64_t n, const double* a, const double* b, double* partial, cudaStream_t s);
+// x += y
+void launch_axpy1(int64_t n, double* x, const double* y, cudaStream_t s);
+
+// indices into the device scalar block of the Krylov loop
+enum Scal { S_RZ = 0, S_PQ = 1, S_RR = 2, S_ALPHA = 3, S_BETA = 4, S_RZ_NEW = 5, S_ZROLD = 6, S_TMP = 7, S_COUNT = 8 };
+
+}  // namespace amgh

@@ -1,0 +1,386 @@
+// Setup numerics on the device (FP64): local harmonic-extension solves (Eq. sparseP), Galerkin
+// product (Eq. tl), star-block and coarsest inverses, l1 row norms, SELL layouts.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace amgh {
+
+namespace {
+
+__device__ __forceinline__ int bsearch_i32(const int32_t* __restrict__ a, int lo, int hi, int key) {
+    // position of key in a[lo, hi) (ascending) or -1
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        int v = a[mid];
+        if (v == key) return mid;
+        if (v < key) lo = mid + 1; else hi = mid;
+    }
+    return -1;
+}
+
+template <class V> __device__ __forceinline__ V from_double(double x);
+template <> __device__ __forceinline__ double from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double x) {
+    return __float2bfloat16_rn((float)x);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One CTA per coarse edge: gather A_pp and the right-hand side -(A_{p,d1} s1 + A_{p,d2} s2) into
+// shared memory, Cholesky-factor A_pp in place (right-looking), two triangular solves, scatter.
+// ---------------------------------------------------------------------------------------------
+__global__ void patch_solve_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                   const double* __restrict__ Aval, int c0, int nc,
+                                   const int32_t* __restrict__ edges4, const int32_t* __restrict__ patch_ptr,
+                                   const int32_t* __restrict__ patch_idx, const int64_t* __restrict__ pos_P,
+                                   const int64_t* __restrict__ pos_PT, double* __restrict__ Pval,
+                                   double* __restrict__ PTval, int max_patch, int* err_flag) {
+    extern __shared__ double smem[];
+    const int c = c0 + blockIdx.x;
+    if (c >= nc) return;
+    const int p0 = patch_ptr[c];
+    const int m = patch_ptr[c + 1] - p0;
+    if (m == 0) return;
+    double* L = smem;                               // m x m, row-major
+    double* y = smem + (size_t)max_patch * max_patch;
+    int* pidx = reinterpret_cast<int*>(y + max_patch);
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) bad = 0;
+    for (int a = tid; a < m; a += nt) pidx[a] = patch_idx[p0 + a];
+    for (int e = tid; e < m * m; e += nt) L[e] = 0.0;
+    __syncthreads();
+    const int d1 = edges4[4 * c], s1 = edges4[4 * c + 1], d2 = edges4[4 * c + 2], s2 = edges4[4 * c + 3];
+    for (int a = tid; a < m; a += nt) {
+        const int g = pidx[a];
+        const int rb = Aptr[g], re = Aptr[g + 1];
+        for (int q = rb; q < re; ++q) {
+            const int b = bsearch_i32(pidx, 0, m, Aidx[q]);
+            if (b >= 0) L[a * m + b] = Aval[q];
+        }
+        const int q1 = bsearch_i32(Aidx, rb, re, d1);
+        const int q2 = bsearch_i32(Aidx, rb, re, d2);
+        double rhs = 0.0;
+        if (q1 >= 0) rhs -= Aval[q1] * (double)s1;
+        if (q2 >= 0) rhs -= Aval[q2] * (double)s2;
+        y[a] = rhs;
+    }
+    // Cholesky (lower) in place
+    for (int k = 0; k < m; ++k) {
+        __syncthreads();
+        if (tid == 0) {
+            double piv = L[k * m + k];
+            if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
+            L[k * m + k] = sqrt(piv);
+        }
+        __syncthreads();
+        const double dkk = L[k * m + k];
+        for (int i = k + 1 + tid; i < m; i += nt) L[i * m + k] /= dkk;
+        __syncthreads();
+        const int w = m - k - 1;
+        for (int e = tid; e < w * w; e += nt) {
+            const int i = k + 1 + e / w, j = k + 1 + e % w;
+            if (j <= i) L[i * m + j] -= L[i * m + k] * L[j * m + k];
+        }
+    }
+    // L z = y
+    for (int k = 0; k < m; ++k) {
+        __syncthreads();
+        if (tid == 0) y[k] /= L[k * m + k];
+        __syncthreads();
+        for (int i = k + 1 + tid; i < m; i += nt) y[i] -= L[i * m + k] * y[k];
+    }
+    // L^T x = z
+    for (int k = m - 1; k >= 0; --k) {
+        __syncthreads();
+        if (tid == 0) y[k] /= L[k * m + k];
+        __syncthreads();
+        for (int i = tid; i < k; i += nt) y[i] -= L[k * m + i] * y[k];
+    }
+    __syncthreads();
+    if (bad && tid == 0) atomicExch(err_flag, 1);
+    for (int a = tid; a < m; a += nt) {
+        Pval[pos_P[p0 + a]] = y[a];
+        PTval[pos_PT[p0 + a]] = y[a];
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Galerkin product: warp per output row, lanes over the row's pattern entries; every entry
+// sums its terms in ascending order (deterministic).
+// ---------------------------------------------------------------------------------------------
+__global__ void ap_kernel(int n, const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                          const double* __restrict__ Aval, const int32_t* __restrict__ Pptr,
+                          const int32_t* __restrict__ Pidx, const double* __restrict__ Pval,
+                          const int32_t* __restrict__ Optr, const int32_t* __restrict__ Oidx,
+                          double* __restrict__ Oval) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int ob = Optr[warp], oe = Optr[warp + 1];
+    const int ab = Aptr[warp], ae = Aptr[warp + 1];
+    for (int o = ob + lane; o < oe; o += 32) {
+        const int J = Oidx[o];
+        double s = 0.0;
+        for (int q = ab; q < ae; ++q) {
+            const int j = Aidx[q];
+            const int t = bsearch_i32(Pidx, Pptr[j], Pptr[j + 1], J);
+            if (t >= 0) s += Aval[q] * Pval[t];
+        }
+        Oval[o] = s;
+    }
+}
+
+__global__ void l1inv_kernel_d(int n, const int32_t* __restrict__ ptr, const double* __restrict__ val,
+                               double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int q = ptr[i]; q < ptr[i + 1]; ++q) s += fabs(val[q]);
+    out[i] = 1.0 / s;
+}
+
+template <class T>
+__global__ void convert_kernel(const double* __restrict__ in, T* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = from_double<T>(in[i]);
+}
+template <>
+__global__ void convert_kernel<double>(const double* __restrict__ in, double* __restrict__ out, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i];
+}
+
+template <class V>
+__global__ void sell_fill_kernel(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                 const double* __restrict__ val, int nslices, const int64_t* __restrict__ sptr,
+                                 int32_t* __restrict__ scol, V* __restrict__ sval) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = row >> 5, lane = row & 31;
+    if (slice >= nslices) return;
+    const int64_t st = sptr[slice];
+    const int w = (int)((sptr[slice + 1] - st) >> 5);
+    int b = 0, len = 0;
+    if (row < n) { b = ptr[row]; len = ptr[row + 1] - b; }
+    // padding repeats the row's last column (a valid, nearby column; value 0)
+    const int pad_col = len > 0 ? idx[b + len - 1] : 0;
+    for (int t = 0; t < w; ++t) {
+        const int64_t o = st + 32 * (int64_t)t + lane;
+        if (t < len) { scol[o] = idx[b + t]; sval[o] = from_double<V>(val[b + t]); }
+        else { scol[o] = pad_col; sval[o] = from_double<V>(0.0); }
+    }
+}
+
+template <class V>
+__global__ void slot_fill_kernel(int nwarps, const int32_t* __restrict__ slot_row, const int32_t* __restrict__ ptr,
+                                 const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                 const int64_t* __restrict__ sptr, int32_t* __restrict__ scol, V* __restrict__ sval) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = slot >> 5, lane = slot & 31;
+    if (w >= nwarps) return;
+    const int row = slot_row[slot];
+    const int64_t st = sptr[w];
+    const int width = (int)((sptr[w + 1] - st) >> 5);
+    int b = 0, len = 0;
+    if (row >= 0) { b = ptr[row]; len = ptr[row + 1] - b; }
+    for (int t = 0; t < width; ++t) {
+        const int64_t o = st + 32 * (int64_t)t + lane;
+        if (t < len) { scol[o] = idx[b + t]; sval[o] = from_double<V>(val[b + t]); }
+        else { scol[o] = row >= 0 ? row : 0; sval[o] = from_double<V>(0.0); }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Star-block inverses: one warp per star, Gauss-Jordan on the SPD block (no pivoting needed),
+// rows of the inverse written to the star's slots (column-major within the warp group).
+// ---------------------------------------------------------------------------------------------
+template <class V>
+__global__ void star_inverse_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                    const double* __restrict__ Aval, int nstars, const int32_t* __restrict__ star_ptr,
+                                    const int32_t* __restrict__ star_idx, const int32_t* __restrict__ star_warp,
+                                    const int32_t* __restrict__ star_base, int bmax, V* __restrict__ inv,
+                                    int* err_flag) {
+    __shared__ double sm[2][2][32 * 33];
+    __shared__ double fac[2][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 2 + wl;
+    if (j >= nstars) return;
+    const int b0 = star_ptr[j], b = star_ptr[j + 1] - b0;
+    double* M = sm[wl][0];
+    double* I = sm[wl][1];
+    // gather: lane r handles row r of the block
+    for (int r = 0; r < b; ++r) { if (lane < b) { M[r * 33 + lane] = 0.0; I[r * 33 + lane] = (r == lane); } }
+    __syncwarp();
+    if (lane < b) {
+        const int g = star_idx[b0 + lane];
+        for (int q = Aptr[g]; q < Aptr[g + 1]; ++q) {
+            const int c = bsearch_i32(star_idx, b0, b0 + b, Aidx[q]);
+            if (c >= 0) M[lane * 33 + (c - b0)] = Aval[q];
+        }
+    }
+    __syncwarp();
+    bool bad = false;
+    for (int k = 0; k < b; ++k) {
+        double piv = M[k * 33 + k];
+        if (!(piv > 0.0)) { bad = true; piv = 1.0; }
+        __syncwarp();
+        if (lane < b) { M[k * 33 + lane] /= piv; I[k * 33 + lane] /= piv; }
+        if (lane < b) fac[wl][lane] = M[lane * 33 + k];
+        __syncwarp();
+        if (lane < b) {
+            // after the division row k holds M[k][k] = 1 (fac[k] was read after division)
+            for (int i = 0; i < b; ++i) {
+                if (i == k) continue;
+                const double f = fac[wl][i];
+                M[i * 33 + lane] -= f * M[k * 33 + lane];
+                I[i * 33 + lane] -= f * I[k * 33 + lane];
+            }
+        }
+        __syncwarp();
+    }
+    if (bad && lane == 0) atomicExch(err_flag, 1);
+    const int w = star_warp[j], base = star_base[j];
+    // slot (base + r) row r of the inverse: inv[w*32*bmax + k*32 + base + r] = I[r][k]
+    if (lane < b) {
+        const int r = lane;
+        for (int k = 0; k < b; ++k)
+            inv[(int64_t)w * 32 * bmax + k * 32 + base + r] = from_double<V>(I[r * 33 + k]);
+    }
+}
+
+// Dense inverse of the coarsest matrix, one CTA: gather, Gauss-Jordan (SPD, no pivoting).
+__global__ void coarse_inverse_kernel(int n, const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                      const double* __restrict__ Aval, double* __restrict__ inv,
+                                      double* __restrict__ M, int* err_flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double piv_s;
+    for (int e = tid; e < n * n; e += nt) { M[e] = 0.0; inv[e] = (e / n == e % n) ? 1.0 : 0.0; }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt)
+        for (int q = Aptr[r]; q < Aptr[r + 1]; ++q) M[(int64_t)r * n + Aidx[q]] = Aval[q];
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        if (tid == 0) {
+            double p = M[(int64_t)k * n + k];
+            if (!(p > 0.0)) { atomicExch(err_flag, 1); p = 1.0; }
+            piv_s = p;
+        }
+        __syncthreads();
+        const double p = piv_s;
+        for (int j = tid; j < n; j += nt) { M[(int64_t)k * n + j] /= p; inv[(int64_t)k * n + j] /= p; }
+        __syncthreads();
+        for (int e = tid; e < n * n; e += nt) {
+            const int i = e / n, j = e % n;
+            if (i == k) continue;
+            const double f = M[(int64_t)i * n + k];
+            // column k of M is read by every j of row i: update column k last (j == k handled below)
+            if (j != k) {
+                M[(int64_t)i * n + j] -= f * M[(int64_t)k * n + j];
+            }
+            inv[(int64_t)i * n + j] -= f * inv[(int64_t)k * n + j];
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += nt)
+            if (i != k) M[(int64_t)i * n + k] = 0.0;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const int32_t* patch_ptr,
+                        const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
+                        double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s) {
+    if (nc == 0 || max_patch == 0) return;
+    const size_t shm = (size_t)max_patch * max_patch * 8 + (size_t)max_patch * 8 + (size_t)max_patch * 4;
+    static_assert(sizeof(int) == 4, "int");
+    AMGH_CUDA(cudaFuncSetAttribute(patch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    const int chunk = 65535;
+    for (int c0 = 0; c0 < nc; c0 += chunk) {
+        const int cnt = std::min(chunk, nc - c0);
+        patch_solve_kernel<<<cnt, 128, shm, s>>>(A.ptr.p, A.idx.p, A.val.p, c0, nc, edges4, patch_ptr, patch_idx,
+                                                 pos_P, pos_PT, Pval, PTval, max_patch, err_flag);
+        AMGH_LAUNCHED();
+    }
+}
+
+void launch_ap_numeric(const DevCSR& A, const DevCSR& P, DevCSR& AP, cudaStream_t s) {
+    const int n = AP.nrows;
+    if (n == 0) return;
+    const int threads = 256, warps_per_block = threads / 32;
+    ap_kernel<<<(n + warps_per_block - 1) / warps_per_block, threads, 0, s>>>(
+        n, A.ptr.p, A.idx.p, A.val.p, P.ptr.p, P.idx.p, P.val.p, AP.ptr.p, AP.idx.p, AP.val.p);
+    AMGH_LAUNCHED();
+}
+
+void launch_ac_numeric(const DevCSR& PT, const DevCSR& AP, DevCSR& Ac, cudaStream_t s) {
+    // same kernel shape: row I of Ac = sum_i PT(I, i) AP(i, :)
+    launch_ap_numeric(PT, AP, Ac, s);
+}
+
+template <class T>
+void launch_l1inv(const DevCSR& A, T* out, cudaStream_t s) {
+    if (A.nrows == 0) return;
+    DevArray<double> tmp;
+    double* dst = nullptr;
+    if constexpr (std::is_same<T, double>::value) dst = out;
+    else { tmp.alloc(A.nrows); dst = tmp.p; }
+    l1inv_kernel_d<<<(A.nrows + 255) / 256, 256, 0, s>>>(A.nrows, A.ptr.p, A.val.p, dst);
+    AMGH_LAUNCHED();
+    if constexpr (!std::is_same<T, double>::value) {
+        launch_convert<T>(dst, out, A.nrows, s);
+        AMGH_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+template <class V>
+void launch_sell_fill(const DevCSR& M, Sell<V>& S, cudaStream_t s) {
+    if (S.nslices == 0) return;
+    sell_fill_kernel<V><<<S.nslices, 32, 0, s>>>(M.nrows, M.ptr.p, M.idx.p, M.val.p, S.nslices, S.slice_ptr.p,
+                                                 S.col.p, S.val.p);
+    AMGH_LAUNCHED();
+}
+
+template <class V>
+void launch_slot_fill(const DevCSR& A, const int32_t* slot_row, Sell<V>& S, cudaStream_t s) {
+    if (S.nslices == 0) return;
+    slot_fill_kernel<V><<<S.nslices, 32, 0, s>>>(S.nslices, slot_row, A.ptr.p, A.idx.p, A.val.p, S.slice_ptr.p,
+                                                 S.col.p, S.val.p);
+    AMGH_LAUNCHED();
+}
+
+template <class V>
+void launch_star_inverse(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
+                         const int32_t* star_warp, const int32_t* star_base, int bmax, V* inv, int* err_flag,
+                         cudaStream_t s) {
+    if (nstars == 0) return;
+    star_inverse_kernel<V><<<(nstars + 1) / 2, 64, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, nstars, star_ptr, star_idx,
+                                                            star_warp, star_base, bmax, inv, err_flag);
+    AMGH_LAUNCHED();
+}
+
+void launch_coarse_inverse(const DevCSR& A, double* inv, double* work, int* err_flag, cudaStream_t s) {
+    coarse_inverse_kernel<<<1, 1024, 0, s>>>(A.nrows, A.ptr.p, A.idx.p, A.val.p, inv, work, err_flag);
+    AMGH_LAUNCHED();
+}
+
+template <class T>
+void launch_convert(const double* in, T* out, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    convert_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+    AMGH_LAUNCHED();
+}
+
+#define INST_V(V)                                                                                     \
+    template void launch_sell_fill<V>(const DevCSR&, Sell<V>&, cudaStream_t);                         \
+    template void launch_slot_fill<V>(const DevCSR&, const int32_t*, Sell<V>&, cudaStream_t);         \
+    template void launch_star_inverse<V>(const DevCSR&, int, const int32_t*, const int32_t*,          \
+                                         const int32_t*, const int32_t*, int, V*, int*, cudaStream_t); \
+    template void launch_convert<V>(const double*, V*, int64_t, cudaStream_t);
+INST_V(double)
+INST_V(float)
+INST_V(__nv_bfloat16)
+template void launch_l1inv<double>(const DevCSR&, double*, cudaStream_t);
+template void launch_l1inv<float>(const DevCSR&, float*, cudaStream_t);
+
+}  // namespace amgh

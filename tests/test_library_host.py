@@ -1,0 +1,116 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, validates inputs, and
+its host graph steps (Alg. 1-3, patches, smoother stars/colours, symbolic Galerkin pattern)
+reproduce the oracle's structure bit for bit.  No GPU call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import amg as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def amgh():
+    from paper_2602_23613_gb300 import build, amgh as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def test_exports_every_declared_symbol(amgh):
+    header = open(os.path.join(ROOT, "include", "amgh.h")).read()
+    declared = set(re.findall(r"^\s*(?:amgh_status|void|int64_t|const char\*)\s+(amgh_\w+)\s*\(", header, re.M))
+    assert len(declared) >= 14
+    lib = ctypes.CDLL(amgh.lib_path())
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared <= set(amgh.EXPORTS)
+
+
+def _oracle_structure(p):
+    cz = O.coarsen(p["A"], p["G"])
+    state = np.full(cz["Gt"].shape[1], 2, np.int8)
+    state[cz["cG"]] = 1
+    state[cz["B"]] = 1
+    edges = np.array([list(e) for e in cz["edges"]], np.int64)
+    pptr = np.concatenate([[0], np.cumsum([len(x) for x in cz["patches"]])])
+    return cz, state, edges, pptr
+
+
+@pytest.mark.parametrize("maker", [lambda: W.hex_problem(8, 1.0, 1.0),
+                                   lambda: W.hex_problem(10, W.fields.log_uniform(10, 3), 0.1),
+                                   lambda: W.make_config("hex16_checker"),
+                                   lambda: W.tri_problem(16, 1.0, 0.01),
+                                   lambda: W.quad_problem(10, 1.0, 0.01)])
+def test_host_structure_matches_oracle(amgh, maker):
+    p = maker()
+    h = amgh.amgh_setup_host_structure(p["A"], p["G"])
+    s = amgh.amgh_level_structure(h, 0)
+    cz, state, edges, pptr = _oracle_structure(p)
+    np.testing.assert_array_equal(s["cf_state"], state)
+    np.testing.assert_array_equal(s["edges"].astype(np.int64), edges)
+    np.testing.assert_array_equal(s["coarse_nodes"], cz["coarse_nodes"])
+    np.testing.assert_array_equal(s["patch_ptr"], pptr)
+    np.testing.assert_array_equal(s["patch_idx"], np.concatenate(cz["patches"]))
+    np.testing.assert_array_equal(s["colour"], O.colour_stars(p["A"], p["G"]))
+    P = amgh.amgh_level_matrix(h, 0, 1)
+    np.testing.assert_array_equal(P.indptr, cz["P"].indptr)
+    np.testing.assert_array_equal(P.indices, cz["P"].indices)
+    # the exterior rows of P are R^T exactly (Eq. sparseP)
+    ext = np.zeros(p["ndof"], bool)
+    ext[edges[:, 0]] = ext[edges[:, 2]] = True
+    np.testing.assert_array_equal(P[ext].toarray(), cz["P"][ext].toarray())
+    Ac = amgh.amgh_level_matrix(h, 0, 3)
+    Aco = O.galerkin(p["A"], cz["P"])
+    np.testing.assert_array_equal(Ac.indptr, Aco.indptr)
+    np.testing.assert_array_equal(Ac.indices, Aco.indices)
+    Gc = cz["Gc"]
+    np.testing.assert_array_equal(np.diff(Gc.indptr) >= 1, True)
+
+
+@pytest.mark.slow
+def test_host_structure_matches_oracle_32(amgh):
+    test_host_structure_matches_oracle(amgh, lambda: W.make_config("hex32_checker"))
+
+
+def test_input_validation(amgh):
+    p = W.hex_problem(4, 1.0, 1.0)
+    G = p["G"].tolil()
+    G[0, 0] = 2.0
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_setup_host_structure(p["A"], G.tocsr())
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+    G = p["G"].tolil()
+    r = G.rows[5]
+    G[5, r[0]] = G[5, r[1]] if len(r) > 1 else G[5, r[0]]
+    if len(r) > 1:
+        with pytest.raises(amgh.AmghError):
+            amgh.amgh_setup_host_structure(p["A"], G.tocsr())
+    A = p["A"][:, :-1]
+    with pytest.raises(amgh.AmghError):
+        amgh.amgh_setup_host_structure(A, p["G"])
+    # unsorted columns are rejected
+    A = p["A"].copy()
+    A.has_sorted_indices = True
+    i0 = A.indptr[3]
+    A.indices[i0], A.indices[i0 + 1] = A.indices[i0 + 1], A.indices[i0]
+    from paper_2602_23613_gb300.amgh import _csr, amgh_csr
+    keep = []
+    ca = amgh_csr()
+    rp = np.ascontiguousarray(A.indptr, np.int32)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    va = np.ascontiguousarray(A.data, np.float64)
+    ca.nrows = ca.ncols = A.shape[0]
+    ca.nnz = A.nnz
+    ca.row_ptr, ca.col, ca.val, ca.on_device = rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0
+    cg = _csr(p["G"], keep)
+    out = ctypes.c_void_p()
+    st = amgh.load().amgh_setup_host_structure(ctypes.byref(ca), ctypes.byref(cg), None, ctypes.byref(out))
+    assert st == amgh.AMGH_ERR_INVALID_ARG
+    assert "ascending" in amgh.amgh_last_error()
