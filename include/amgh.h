@@ -116,7 +116,8 @@ amgh_status amgh_setup_host_structure(const amgh_csr* A, const amgh_csr* G, cons
 amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z);
 
 /* Preconditioned conjugate gradients (Section 5) on the finest A with the V-cycle as the
- * preconditioner: stops when ||f - A x_k||_2 (as updated by the recurrence) <= tol ||f - A x_0||_2
+ * preconditioner.  The loop runs on the device inside one CUDA graph (conditional WHILE node);
+ * while kernel timing is enabled (amgh_profile) it is driven from the host instead.  Stops when ||f - A x_k||_2 (as updated by the recurrence) <= tol ||f - A x_0||_2
  * or after maxit iterations.  x holds x_0 on entry and the solution on return; f and x are n
  * doubles, host or device (same kind).  With an FP32/BF16 hierarchy the outer loop is flexible
  * CG (beta = <z_k+1, r_k+1 - r_k> / <z_k, r_k>) with FP64 vectors, SpMV and dots.  iters and
@@ -124,6 +125,16 @@ amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z);
  * Returns NOT_CONVERGED (with x, iters, relres filled) when maxit is reached. */
 amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit,
                            int* iters, double* relres);
+
+/* Solve nsys independent systems at once.  hs[i] comes from amgh_setup (any sizes and
+ * precisions, same GPU); f[i] and x[i] are device pointers of n_i doubles (x[i] holds x0 on entry,
+ * the solution on return).  All systems are enqueued as independent branches of one CUDA graph
+ * whose branches each run their PCG loop on the device (a conditional WHILE node per system that
+ * stops at tol or maxit), and the graph is launched once on hs[0]'s stream; no host round trip
+ * happens until every system has stopped.  iters and relres (may be NULL) receive nsys entries.
+ * Returns NOT_CONVERGED if any system reached maxit.  Section 5's solver per system. */
+amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* const* f, double* const* x,
+                                 double tol, int maxit, int* iters, double* relres);
 
 /* Stand-alone V-cycle iteration x <- x + B (f - A x) (Section 5, "AMG" counts), same stopping
  * rule and argument conventions as amgh_pcg_solve, on the true residual. */

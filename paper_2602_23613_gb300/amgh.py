@@ -40,7 +40,8 @@ class amgh_hier_info(ctypes.Structure):
 
 
 _LIB = None
-EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve", "amgh_amg_solve", "amgh_info",
+EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve",
+           "amgh_batch_pcg_solve", "amgh_amg_solve", "amgh_info",
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
            "amgh_launch_count", "amgh_last_error", "amgh_destroy"]
 
@@ -66,6 +67,8 @@ def load():
     L.amgh_vcycle.argtypes = [P, P, P]
     L.amgh_pcg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_amg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_batch_pcg_solve.argtypes = [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), D, I,
+                                       ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_info.argtypes = [P, ctypes.POINTER(amgh_hier_info)]
     L.amgh_level_structure.argtypes = [P, I] + [ctypes.POINTER(I64)] * 5 + [P] * 6
     L.amgh_level_matrix.argtypes = [P, I, I] + [ctypes.POINTER(I64)] * 3 + [P, P, P]
@@ -207,6 +210,21 @@ def _solve(fn, h, f, x, tol, maxit):
 def amgh_pcg_solve(h, f, x, tol=1e-8, maxit=500):
     """PCG with the V-cycle; x holds x0 on entry.  Returns (iterations, relres, converged)."""
     return _solve(load().amgh_pcg_solve, h, f, x, tol, maxit)
+
+
+def amgh_batch_pcg_solve(hs, fs, xs, tol=1e-8, maxit=500):
+    """All systems in one graph launch (CUDA tensors).  Returns (iterations, relres, converged) lists."""
+    n = len(hs)
+    P = ctypes.c_void_p
+    ha = (P * n)(*[h.ptr for h in hs])
+    fa = (P * n)(*[f.data_ptr() for f in fs])
+    xa = (P * n)(*[x.data_ptr() for x in xs])
+    it = (ctypes.c_int * n)()
+    rel = (ctypes.c_double * n)()
+    st = load().amgh_batch_pcg_solve(n, ha, fa, xa, tol, maxit, it, rel)
+    if st not in (AMGH_OK, AMGH_ERR_NOT_CONVERGED):
+        _check(st, hs[0].ptr)
+    return list(it), list(rel), st == AMGH_OK
 
 
 def amgh_amg_solve(h, f, x, tol=1e-8, maxit=500):

@@ -182,6 +182,8 @@ struct Engine : EngineBase {
         return cnt;
     }
 
+    int64_t enqueue(cudaStream_t s) override { return core(s); }
+
     int64_t vcycle(cudaStream_t s) override {
         const bool want_prof = prof && prof->enabled;
         if (!gexec || want_prof != prof_in_graph || (want_prof && prof_gen != prof->gen)) capture(s);
@@ -300,6 +302,23 @@ struct amgh_ctx {
     Sell<double> A0;   // outer FP64 SpMV
     int64_t nnzA0 = 0;
     DevArray<double> kp, kq, kro, partial, scal, stage_f, stage_x;
+    DevArray<int> iter;
+    // device-resident solve graph (rebuilt when its pointers or parameters change)
+    cudaGraph_t sgraph = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    const double* s_f = nullptr;
+    double* s_x = nullptr;
+    double s_tol = -1.0;
+    int s_maxit = -1;
+    int64_t s_pro_launches = 0, s_body_launches = 0;
+    void drop_solve_graph() {
+        if (sexec) cudaGraphExecDestroy(sexec);
+        if (sgraph) cudaGraphDestroy(sgraph);
+        sexec = nullptr;
+        sgraph = nullptr;
+        s_f = nullptr;
+        s_x = nullptr;
+    }
     double* hscal = nullptr;
     DevArray<int> errflag;
     Profiler prof;
@@ -309,7 +328,9 @@ struct amgh_ctx {
     std::vector<int> max_patch;
     bool own_stream = false;
     bool structure_only = false;
+    bool host_loop = false;   // force the host-driven Krylov loop
     ~amgh_ctx() {
+        drop_solve_graph();
         eng.reset();
         if (hscal) cudaFreeHost(hscal);
         if (own_stream && s) cudaStreamDestroy(s);
@@ -610,6 +631,8 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     h->partial.alloc(2 * RED_BLOCKS);
     h->scal.alloc(S_COUNT);
     h->scal.zero(s);
+    h->iter.alloc(1);
+    h->iter.zero(s);
     AMGH_CUDA(cudaMallocHost(&h->hscal, sizeof(double) * S_COUNT));
     h->eng->capture(s);
     AMGH_CUDA(cudaStreamSynchronize(s));
@@ -746,6 +769,134 @@ static amgh_status pcg_impl(amgh_ctx* h, const double* f_in, double* x_in, doubl
     if (relres) *relres = rel;
     if (status != AMGH_OK) h->err = "PCG reached maxit before the tolerance";
     return status;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device-resident PCG: the whole solve is one branch of a CUDA graph.  The branch holds a
+// prologue (r = f - A x, r0, the first iteration) and a WHILE node whose body runs one more
+// iteration (z = B r, beta, p, q = A p, alpha, x and r, the stopping test that sets the node's
+// condition).  No host round trip happens until the graph has finished.
+// ---------------------------------------------------------------------------------------------
+static void add_solve_branch(amgh_ctx* h, cudaGraph_t G, cudaStream_t cs, const double* f, double* x, double tol,
+                             int maxit) {
+    const int64_t n = h->hl[0].A.nrows;
+    const bool flexible = h->prm.precision != AMGH_F64;
+    double* r = h->eng->in64();
+    double* z = h->eng->out64();
+    double* p = h->kp.p;
+    double* q = h->kq.p;
+    double* ro = flexible ? h->kro.p : nullptr;
+    cudaGraphConditionalHandle hw;
+    AMGH_CUDA(cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault));
+    // event nodes are not allowed inside conditional bodies: the branch is never timed
+    struct ProfOff {
+        Profiler& p;
+        bool was;
+        ProfOff(Profiler& q) : p(q), was(q.enabled) { p.enabled = false; }
+        ~ProfOff() { p.enabled = was; }
+    } prof_off(h->prof);
+    const int64_t before = launch_counter().load();
+    AMGH_CUDA(cudaStreamBeginCaptureToGraph(cs, G, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    std::vector<cudaGraphNode_t> deps;
+    int64_t pro = 0, body = 0;
+    try {
+        launch_sell<double, double>(SELL_RESID, h->A0, x, f, nullptr, r, cs);
+        launch_dot(n, r, r, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, cs);
+        launch_pcg_start(h->scal.p, h->iter.p, cs);
+        pro += 4 + h->eng->enqueue(cs);
+        launch_dot2(n, r, z, nullptr, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_RZ, cs);
+        AMGH_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, cs));
+        launch_spmv_dot(h->A0, p, q, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_ALPHA, cs);
+        launch_cg_update(n, x, r, ro, p, q, h->scal.p, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, cs);
+        launch_pcg_check(hw, h->scal.p, h->iter.p, tol, maxit, cs);
+        pro += 7;
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* d = nullptr;
+        size_t nd = 0;
+        AMGH_CUDA(cudaStreamGetCaptureInfo(cs, &st, nullptr, nullptr, &d, nullptr, &nd));
+        deps.assign(d, d + nd);
+    } catch (...) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(cs, &g);
+        launch_counter().store(before);
+        throw;
+    }
+    cudaGraph_t g_out;
+    AMGH_CUDA(cudaStreamEndCapture(cs, &g_out));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hw;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    AMGH_CUDA(cudaGraphAddNode(&wnode, G, deps.data(), nullptr, deps.size(), &cp));
+    cudaGraph_t bg = cp.conditional.phGraph_out[0];
+    AMGH_CUDA(cudaStreamBeginCaptureToGraph(cs, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        body += h->eng->enqueue(cs);
+        launch_dot2(n, r, z, ro, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, flexible ? SC_BETA_FCG : SC_BETA_CG, cs);
+        launch_p_update(n, p, z, h->scal.p, cs);
+        launch_spmv_dot(h->A0, p, q, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_ALPHA, cs);
+        launch_cg_update(n, x, r, ro, p, q, h->scal.p, h->partial.p, cs);
+        launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, cs);
+        launch_pcg_check(hw, h->scal.p, h->iter.p, tol, maxit, cs);
+        body += 8;
+    } catch (...) {
+        cudaGraph_t g;
+        cudaStreamEndCapture(cs, &g);
+        launch_counter().store(before);
+        throw;
+    }
+    AMGH_CUDA(cudaStreamEndCapture(cs, &bg));
+    launch_counter().store(before);
+    h->s_pro_launches = pro;
+    h->s_body_launches = body;
+}
+
+// read back (iterations, relres) of a finished device-resident solve
+static void read_solve_result(amgh_ctx* h, int* it, double* rel) {
+    int k = 0;
+    AMGH_CUDA(cudaMemcpyAsync(&k, h->iter.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaMemcpyAsync(h->hscal, h->scal.p, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+    *it = k;
+    *rel = h->hscal[S_REL];
+    h->launches += h->s_pro_launches + (int64_t)std::max(0, k - 1) * h->s_body_launches;
+    launch_counter().fetch_add(h->s_pro_launches + (int64_t)std::max(0, k - 1) * h->s_body_launches);
+}
+
+static amgh_status pcg_device_impl(amgh_ctx* h, const double* f_in, double* x_in, double tol, int maxit, int* iters,
+                                   double* relres) {
+    Staged st = stage_in(h, f_in, x_in, true);
+    if (!h->sexec || h->s_f != st.f || h->s_x != st.x || h->s_tol != tol || h->s_maxit != maxit) {
+        h->drop_solve_graph();
+        AMGH_CUDA(cudaGraphCreate(&h->sgraph, 0));
+        add_solve_branch(h, h->sgraph, h->s, st.f, st.x, tol, maxit);
+        AMGH_CUDA(cudaGraphInstantiate(&h->sexec, h->sgraph, 0));
+        h->s_f = st.f;
+        h->s_x = st.x;
+        h->s_tol = tol;
+        h->s_maxit = maxit;
+    }
+    AMGH_CUDA(cudaGraphLaunch(h->sexec, h->s));
+    int it = 0;
+    double rel = 0.0;
+    read_solve_result(h, &it, &rel);
+    stage_out(h, st, x_in);
+    if (!(rel == rel)) throw StatusError{AMGH_ERR_NOT_CONVERGED, "residual became NaN"};
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (rel > tol) {
+        h->err = "PCG reached maxit before the tolerance";
+        return AMGH_ERR_NOT_CONVERGED;
+    }
+    return AMGH_OK;
 }
 
 static amgh_status amg_impl(amgh_ctx* h, const double* f_in, double* x_in, double tol, int maxit, int* iters,
@@ -908,7 +1059,51 @@ amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z) {
 amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
                            double* relres) {
     if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
-    return guarded(h, [&] { return pcg_impl(h, f, x, tol, maxit, iters, relres); });
+    return guarded(h, [&] {
+        if (maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
+        // kernel timing needs the host-driven loop (event nodes cannot sit in conditional bodies)
+        if (h->prof.enabled || maxit < 1 || h->host_loop) return pcg_impl(h, f, x, tol, maxit, iters, relres);
+        return pcg_device_impl(h, f, x, tol, maxit, iters, relres);
+    });
+}
+
+amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* const* f, double* const* x,
+                                 double tol, int maxit, int* iters, double* relres) {
+    if (nsys < 1 || !hs || !f || !x) return AMGH_ERR_INVALID_ARG;
+    for (int i = 0; i < nsys; ++i)
+        if (!hs[i] || hs[i]->structure_only || !f[i] || !x[i]) return AMGH_ERR_INVALID_ARG;
+    amgh_ctx* h0 = hs[0];
+    cudaGraph_t G = nullptr;
+    cudaGraphExec_t GE = nullptr;
+    amgh_status st = guarded(h0, [&] {
+        if (maxit < 1 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
+        for (int i = 0; i < nsys; ++i)
+            if (!is_device_ptr(f[i]) || !is_device_ptr(x[i]))
+                throw StatusError{AMGH_ERR_INVALID_ARG, "batched solves take device pointers"};
+        AMGH_CUDA(cudaStreamSynchronize(h0->s));
+        AMGH_CUDA(cudaGraphCreate(&G, 0));
+        for (int i = 0; i < nsys; ++i) {
+            if (i > 0) AMGH_CUDA(cudaStreamSynchronize(hs[i]->s));
+            add_solve_branch(hs[i], G, h0->s, f[i], x[i], tol, maxit);   // independent branches
+        }
+        AMGH_CUDA(cudaGraphInstantiate(&GE, G, 0));
+        AMGH_CUDA(cudaGraphLaunch(GE, h0->s));
+        AMGH_CUDA(cudaStreamSynchronize(h0->s));
+        amgh_status all = AMGH_OK;
+        for (int i = 0; i < nsys; ++i) {
+            int it = 0;
+            double rel = 0.0;
+            read_solve_result(hs[i], &it, &rel);
+            if (iters) iters[i] = it;
+            if (relres) relres[i] = rel;
+            if (!(rel <= tol)) all = AMGH_ERR_NOT_CONVERGED;
+        }
+        if (all != AMGH_OK) h0->err = "a system of the batch reached maxit before the tolerance";
+        return all;
+    });
+    if (GE) cudaGraphExecDestroy(GE);
+    if (G) cudaGraphDestroy(G);
+    return st;
 }
 
 amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,

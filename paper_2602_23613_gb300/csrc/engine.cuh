@@ -62,6 +62,8 @@ class EngineBase {
     virtual double* out64() = 0;
     // out64 = B in64, enqueued on s (asynchronous); returns the number of kernels launched
     virtual int64_t vcycle(cudaStream_t s) = 0;
+    // enqueue the V-cycle's kernels on s (used while capturing a larger graph); returns launches
+    virtual int64_t enqueue(cudaStream_t s) = 0;
     // single V-cycle steps on level l (test entry), FP64 device pointers
     virtual void level_apply(int l, int op, const double* f, const double* x, double* y, cudaStream_t s) = 0;
     virtual void capture(cudaStream_t s) = 0;

@@ -77,6 +77,14 @@ void launch_dot(int64_t n, const double* a, const double* b, double* partial, cu
 void launch_axpy1(int64_t n, double* x, const double* y, cudaStream_t s);
 
 // indices into the device scalar block of the Krylov loop
-enum Scal { S_RZ = 0, S_PQ = 1, S_RR = 2, S_ALPHA = 3, S_BETA = 4, S_RZ_NEW = 5, S_ZROLD = 6, S_TMP = 7, S_COUNT = 8 };
+enum Scal { S_RZ = 0, S_PQ = 1, S_RR = 2, S_ALPHA = 3, S_BETA = 4, S_RZ_NEW = 5, S_ZROLD = 6, S_TMP = 7,
+            S_R0 = 8, S_REL = 9, S_COUNT = 10 };
+
+// device-resident stopping test: iteration count += 1, rel = sqrt(scal[S_TMP]) / scal[S_R0],
+// keep looping (WHILE handle = 1) while rel > tol and count < maxit
+void launch_pcg_check(cudaGraphConditionalHandle hw, double* scal, int* iter, double tol, int maxit,
+                      cudaStream_t s);
+// scal[S_R0] = sqrt(scal[S_TMP]); iteration count = 0
+void launch_pcg_start(double* scal, int* iter, cudaStream_t s);
 
 }  // namespace amgh

@@ -133,7 +133,7 @@ __global__ void reduce_kernel(const double* __restrict__ partial, int nvals, dou
     if (threadIdx.x != 0) return;
     const double v = sh[0][0], v2 = sh[1][0];
     switch (op) {
-        case SC_ALPHA:   scal[S_PQ] = v; scal[S_ALPHA] = scal[S_RZ] / v; break;
+        case SC_ALPHA:   scal[S_PQ] = v; scal[S_ALPHA] = v != 0.0 ? scal[S_RZ] / v : 0.0; break;
         case SC_BETA_CG: scal[S_RZ_NEW] = v; scal[S_BETA] = v / scal[S_RZ]; scal[S_RZ] = v; break;
         case SC_BETA_FCG: scal[S_RZ_NEW] = v; scal[S_ZROLD] = v2; scal[S_BETA] = (v - v2) / scal[S_RZ]; scal[S_RZ] = v; break;
         case SC_RZ:      scal[S_RZ] = v; break;
@@ -180,6 +180,22 @@ __global__ void p_update_kernel(int64_t n, double* __restrict__ p, const double*
     const double beta = scal[S_BETA];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void pcg_check_kernel(cudaGraphConditionalHandle hw, double* __restrict__ scal, int* __restrict__ iter,
+                                 double tol, int maxit) {
+    const int k = ++iter[0];
+    const double r0 = scal[S_R0];
+    const double rel = r0 > 0.0 ? sqrt(scal[S_TMP]) / r0 : 0.0;
+    scal[S_REL] = rel;
+    const bool go = (rel > tol) && (k < maxit);   // a NaN residual stops the loop
+    cudaGraphSetConditional(hw, go ? 1u : 0u);
+}
+
+__global__ void pcg_start_kernel(double* __restrict__ scal, int* __restrict__ iter) {
+    scal[S_R0] = sqrt(scal[S_TMP]);
+    scal[S_REL] = 1.0;
+    iter[0] = 0;
 }
 
 template <class T>
@@ -260,6 +276,16 @@ void launch_p_update(int64_t n, double* p, const double* z, const double* scal, 
 
 void launch_axpy1(int64_t n, double* x, const double* y, cudaStream_t s) {
     axpy1_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(n, x, y);
+    AMGH_LAUNCHED();
+}
+
+void launch_pcg_check(cudaGraphConditionalHandle hw, double* scal, int* iter, double tol, int maxit, cudaStream_t s) {
+    pcg_check_kernel<<<1, 1, 0, s>>>(hw, scal, iter, tol, maxit);
+    AMGH_LAUNCHED();
+}
+
+void launch_pcg_start(double* scal, int* iter, cudaStream_t s) {
+    pcg_start_kernel<<<1, 1, 0, s>>>(scal, iter);
     AMGH_LAUNCHED();
 }
 
