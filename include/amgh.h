@@ -136,6 +136,25 @@ amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol
 amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* const* f, double* const* x,
                                  double tol, int maxit, int* iters, double* relres);
 
+/* PCG exactly as amgh_pcg_solve, but allocating nothing: its Krylov buffers (search direction,
+ * A times it, previous residual, partial sums, scalars) live in one fixed device array that the
+ * library defines at file scope (6.3 MB on every GPU that loads the library, kept until the
+ * process exits), the loop is driven from the host and the V-cycle kernels are launched one by
+ * one, so no memory, graph or staging buffer is created.  It is meant for callers that cannot
+ * allocate device memory when they solve: code running while a stream capture in global mode is
+ * active (cudaMalloc is refused there), applications whose caching allocator has reserved nearly
+ * all device memory, and latency-bound loops that cannot afford the device-wide synchronisation
+ * of cudaMalloc/cudaFree.  The paper has no counterpart; it is a deployment variant.
+ *  - f and x must be device pointers of the handle's device, which must be current; n <= 262144
+ *    rows, larger systems are rejected with INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ *    that first call before any stream capture begins.
+ *  - All calls share the array: calls whose work overlaps on the GPU (other host threads, other
+ *    handles on other streams) race and must be serialised by the caller.
+ * Returns as amgh_pcg_solve. */
+amgh_status amgh_pcg_solve_noalloc(amgh_handle h, const double* f, double* x, double tol, int maxit,
+                                   int* iters, double* relres);
+
 /* Stand-alone V-cycle iteration x <- x + B (f - A x) (Section 5, "AMG" counts), same stopping
  * rule and argument conventions as amgh_pcg_solve, on the true residual. */
 amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit,

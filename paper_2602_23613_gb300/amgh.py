@@ -41,7 +41,7 @@ class amgh_hier_info(ctypes.Structure):
 
 _LIB = None
 EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve",
-           "amgh_batch_pcg_solve", "amgh_amg_solve", "amgh_info",
+           "amgh_batch_pcg_solve", "amgh_pcg_solve_noalloc", "amgh_amg_solve", "amgh_info",
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
            "amgh_launch_count", "amgh_last_error", "amgh_destroy"]
 
@@ -67,6 +67,7 @@ def load():
     L.amgh_vcycle.argtypes = [P, P, P]
     L.amgh_pcg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_amg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_pcg_solve_noalloc.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_batch_pcg_solve.argtypes = [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), D, I,
                                        ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_info.argtypes = [P, ctypes.POINTER(amgh_hier_info)]
@@ -225,6 +226,12 @@ def amgh_batch_pcg_solve(hs, fs, xs, tol=1e-8, maxit=500):
     if st not in (AMGH_OK, AMGH_ERR_NOT_CONVERGED):
         _check(st, hs[0].ptr)
     return list(it), list(rel), st == AMGH_OK
+
+
+def amgh_pcg_solve_noalloc(h, f, x, tol=1e-8, maxit=500):
+    """PCG that allocates nothing (Krylov buffers in the library's fixed device array); CUDA
+    tensors only, at most 262144 rows.  Returns (iterations, relres, converged)."""
+    return _solve(load().amgh_pcg_solve_noalloc, h, f, x, tol, maxit)
 
 
 def amgh_amg_solve(h, f, x, tol=1e-8, maxit=500):

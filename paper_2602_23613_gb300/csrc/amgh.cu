@@ -13,6 +13,7 @@
 #endif
 
 #include "engine.cuh"
+#include "krylov_scratch.h"
 
 namespace amgh {
 
@@ -938,6 +939,75 @@ static amgh_status amg_impl(amgh_ctx* h, const double* f_in, double* x_in, doubl
 
 }  // namespace amgh
 
+namespace amgh {
+
+// Host-driven PCG whose Krylov buffers come from the caller (see krylov_scratch.h).  It mirrors
+// pcg_impl step for step; the V-cycle is enqueued kernel by kernel, so nothing is instantiated.
+static amgh_status pcg_scratch_impl(amgh_ctx* h, const double* f, double* x, double tol, int maxit, int* iters,
+                                    double* relres, const KrylovScratch& ks, int64_t max_rows) {
+    if (maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
+    const int64_t n = h->hl[0].A.nrows;
+    if (n > max_rows)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "system has " + std::to_string(n) +
+                                                    " rows; the allocation-free solve takes at most " +
+                                                    std::to_string(max_rows)};
+    if (!is_device_ptr(f) || !is_device_ptr(x))
+        throw StatusError{AMGH_ERR_INVALID_ARG, "the allocation-free solve takes device pointers only"};
+    struct ProfOff {
+        Profiler& p;
+        bool was;
+        ProfOff(Profiler& q) : p(q), was(q.enabled) { p.enabled = false; }
+        ~ProfOff() { p.enabled = was; }
+    } prof_off(h->prof);
+    cudaStream_t s = h->s;
+    const bool flexible = h->prm.precision != AMGH_F64;
+    double* r = h->eng->in64();
+    double* z = h->eng->out64();
+    double hs[S_COUNT];
+    auto read = [&](int slot) {
+        AMGH_CUDA(cudaMemcpyAsync(hs, ks.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return hs[slot];
+    };
+    AMGH_CUDA(cudaMemsetAsync(ks.scal, 0, sizeof(double) * S_COUNT, s));   // shared scalars start at zero
+    launch_sell<double, double>(SELL_RESID, h->A0, x, f, nullptr, r, s);
+    launch_dot(n, r, r, ks.partial, s);
+    launch_reduce(ks.partial, RED_BLOCKS, ks.scal, SC_STORE, s);
+    const double r0 = std::sqrt(read(S_TMP));
+    int it = 0;
+    double rel = 0.0;
+    amgh_status status = AMGH_OK;
+    if (r0 > 0.0) {
+        h->eng->enqueue(s);
+        launch_dot2(n, r, z, nullptr, ks.partial, s);
+        launch_reduce(ks.partial, RED_BLOCKS, ks.scal, SC_RZ, s);
+        AMGH_CUDA(cudaMemcpyAsync(ks.p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        rel = 1.0;
+        bool conv = false;
+        for (it = 1; it <= maxit; ++it) {
+            launch_spmv_dot(h->A0, ks.p, ks.q, ks.partial, s);
+            launch_reduce(ks.partial, RED_BLOCKS, ks.scal, SC_ALPHA, s);
+            launch_cg_update(n, x, r, flexible ? ks.r_old : nullptr, ks.p, ks.q, ks.scal, ks.partial, s);
+            launch_reduce(ks.partial, RED_BLOCKS, ks.scal, SC_STORE, s);
+            rel = std::sqrt(read(S_TMP)) / r0;
+            if (!(rel == rel)) throw StatusError{AMGH_ERR_NOT_CONVERGED, "residual became NaN"};
+            if (rel <= tol) { conv = true; break; }
+            h->eng->enqueue(s);
+            launch_dot2(n, r, z, flexible ? ks.r_old : nullptr, ks.partial, s);
+            launch_reduce(ks.partial, RED_BLOCKS, ks.scal, flexible ? SC_BETA_FCG : SC_BETA_CG, s);
+            launch_p_update(n, ks.p, z, ks.scal, s);
+        }
+        if (!conv) { it = maxit; status = AMGH_ERR_NOT_CONVERGED; }
+    }
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    if (status != AMGH_OK) h->err = "PCG reached maxit before the tolerance";
+    return status;
+}
+
+}  // namespace amgh
+
 // =============================================================================================
 // C-ABI
 // =============================================================================================
@@ -1250,3 +1320,13 @@ void amgh_destroy(amgh_handle h) {
 }
 
 }  // extern "C"
+
+namespace amgh {
+
+amgh_status pcg_with_scratch(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
+                             double* relres, const KrylovScratch& ks, int64_t max_rows) {
+    if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] { return pcg_scratch_impl(h, f, x, tol, maxit, iters, relres, ks, max_rows); });
+}
+
+}  // namespace amgh
