@@ -265,7 +265,9 @@ def run_gpu(args, rank, world, local_rank):
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "n_dofs": n, "nnz": int(A.nnz),
                    "precision": args.precision, "tol": 1e-8,
                    "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
-                   "levels": info["n"], "op_complexity": round(info["op_complexity"], 4)},
+                   "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
+                   "level_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["precision"]],
+                   "smoother_lanes": info["lanes"], "smoother_fused": info["fused"]},
         "pcg_iters": last["iters"], "relres": last["relres"], "converged": last["ok"],
         "solve_ms": 1000 * statistics.mean(r["solve_s"] for r in res),
         "setup_host_ms": info["setup_host_ms"], "setup_device_ms": info["setup_device_ms"],

@@ -73,7 +73,10 @@ enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1 };
 typedef struct {
     int max_levels;       /* at most this many levels, finest included (Section 5: 20)          */
     int coarse_size;      /* stop coarsening once a level has <= coarse_size DoFs (Sec. 5: 32)  */
-    int precision;        /* AMGH_F64 | AMGH_F32 | AMGH_BF16                                    */
+    int precision;        /* AMGH_F64 | AMGH_F32 | AMGH_BF16: requested V-cycle storage; a level
+                             keeps FP64 unless kappa * u <= 1/4 for the largest 1-norm condition
+                             estimate kappa of its smoother blocks and the unit roundoff u of the
+                             reduced format (BF16 falls back to FP32 first)                     */
     int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED                            */
     int ring;             /* rings of interior A-neighbours in a truncated patch (>= 1)        */
     int p_max;            /* largest patch of one local harmonic extension (<= 256)            */
@@ -171,7 +174,12 @@ typedef struct {
     double op_complexity; /* sum nnz(A_l) / nnz(A_0)                                           */
     double grid_complexity; /* sum n_l / n_0                                                    */
     double setup_host_ms; /* host graph steps (Alg. 1-3, patterns, colouring)                 */
-    double setup_device_ms; /* device numerics (patch solves, Galerkin product, inverses)       */
+    double setup_device_ms; /* device numerics (patch solves, Galerkin product, inverses, tuning) */
+    int precision[32];    /* storage precision each level ended up with (AMGH_F64/F32/BF16)   */
+    int lanes[32];        /* lanes per row of the level's smoother layout (autotuned)          */
+    int fused[32];        /* 1 if the level's whole Schwarz sweep runs as one launch           */
+    double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
+                               (coarsest level: of its matrix)                                  */
 } amgh_hier_info;
 
 /* Hierarchy statistics (levels, sizes, complexities as defined in Section 5, setup time split). */

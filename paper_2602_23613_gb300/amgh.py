@@ -36,7 +36,8 @@ class amgh_hier_info(ctypes.Structure):
                 ("nnz_p", ctypes.c_int64 * 32), ("ncolours", ctypes.c_int * 32), ("max_block", ctypes.c_int * 32),
                 ("max_patch", ctypes.c_int * 32), ("op_complexity", ctypes.c_double),
                 ("grid_complexity", ctypes.c_double), ("setup_host_ms", ctypes.c_double),
-                ("setup_device_ms", ctypes.c_double)]
+                ("setup_device_ms", ctypes.c_double), ("precision", ctypes.c_int * 32),
+                ("lanes", ctypes.c_int * 32), ("fused", ctypes.c_int * 32), ("block_kappa", ctypes.c_double * 32)]
 
 
 _LIB = None
@@ -247,7 +248,8 @@ def amgh_info(h):
                 ncolours=list(info.ncolours[:L]), max_block=list(info.max_block[:L]),
                 max_patch=list(info.max_patch[:L]), op_complexity=info.op_complexity,
                 grid_complexity=info.grid_complexity, setup_host_ms=info.setup_host_ms,
-                setup_device_ms=info.setup_device_ms)
+                setup_device_ms=info.setup_device_ms, precision=list(info.precision[:L]),
+                lanes=list(info.lanes[:L]), fused=list(info.fused[:L]), block_kappa=list(info.block_kappa[:L]))
 
 
 def amgh_level_structure(h, l):

@@ -12,8 +12,14 @@
 #include <omp.h>
 #endif
 
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <variant>
+
 #include "engine.cuh"
 #include "krylov_scratch.h"
+#include "vcycle_kernels.h"
 
 namespace amgh {
 
@@ -69,13 +75,37 @@ static void build_sell(const HostCSR& pat, const DevCSR& dev, Sell<V>& S, cudaSt
     launch_sell_fill<V>(dev, S, s);
 }
 
+// ---------------------------------------------------------------------------------------------
+// V-cycle engine: every level carries its own storage precision (FP64, or FP32 / BF16 with FP32
+// vectors) and its own layouts, chosen at setup by the precision policy and the autotuner.
+// ---------------------------------------------------------------------------------------------
 template <class V, class T>
+struct LevelX {
+    using VT = V;
+    using TT = T;
+    int n = 0;
+    SellL<V> A, P, PT;
+    SmootherL<V> sm;
+    DevArray<T> l1inv, f, x, y, r;
+    int64_t nnzA = 0, nnzP = 0;
+    std::vector<int64_t> col_nnz, col_inv, col_rows;   // per colour, for the algorithmic bytes
+};
+using LevelVar = std::variant<LevelX<double, double>, LevelX<float, float>, LevelX<__nv_bfloat16, float>>;
+
+struct LevelChoice {
+    int prec = AMGH_F64;
+    int L_A = 1, L_P = 1, L_PT = 1, L_sm = 1;
+    bool fused = false;
+    double kappa = 0.0;
+};
+
 struct Engine : EngineBase {
-    std::vector<LevelDev<V, T>> L;
-    std::vector<int> ncol;
+    std::vector<LevelVar> L;
+    std::vector<LevelChoice> choice;
     int nlev = 0, nL = 0;
-    DevArray<T> cinv;
-    DevArray<double> io_in, io_out;   // FP64 staging when T != double
+    DevArray<double> cinv_d;
+    DevArray<float> cinv_f;
+    DevArray<double> io_in, io_out;   // FP64 staging when level 0 stores float vectors
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool prof_in_graph = false;
@@ -84,13 +114,12 @@ struct Engine : EngineBase {
 
     ~Engine() override { release_graph(); }
 
+    bool level0_double() const { return std::holds_alternative<LevelX<double, double>>(L[0]); }
     double* in64() override {
-        if constexpr (std::is_same<T, double>::value) return L[0].f.p;
-        else return io_in.p;
+        return level0_double() ? std::get<LevelX<double, double>>(L[0]).f.p : io_in.p;
     }
     double* out64() override {
-        if constexpr (std::is_same<T, double>::value) return L[0].x.p;
-        else return io_out.p;
+        return level0_double() ? std::get<LevelX<double, double>>(L[0]).x.p : io_out.p;
     }
 
     template <class F>
@@ -114,70 +143,111 @@ struct Engine : EngineBase {
         return seq;
     }
 
-    // bytes one pass over a SELL matrix must move: values + column indices of the stored
-    // (non-padding) entries, plus row pointers (4 B per row), plus the vectors it reads and writes
-    double bytes_sell(const Sell<V>& A, int64_t nnz, int vec_rw) const {
-        return (double)nnz * (sizeof(V) + 4) + 4.0 * A.nrows + (double)vec_rw * sizeof(T) * A.nrows;
+    template <class Lv>
+    double bytes_pass(const Lv& d, int64_t nnz, int64_t rows, int vecs) const {
+        using V = typename Lv::VT;
+        using T = typename Lv::TT;
+        return (double)nnz * (sizeof(V) + 4) + 4.0 * rows + (double)vecs * sizeof(T) * rows;
+    }
+    template <class Lv>
+    double bytes_colour(const Lv& d, int c) const {
+        using V = typename Lv::VT;
+        using T = typename Lv::TT;
+        return (double)d.col_nnz[c] * (sizeof(V) + 4) + (double)d.col_inv[c] * sizeof(V) +
+               3.0 * sizeof(T) * d.col_rows[c];
     }
 
-    std::vector<int64_t> nnzA, nnzP, sm_nnz, sm_inv;   // per level: algorithmic counts
-
-    void smooth_pre(int l, cudaStream_t s, int64_t& cnt) {
-        auto& d = L[l];
-        for (int c : colour_sequence(ncol[l])) {
-            const double by = (double)sm_nnz_col[l][c] * (sizeof(V) + 4) + (double)sm_inv_col[l][c] * sizeof(V) +
-                              3.0 * sizeof(T) * sm_rows_col[l][c];
-            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_colour<V, T>(d.sm, c, d.f.p, d.x.p, s); });
+    template <class Lv>
+    void sweep(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
+        using V = typename Lv::VT;
+        using T = typename Lv::TT;
+        if (d.sm.fused) {
+            double by = 0;
+            for (int c : colour_sequence(d.sm.ncolours)) by += bytes_colour(d, c);
+            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_fused<V, T>(d.sm, d.f.p, d.x.p, s); });
             cnt++;
+            return;
         }
-        timed(K_L1, l, bytes_sell(d.A, nnzA[l], 4), s,
-              [&] { launch_sell<V, T>(SELL_L1, d.A, d.x.p, d.f.p, d.l1inv.p, d.y.p, s); });
-        cnt++;
-    }
-    void smooth_post(int l, cudaStream_t s, int64_t& cnt) {
-        auto& d = L[l];
-        timed(K_L1, l, bytes_sell(d.A, nnzA[l], 4), s,
-              [&] { launch_sell<V, T>(SELL_L1, d.A, d.y.p, d.f.p, d.l1inv.p, d.x.p, s); });
-        cnt++;
-        for (int c : colour_sequence(ncol[l])) {
-            const double by = (double)sm_nnz_col[l][c] * (sizeof(V) + 4) + (double)sm_inv_col[l][c] * sizeof(V) +
-                              3.0 * sizeof(T) * sm_rows_col[l][c];
-            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_colour<V, T>(d.sm, c, d.f.p, d.x.p, s); });
+        for (int c : colour_sequence(d.sm.ncolours)) {
+            timed(K_SCHWARZ, l, bytes_colour(d, c), s, [&] { launch_schwarz_colourL<V, T>(d.sm, c, d.f.p, d.x.p, s); });
             cnt++;
         }
     }
-    std::vector<std::vector<int64_t>> sm_nnz_col, sm_inv_col, sm_rows_col;
+    template <class Lv>
+    void smooth_pre(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
+        using V = typename Lv::VT;
+        using T = typename Lv::TT;
+        sweep(d, l, s, cnt);
+        timed(K_L1, l, bytes_pass(d, d.nnzA, d.n, 4), s,
+              [&] { launch_sellL<V, T, T>(SM_L1, d.A, d.x.p, d.f.p, d.l1inv.p, d.y.p, s); });
+        cnt++;
+    }
+    template <class Lv>
+    void smooth_post(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
+        using V = typename Lv::VT;
+        using T = typename Lv::TT;
+        timed(K_L1, l, bytes_pass(d, d.nnzA, d.n, 4), s,
+              [&] { launch_sellL<V, T, T>(SM_L1, d.A, d.y.p, d.f.p, d.l1inv.p, d.x.p, s); });
+        cnt++;
+        sweep(d, l, s, cnt);
+    }
 
     int64_t core(cudaStream_t s) {
         int64_t cnt = 0;
-        if constexpr (!std::is_same<T, double>::value) {
-            launch_convert<T>(io_in.p, L[0].f.p, L[0].n, s);
+        if (!level0_double()) {
+            launch_convert<float>(io_in.p, std::get_if<LevelX<float, float>>(&L[0])
+                                               ? std::get<LevelX<float, float>>(L[0]).f.p
+                                               : std::get<LevelX<__nv_bfloat16, float>>(L[0]).f.p,
+                                  std::visit([](auto& d) { return (int64_t)d.n; }, L[0]), s);
             cnt++;
         }
         for (int l = 0; l + 1 < nlev; ++l) {
-            auto& d = L[l];
-            d.x.zero(s);
-            smooth_pre(l, s, cnt);
-            // after the pre-step the iterate lives in y
-            timed(K_RESID, l, bytes_sell(d.A, nnzA[l], 3), s,
-                  [&] { launch_sell<V, T>(SELL_RESID, d.A, d.y.p, d.f.p, nullptr, d.r.p, s); });
-            cnt++;
-            timed(K_RESTRICT, l, bytes_sell(d.PT, nnzP[l], 0) + sizeof(T) * (double)(d.n + L[l + 1].n), s,
-                  [&] { launch_sell<V, T>(SELL_AX, d.PT, d.r.p, nullptr, nullptr, L[l + 1].f.p, s); });
-            cnt++;
+            std::visit([&](auto& d) {
+                using V = typename std::decay_t<decltype(d)>::VT;
+                using T = typename std::decay_t<decltype(d)>::TT;
+                d.x.zero(s);
+                smooth_pre(d, l, s, cnt);
+                timed(K_RESID, l, bytes_pass(d, d.nnzA, d.n, 3), s,
+                      [&] { launch_sellL<V, T, T>(SM_RESID, d.A, d.y.p, d.f.p, (const T*)nullptr, d.r.p, s); });
+                cnt++;
+            }, L[l]);
+            std::visit([&](auto& a, auto& b) {
+                using V = typename std::decay_t<decltype(a)>::VT;
+                using Ta = typename std::decay_t<decltype(a)>::TT;
+                using Tb = typename std::decay_t<decltype(b)>::TT;
+                const double by = bytes_pass(a, a.nnzP, b.n, 0) + sizeof(Ta) * (double)a.n + sizeof(Tb) * (double)b.n;
+                timed(K_RESTRICT, l, by, s, [&] {
+                    launch_sellL<V, Ta, Tb>(SM_AX, a.PT, a.r.p, (const Tb*)nullptr, (const Tb*)nullptr, b.f.p, s);
+                });
+                cnt++;
+            }, L[l], L[l + 1]);
         }
-        timed(K_COARSE, nlev - 1, (double)nL * nL * sizeof(T), s,
-              [&] { launch_coarse_apply<T>(cinv.p, nL, L[nlev - 1].f.p, L[nlev - 1].x.p, s); });
-        cnt++;
+        std::visit([&](auto& d) {
+            using T = typename std::decay_t<decltype(d)>::TT;
+            const T* ci;
+            if constexpr (std::is_same<T, double>::value) ci = cinv_d.p;
+            else ci = cinv_f.p;
+            timed(K_COARSE, nlev - 1, (double)nL * nL * sizeof(T), s,
+                  [&] { launch_coarse_apply<T>(ci, nL, d.f.p, d.x.p, s); });
+            cnt++;
+        }, L[nlev - 1]);
         for (int l = nlev - 2; l >= 0; --l) {
-            auto& d = L[l];
-            timed(K_PROLONG, l, bytes_sell(d.P, nnzP[l], 2) + sizeof(T) * (double)L[l + 1].n, s,
-                  [&] { launch_sell<V, T>(SELL_ADD, d.P, L[l + 1].x.p, nullptr, nullptr, d.y.p, s); });
-            cnt++;
-            smooth_post(l, s, cnt);
+            std::visit([&](auto& a, auto& b) {
+                using V = typename std::decay_t<decltype(a)>::VT;
+                using Ta = typename std::decay_t<decltype(a)>::TT;
+                using Tb = typename std::decay_t<decltype(b)>::TT;
+                const double by = bytes_pass(a, a.nnzP, a.n, 2) + sizeof(Tb) * (double)b.n;
+                timed(K_PROLONG, l, by, s, [&] {
+                    launch_sellL<V, Tb, Ta>(SM_ADD, a.P, b.x.p, (const Ta*)nullptr, (const Ta*)nullptr, a.y.p, s);
+                });
+                cnt++;
+            }, L[l], L[l + 1]);
+            std::visit([&](auto& d) { smooth_post(d, l, s, cnt); }, L[l]);
         }
-        if constexpr (!std::is_same<T, double>::value) {
-            launch_to_double<T>(L[0].x.p, io_out.p, L[0].n, s);
+        if (!level0_double()) {
+            const float* x0 = std::get_if<LevelX<float, float>>(&L[0]) ? std::get<LevelX<float, float>>(L[0]).x.p
+                                                                     : std::get<LevelX<__nv_bfloat16, float>>(L[0]).x.p;
+            launch_to_double<float>(x0, io_out.p, std::visit([](auto& d) { return (int64_t)d.n; }, L[0]), s);
             cnt++;
         }
         return cnt;
@@ -208,6 +278,7 @@ struct Engine : EngineBase {
             cudaStreamEndCapture(s, &g);
             if (g) cudaGraphDestroy(g);
             if (prof) prof->capturing = false;
+            launch_counter().store(before);
             throw;
         }
         AMGH_CUDA(cudaStreamEndCapture(s, &graph));
@@ -228,65 +299,71 @@ struct Engine : EngineBase {
         if (op == 6) l = nlev - 1;
         if (l < 0 || l >= nlev || (op != 6 && l == nlev - 1))
             throw StatusError{AMGH_ERR_INVALID_ARG, "level out of range for this operation"};
-        auto& d = L[l];
-        const int n = d.n;
-        auto to_T = [&](const double* src, T* dst, int64_t cnt) { launch_convert<T>(src, dst, cnt, s); };
-        auto from_T = [&](const T* src, double* dst, int64_t cnt) { launch_to_double<T>(src, dst, cnt, s); };
-        switch (op) {
-            case 0:
-            case 1:
-                to_T(x, d.x.p, n);
-                if (op == 1) to_T(f, d.f.p, n);
-                launch_sell<V, T>(op == 0 ? SELL_AX : SELL_RESID, d.A, d.x.p, d.f.p, nullptr, d.r.p, s);
-                from_T(d.r.p, y, n);
-                break;
-            case 2: {   // pre-step from iterate x: result in y
-                int64_t c = 0;
-                to_T(x, d.x.p, n);
-                to_T(f, d.f.p, n);
-                smooth_pre(l, s, c);
-                from_T(d.y.p, y, n);
-                break;
-            }
-            case 3: {   // post-step from iterate x
-                int64_t c = 0;
-                to_T(x, d.y.p, n);
-                to_T(f, d.f.p, n);
-                smooth_post(l, s, c);
-                from_T(d.x.p, y, n);
-                break;
-            }
-            case 4: {
-                auto& c = L[l + 1];
-                to_T(x, d.r.p, n);
-                launch_sell<V, T>(SELL_AX, d.PT, d.r.p, nullptr, nullptr, c.f.p, s);
-                from_T(c.f.p, y, c.n);
-                break;
-            }
-            case 5: {
-                auto& c = L[l + 1];
-                to_T(x, c.x.p, c.n);
-                to_T(y, d.y.p, n);
-                launch_sell<V, T>(SELL_ADD, d.P, c.x.p, nullptr, nullptr, d.y.p, s);
-                from_T(d.y.p, y, n);
-                break;
-            }
-            case 6:
-                to_T(x, d.f.p, n);
-                launch_coarse_apply<T>(cinv.p, nL, d.f.p, d.x.p, s);
-                from_T(d.x.p, y, n);
-                break;
-            default:
-                throw StatusError{AMGH_ERR_INVALID_ARG, "unknown level operation"};
+        auto in = [&](const double* src, auto* dst, int64_t cnt) {
+            using T = std::remove_pointer_t<decltype(dst)>;
+            launch_convert<T>(src, dst, cnt, s);
+        };
+        auto out = [&](const auto* src, double* dst, int64_t cnt) {
+            using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
+            launch_to_double<T>(src, dst, cnt, s);
+        };
+        if (op == 4 || op == 5) {
+            std::visit([&](auto& a, auto& b) {
+                using V = typename std::decay_t<decltype(a)>::VT;
+                using Ta = typename std::decay_t<decltype(a)>::TT;
+                using Tb = typename std::decay_t<decltype(b)>::TT;
+                if (op == 4) {
+                    in(x, a.r.p, a.n);
+                    launch_sellL<V, Ta, Tb>(SM_AX, a.PT, a.r.p, (const Tb*)nullptr, (const Tb*)nullptr, b.f.p, s);
+                    out(b.f.p, y, b.n);
+                } else {
+                    in(x, b.x.p, b.n);
+                    in(y, a.y.p, a.n);
+                    launch_sellL<V, Tb, Ta>(SM_ADD, a.P, b.x.p, (const Ta*)nullptr, (const Ta*)nullptr, a.y.p, s);
+                    out(a.y.p, y, a.n);
+                }
+            }, L[l], L[l + 1]);
+            return;
         }
+        std::visit([&](auto& d) {
+            using V = typename std::decay_t<decltype(d)>::VT;
+            using T = typename std::decay_t<decltype(d)>::TT;
+            int64_t c = 0;
+            switch (op) {
+                case 0:
+                case 1:
+                    in(x, d.x.p, d.n);
+                    if (op == 1) in(f, d.f.p, d.n);
+                    launch_sellL<V, T, T>(op == 0 ? SM_AX : SM_RESID, d.A, d.x.p, d.f.p, (const T*)nullptr, d.r.p, s);
+                    out(d.r.p, y, d.n);
+                    break;
+                case 2:
+                    in(x, d.x.p, d.n);
+                    in(f, d.f.p, d.n);
+                    smooth_pre(d, l, s, c);
+                    out(d.y.p, y, d.n);
+                    break;
+                case 3:
+                    in(x, d.y.p, d.n);
+                    in(f, d.f.p, d.n);
+                    smooth_post(d, l, s, c);
+                    out(d.x.p, y, d.n);
+                    break;
+                case 6: {
+                    const T* ci;
+                    if constexpr (std::is_same<T, double>::value) ci = cinv_d.p;
+                    else ci = cinv_f.p;
+                    in(x, d.f.p, d.n);
+                    launch_coarse_apply<T>(ci, nL, d.f.p, d.x.p, s);
+                    out(d.x.p, y, d.n);
+                    break;
+                }
+                default:
+                    throw StatusError{AMGH_ERR_INVALID_ARG, "unknown level operation"};
+            }
+        }, L[l]);
     }
 };
-
-std::unique_ptr<EngineBase> new_engine(int precision) {
-    if (precision == AMGH_F64) return std::unique_ptr<EngineBase>(new Engine<double, double>());
-    if (precision == AMGH_F32) return std::unique_ptr<EngineBase>(new Engine<float, float>());
-    return std::unique_ptr<EngineBase>(new Engine<__nv_bfloat16, float>());
-}
 
 }  // namespace amgh
 
@@ -342,93 +419,373 @@ static thread_local std::string g_setup_error;
 
 namespace amgh {
 
+// ---------------------------------------------------------------------------------------------
+// Engine construction: precision policy, layouts and the autotuner
+// ---------------------------------------------------------------------------------------------
+
+// Pack the stars of every colour, without splitting a star, into chunks of 256/L row slots.
+static StarPacking pack_stars(const StarLayout& st, int L) {
+    StarPacking pk;
+    pk.L = L;
+    pk.slots = CTA_THREADS / L;
+    pk.colour_cta_begin.assign(st.ncolours + 1, 0);
+    pk.star_cta.assign(st.nstars, 0);
+    pk.star_base.assign(st.nstars, 0);
+    int nctas = 0;
+    for (int c = 0; c < st.ncolours; ++c) {
+        pk.colour_cta_begin[c] = nctas;
+        int used = pk.slots;   // forces a new chunk for the colour's first star
+        for (int j = 0; j < st.nstars; ++j) {
+            if (st.colour[j] != c) continue;
+            const int b = st.star_ptr[j + 1] - st.star_ptr[j];
+            if (b == 0) continue;
+            if (used + b > pk.slots) {
+                nctas++;
+                const size_t base = (size_t)(nctas - 1) * pk.slots;
+                pk.slot_row.resize(base + pk.slots, -1);
+                pk.slot_star.resize(base + pk.slots, -1);
+                pk.slot_base.resize(base + pk.slots, 0);
+                pk.slot_bsize.resize(base + pk.slots, 0);
+                used = 0;
+            }
+            const size_t base = (size_t)(nctas - 1) * pk.slots;
+            for (int q = 0; q < b; ++q) {
+                pk.slot_row[base + used + q] = st.star_idx[st.star_ptr[j] + q];
+                pk.slot_star[base + used + q] = j;
+                pk.slot_base[base + used + q] = (int16_t)used;
+                pk.slot_bsize[base + used + q] = (int8_t)b;
+            }
+            pk.star_cta[j] = nctas - 1;
+            pk.star_base[j] = used;
+            used += b;
+        }
+    }
+    pk.colour_cta_begin[st.ncolours] = nctas;
+    pk.nctas = nctas;
+    return pk;
+}
+
+// slice pointers of a SELL-L layout: rows[q] for q < count (or 0..nrows-1 when rows is null)
+static std::vector<int64_t> sellL_slices(const HostCSR& M, const std::vector<int32_t>* rows, int L) {
+    const int64_t count = rows ? (int64_t)rows->size() : M.nrows;
+    const int R = 32 / L;
+    const int64_t ns = (count + R - 1) / R;
+    std::vector<int64_t> sp(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) {
+        int w = 0;
+        for (int64_t q = R * s; q < std::min<int64_t>(count, R * s + R); ++q) {
+            const int r = rows ? (*rows)[q] : (int)q;
+            if (r >= 0) w = std::max(w, (M.ptr[r + 1] - M.ptr[r] + L - 1) / L);
+        }
+        sp[s + 1] = sp[s] + 32 * (int64_t)w;
+    }
+    return sp;
+}
+
+template <class V>
+static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& S, cudaStream_t s) {
+    auto sp = sellL_slices(pat, nullptr, L);
+    S.L = L;
+    S.nrows = pat.nrows;
+    S.nslices = (int)(sp.size() - 1);
+    S.stored = sp.back();
+    S.slice_ptr.upload(sp, s);
+    S.col.alloc(S.stored);
+    S.val.alloc(S.stored);
+    launch_sellL_fill<V>(dev, S, s);
+}
+
+template <class V>
+static void build_smoother(amgh_ctx* h, int l, int L, bool fused, SmootherL<V>& sm, std::vector<int64_t>* cn,
+                           std::vector<int64_t>* ci, std::vector<int64_t>* cr) {
+    cudaStream_t s = h->s;
+    const LevelHost& hl = h->hl[l];
+    const StarLayout& st = hl.stars;
+    StarPacking pk = pack_stars(st, L);
+    sm.L = L;
+    sm.slots = pk.slots;
+    sm.nctas = pk.nctas;
+    sm.bmax = std::max(1, st.max_block);
+    sm.ncolours = st.ncolours;
+    sm.fused = fused;
+    sm.colour_cta_begin = pk.colour_cta_begin;
+    sm.colour_cta_begin_d.upload(pk.colour_cta_begin, s);
+    std::vector<int32_t> seq;
+    for (int c = 0; c < st.ncolours; ++c) seq.push_back(c);
+    for (int c = st.ncolours - 2; c >= 0; --c) seq.push_back(c);
+    sm.sweep_d.upload(seq, s);
+    sm.slot_row.upload(pk.slot_row, s);
+    sm.slot_base.upload(pk.slot_base, s);
+    sm.slot_bsize.upload(pk.slot_bsize, s);
+    // slot rows as SELL-L slices, 8 per chunk
+    std::vector<int32_t> rows_for_slices;   // row of each (slice-row) position
+    auto sp = sellL_slices(hl.A, &pk.slot_row, L);
+    sm.rows.L = L;
+    sm.rows.nrows = (int)pk.slot_row.size();
+    sm.rows.nslices = (int)(sp.size() - 1);
+    sm.rows.stored = sp.back();
+    sm.rows.slice_ptr.upload(sp, s);
+    sm.rows.col.alloc(sm.rows.stored);
+    sm.rows.val.alloc(sm.rows.stored);
+    launch_slotL_fill<V>(h->A64[l], sm, s);
+    sm.inv.alloc((size_t)sm.nctas * sm.bmax * sm.slots);
+    sm.inv.zero(s);
+    DevArray<int32_t> dsp, dsi, dsc, dsb;
+    dsp.upload(st.star_ptr, s);
+    dsi.upload(st.star_idx, s);
+    dsc.upload(pk.star_cta, s);
+    dsb.upload(pk.star_base, s);
+    launch_star_inverseL<V>(h->A64[l], st.nstars, dsp.p, dsi.p, dsc.p, dsb.p, sm, h->errflag.p, s);
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    sm.stored_rows_nnz = 0;
+    if (cn) {
+        cn->assign(st.ncolours, 0);
+        ci->assign(st.ncolours, 0);
+        cr->assign(st.ncolours, 0);
+        for (int c = 0; c < st.ncolours; ++c)
+            for (int k = pk.colour_cta_begin[c]; k < pk.colour_cta_begin[c + 1]; ++k)
+                for (int q = 0; q < pk.slots; ++q) {
+                    const int r = pk.slot_row[(size_t)k * pk.slots + q];
+                    if (r < 0) continue;
+                    (*cn)[c] += hl.A.ptr[r + 1] - hl.A.ptr[r];
+                    (*ci)[c] += pk.slot_bsize[(size_t)k * pk.slots + q];
+                    (*cr)[c] += 1;
+                }
+    }
+}
+
+// time fn() (enqueued on s): best of `reps` after one warm-up, in ms
+template <class F>
+static float time_best(cudaStream_t s, int reps, F&& fn) {
+    cudaEvent_t a, b;
+    AMGH_CUDA(cudaEventCreate(&a));
+    AMGH_CUDA(cudaEventCreate(&b));
+    fn();
+    float best = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+        AMGH_CUDA(cudaEventRecord(a, s));
+        fn();
+        AMGH_CUDA(cudaEventRecord(b, s));
+        AMGH_CUDA(cudaEventSynchronize(b));
+        float ms = 0.f;
+        AMGH_CUDA(cudaEventElapsedTime(&ms, a, b));
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+static bool tuning_enabled() {
+    const char* e = std::getenv("AMGH_TUNE");
+    return !(e && std::string(e) == "0");
+}
+
+// process-wide cache of tuned choices, keyed by the shape of a level
+static std::mutex g_tune_mu;
+static std::map<std::string, LevelChoice> g_tune_cache;
+
+static std::vector<int> lane_candidates(double avg_len, int n, int need_slots_for) {
+    std::vector<int> out;
+    for (int L : {1, 2, 4, 8, 16, 32}) {
+        if (need_slots_for > 0 && CTA_THREADS / L < need_slots_for) continue;
+        if (L > 1 && L > avg_len / 2.0) continue;
+        if (n > 400000 && L > 2) continue;   // large levels: the FP64 pipe decides, keep L small
+        out.push_back(L);
+    }
+    if (out.empty()) out.push_back(1);
+    return out;
+}
+
 template <class V, class T>
-static void build_engine(amgh_ctx* h, Engine<V, T>* e) {
+static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
+    cudaStream_t s = h->s;
+    const LevelHost& hl = h->hl[l];
+    d.n = hl.A.nrows;
+    d.nnzA = hl.A.nnz();
+    d.nnzP = hl.cz.P.nnz();
+    d.f.alloc(d.n);
+    d.x.alloc(d.n);
+    d.y.alloc(d.n);
+    d.r.alloc(d.n);
+    d.f.zero(s);
+    d.x.zero(s);
+    d.y.zero(s);
+    d.r.zero(s);
+    d.l1inv.alloc(d.n);
+    launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
+    const double avg = d.n ? (double)d.nnzA / d.n : 1.0;
+    const double avgPT = hl.cz.PT.nrows ? (double)hl.cz.PT.nnz() / hl.cz.PT.nrows : 1.0;
+    const std::string key = std::to_string(sizeof(V)) + "|" + std::to_string(d.n) + "|" + std::to_string(d.nnzA) +
+                            "|" + std::to_string(hl.stars.ncolours) + "|" + std::to_string(hl.cz.P.nnz());
+    bool cached = false;
+    if (tuning_enabled()) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const double kap = ch.kappa;
+            ch = it->second;
+            ch.kappa = kap;
+            cached = true;
+        }
+    }
+    const bool tune = tuning_enabled() && !cached;
+    // coarse-level vectors for P / P^T timing use this level's type on both sides
+    DevArray<T> cvec;
+    if (tune) {
+        cvec.alloc(std::max(1, hl.cz.P.ncols));
+        cvec.zero(s);
+    }
+    // ---- A (l1-Jacobi, residual) ----
+    if (tune) {
+        float best = 1e30f;
+        for (int Lc : lane_candidates(avg, d.n, 0)) {
+            SellL<V> cand;
+            build_sellL<V>(hl.A, h->A64[l], Lc, cand, s);
+            const float ms = time_best(s, 3, [&] {
+                launch_sellL<V, T, T>(SM_RESID, cand, d.x.p, d.f.p, (const T*)nullptr, d.r.p, s);
+            });
+            if (ms < best) { best = ms; ch.L_A = Lc; }
+        }
+    }
+    build_sellL<V>(hl.A, h->A64[l], ch.L_A, d.A, s);
+    // ---- P (prolongation) and P^T (restriction) ----
+    if (tune) {
+        float best = 1e30f;
+        for (int Lc : {1, 2}) {
+            SellL<V> cand;
+            build_sellL<V>(hl.cz.P, h->P64[l], Lc, cand, s);
+            const float ms = time_best(s, 3, [&] {
+                launch_sellL<V, T, T>(SM_ADD, cand, cvec.p, (const T*)nullptr, (const T*)nullptr, d.y.p, s);
+            });
+            if (ms < best) { best = ms; ch.L_P = Lc; }
+        }
+        best = 1e30f;
+        for (int Lc : lane_candidates(avgPT, hl.cz.PT.nrows, 0)) {
+            if (Lc > 8) continue;
+            SellL<V> cand;
+            build_sellL<V>(hl.cz.PT, h->PT64[l], Lc, cand, s);
+            const float ms = time_best(s, 3, [&] {
+                launch_sellL<V, T, T>(SM_AX, cand, d.r.p, (const T*)nullptr, (const T*)nullptr, cvec.p, s);
+            });
+            if (ms < best) { best = ms; ch.L_PT = Lc; }
+        }
+    }
+    build_sellL<V>(hl.cz.P, h->P64[l], ch.L_P, d.P, s);
+    build_sellL<V>(hl.cz.PT, h->PT64[l], ch.L_PT, d.PT, s);
+    // ---- smoother ----
+    if (tune) {
+        float best = 1e30f;
+        const bool small = d.nnzA <= 3000000 && d.n <= 60000;
+        for (int Lc : lane_candidates(avg, d.n, hl.stars.max_block)) {
+            for (int fz = 0; fz <= (small ? 1 : 0); ++fz) {
+                SmootherL<V> cand;
+                build_smoother<V>(h, l, Lc, fz != 0, cand, nullptr, nullptr, nullptr);
+                const float ms = time_best(s, 2, [&] {
+                    if (cand.fused) {
+                        launch_schwarz_fused<V, T>(cand, d.f.p, d.x.p, s);
+                    } else {
+                        for (int c : Engine::colour_sequence(cand.ncolours))
+                            launch_schwarz_colourL<V, T>(cand, c, d.f.p, d.x.p, s);
+                    }
+                });
+                if (ms < best) { best = ms; ch.L_sm = Lc; ch.fused = fz != 0; }
+            }
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = ch;
+    }
+    build_smoother<V>(h, l, ch.L_sm, ch.fused, d.sm, &d.col_nnz, &d.col_inv, &d.col_rows);
+    AMGH_CUDA(cudaStreamSynchronize(s));
+}
+
+// storage precision of a level from the requested one and a condition estimate kappa of its
+// smoother blocks: reduced precision with unit roundoff u only where kappa u <= 1/4, so that the
+// block solves stay contractions; FP64 otherwise
+static int level_precision(int requested, double kappa) {
+    if (requested == AMGH_F64) return AMGH_F64;
+    const double u32 = 5.9604644775390625e-08, u16 = 3.90625e-03;
+    if (requested == AMGH_BF16 && kappa * u16 <= 0.25) return AMGH_BF16;
+    if (kappa * u32 <= 0.25) return AMGH_F32;
+    return AMGH_F64;
+}
+
+static double level_kappa(amgh_ctx* h, int l) {
+    cudaStream_t s = h->s;
+    const StarLayout& st = h->hl[l].stars;
+    DevArray<double> kap;
+    kap.alloc(1);
+    kap.zero(s);
+    DevArray<int32_t> dsp, dsi;
+    dsp.upload(st.star_ptr, s);
+    dsi.upload(st.star_idx, s);
+    launch_star_kappa(h->A64[l], st.nstars, dsp.p, dsi.p, kap.p, h->errflag.p, s);
+    double k = 0.0;
+    AMGH_CUDA(cudaMemcpyAsync(&k, kap.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    return k;
+}
+
+static void build_engine(amgh_ctx* h, Engine* e) {
     cudaStream_t s = h->s;
     const int nlev = (int)h->hl.size();
     e->nlev = nlev;
-    e->L.resize(nlev);
-    e->ncol.assign(nlev, 0);
-    e->nnzA.assign(nlev, 0);
-    e->nnzP.assign(nlev, 0);
-    e->sm_nnz_col.assign(nlev, {});
-    e->sm_inv_col.assign(nlev, {});
-    e->sm_rows_col.assign(nlev, {});
-    for (int l = 0; l < nlev; ++l) {
-        auto& d = e->L[l];
-        const LevelHost& hl = h->hl[l];
-        d.n = hl.A.nrows;
-        d.f.alloc(d.n);
-        d.x.alloc(d.n);
-        d.y.alloc(d.n);
-        d.r.alloc(d.n);
-        d.f.zero(s);
-        d.x.zero(s);
-        d.y.zero(s);
-        d.r.zero(s);
-        if (l == nlev - 1) break;
-        e->nnzA[l] = hl.A.nnz();
-        e->nnzP[l] = hl.cz.P.nnz();
-        build_sell<V>(hl.A, h->A64[l], d.A, s);
-        d.l1inv.alloc(d.n);
-        launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
-        // smoother
-        const StarLayout& st = hl.stars;
-        auto& sm = d.sm;
-        sm.ncolours = st.ncolours;
-        sm.nwarps = (int)(st.slot_row.size() / 32);
-        sm.bmax = std::max(1, st.max_block);
-        sm.colour_warp_begin = st.colour_warp_begin;
-        e->ncol[l] = st.ncolours;
-        sm.slot_row.upload(st.slot_row, s);
-        sm.slot_base.upload(st.slot_base, s);
-        sm.slot_bsize.upload(st.slot_bsize, s);
-        auto sp = sell_slices(hl.A, &st.slot_row);
-        sm.rows.nrows = (int)st.slot_row.size();
-        sm.rows.nslices = sm.nwarps;
-        sm.rows.stored = sp.back();
-        sm.rows.slice_ptr.upload(sp, s);
-        sm.rows.col.alloc(sm.rows.stored);
-        sm.rows.val.alloc(sm.rows.stored);
-        launch_slot_fill<V>(h->A64[l], sm.slot_row.p, sm.rows, s);
-        sm.inv.alloc((size_t)sm.nwarps * 32 * sm.bmax);
-        sm.inv.zero(s);
-        std::vector<int32_t> star_warp(st.nstars, 0), star_base(st.nstars, 0);
-        for (size_t q = 0; q < st.slot_row.size(); ++q)
-            if (st.slot_star[q] >= 0 && st.slot_pos[q] == 0) {
-                star_warp[st.slot_star[q]] = (int32_t)(q / 32);
-                star_base[st.slot_star[q]] = (int32_t)(q % 32);
-            }
-        DevArray<int32_t> dsp, dsi, dsw, dsb;
-        dsp.upload(st.star_ptr, s);
-        dsi.upload(st.star_idx, s);
-        dsw.upload(star_warp, s);
-        dsb.upload(star_base, s);
-        launch_star_inverse<V>(h->A64[l], st.nstars, dsp.p, dsi.p, dsw.p, dsb.p, sm.bmax, sm.inv.p, h->errflag.p, s);
-        AMGH_CUDA(cudaStreamSynchronize(s));
-        // per-colour algorithmic counts
-        e->sm_nnz_col[l].assign(st.ncolours, 0);
-        e->sm_inv_col[l].assign(st.ncolours, 0);
-        e->sm_rows_col[l].assign(st.ncolours, 0);
-        for (int c = 0; c < st.ncolours; ++c)
-            for (int w = st.colour_warp_begin[c]; w < st.colour_warp_begin[c + 1]; ++w)
-                for (int q = 0; q < 32; ++q) {
-                    int r = st.slot_row[(size_t)w * 32 + q];
-                    if (r < 0) continue;
-                    e->sm_nnz_col[l][c] += hl.A.ptr[r + 1] - hl.A.ptr[r];
-                    e->sm_inv_col[l][c] += st.slot_bsize[(size_t)w * 32 + q];
-                    e->sm_rows_col[l][c] += 1;
-                }
-        // transfers
-        build_sell<V>(hl.cz.P, h->P64[l], d.P, s);
-        build_sell<V>(hl.cz.PT, h->PT64[l], d.PT, s);
+    e->L.clear();
+    e->choice.assign(nlev, LevelChoice());
+    for (int l = 0; l + 1 < nlev; ++l) {
+        LevelChoice& ch = e->choice[l];
+        ch.kappa = level_kappa(h, l);
+        ch.prec = level_precision(h->prm.precision, ch.kappa);
+        if (ch.prec == AMGH_F64) {
+            e->L.emplace_back(std::in_place_type<LevelX<double, double>>);
+            build_level(h, l, std::get<LevelX<double, double>>(e->L.back()), ch);
+        } else if (ch.prec == AMGH_F32) {
+            e->L.emplace_back(std::in_place_type<LevelX<float, float>>);
+            build_level(h, l, std::get<LevelX<float, float>>(e->L.back()), ch);
+        } else {
+            e->L.emplace_back(std::in_place_type<LevelX<__nv_bfloat16, float>>);
+            build_level(h, l, std::get<LevelX<__nv_bfloat16, float>>(e->L.back()), ch);
+        }
     }
-    e->nL = h->hl.back().A.nrows;
-    e->cinv.alloc((size_t)e->nL * e->nL);
-    launch_convert<T>(h->cinv64.p, e->cinv.p, (int64_t)e->nL * e->nL, s);
-    if constexpr (!std::is_same<T, double>::value) {
-        e->io_in.alloc(e->L[0].n);
-        e->io_out.alloc(e->L[0].n);
+    // coarsest level: dense inverse, precision from its 1-norm condition estimate
+    const HostCSR& Ac = h->hl.back().A;
+    const int nL = Ac.nrows;
+    e->nL = nL;
+    std::vector<double> inv((size_t)nL * nL);
+    AMGH_CUDA(cudaMemcpyAsync(inv.data(), h->cinv64.p, sizeof(double) * inv.size(), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    double na = 0, ni = 0;
+    for (int c = 0; c < nL; ++c) {
+        double sa = 0, si = 0;
+        for (int r = 0; r < nL; ++r) si += std::fabs(inv[(size_t)r * nL + c]);
+        for (int32_t q = Ac.ptr[c]; q < Ac.ptr[c + 1]; ++q) sa += std::fabs(Ac.val[q]);   // symmetric
+        na = std::max(na, sa);
+        ni = std::max(ni, si);
+    }
+    LevelChoice& chL = e->choice[nlev - 1];
+    chL.kappa = na * ni;
+    chL.prec = level_precision(h->prm.precision, chL.kappa) == AMGH_F64 ? AMGH_F64 : AMGH_F32;
+    if (chL.prec == AMGH_F64) {
+        e->L.emplace_back(std::in_place_type<LevelX<double, double>>);
+        auto& d = std::get<LevelX<double, double>>(e->L.back());
+        d.n = nL;
+        d.f.alloc(nL);
+        d.x.alloc(nL);
+        e->cinv_d.alloc((size_t)nL * nL);
+        AMGH_CUDA(cudaMemcpyAsync(e->cinv_d.p, h->cinv64.p, sizeof(double) * inv.size(), cudaMemcpyDeviceToDevice, s));
+    } else {
+        e->L.emplace_back(std::in_place_type<LevelX<float, float>>);
+        auto& d = std::get<LevelX<float, float>>(e->L.back());
+        d.n = nL;
+        d.f.alloc(nL);
+        d.x.alloc(nL);
+        e->cinv_f.alloc((size_t)nL * nL);
+        launch_convert<float>(h->cinv64.p, e->cinv_f.p, (int64_t)nL * nL, s);
+    }
+    if (!e->level0_double()) {
+        const int64_t n0 = h->hl[0].A.nrows;
+        e->io_in.alloc(n0);
+        e->io_out.alloc(n0);
     }
     AMGH_CUDA(cudaStreamSynchronize(s));
 }
@@ -617,11 +974,12 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         launch_coarse_inverse(h->A64.back(), h->cinv64.p, work.p, h->errflag.p, s);
         check_flag(h, "the coarsest factorisation");
     }
-    h->eng = new_engine(prm.precision);
-    h->eng->prof = &h->prof;
-    if (prm.precision == AMGH_F64) build_engine(h, static_cast<Engine<double, double>*>(h->eng.get()));
-    else if (prm.precision == AMGH_F32) build_engine(h, static_cast<Engine<float, float>*>(h->eng.get()));
-    else build_engine(h, static_cast<Engine<__nv_bfloat16, float>*>(h->eng.get()));
+    {
+        auto* e = new Engine();
+        h->eng.reset(e);
+        e->prof = &h->prof;
+        build_engine(h, e);
+    }
     check_flag(h, "a smoother block");
     build_sell<double>(h->hl[0].A, h->A64[0], h->A0, s);
     h->nnzA0 = h->hl[0].A.nnz();
@@ -1204,6 +1562,13 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
         info->grid_complexity = sg / n0;
         info->setup_host_ms = h->host_ms;
         info->setup_device_ms = h->dev_ms;
+        auto* e = static_cast<Engine*>(h->eng.get());
+        for (int l = 0; l < nlev && l < 32 && l < (int)e->choice.size(); ++l) {
+            info->precision[l] = e->choice[l].prec;
+            info->lanes[l] = e->choice[l].L_sm;
+            info->fused[l] = e->choice[l].fused ? 1 : 0;
+            info->block_kappa[l] = e->choice[l].kappa;
+        }
         return AMGH_OK;
     });
 }

@@ -100,36 +100,11 @@ inline SellView<V> view(const Sell<V>& s) {
     return {s.nrows, s.nslices, s.slice_ptr.p, s.col.p, s.val.p};
 }
 
-// Schwarz colour sweep data: stars of one colour packed into 32-lane warps; every warp stores the
-// rows of its slots as a 32-row SELL slice, and the block inverses column-major (32 x bmax).
-template <class V>
-struct Smoother {
-    int ncolours = 0, nwarps = 0, bmax = 0;
-    std::vector<int32_t> colour_warp_begin;     // host copy, ncolours + 1
-    DevArray<int32_t> slot_row;                 // 32 per warp
-    DevArray<int8_t> slot_base, slot_bsize;     // per slot
-    Sell<V> rows;                               // nslices = nwarps
-    DevArray<V> inv;                            // nwarps * 32 * bmax
-    // FP64 inverses kept for conversion
-};
-
 struct LevelHost {
     HostCSR A;            // values on host (needed by the next coarsening's strength test)
     HostCSR G;
     Coarsening cz;        // empty on the coarsest level
     StarLayout stars;
-};
-
-// per-level device data, in the V-cycle precision V (storage) / T (vectors, accumulation)
-template <class V, class T>
-struct LevelDev {
-    int n = 0;
-    Sell<V> A;            // for residual, l1-Jacobi and the outer SpMV
-    DevArray<T> l1inv;    // 1 / sum_j |a_ij|
-    Smoother<V> sm;
-    Sell<V> P;            // n x n_c (prolongation  y += P x)
-    Sell<V> PT;           // n_c x n (restriction   y = P^T x)
-    DevArray<T> f, x, y, r;   // right-hand side, iterate, l1 target, residual
 };
 
 }  // namespace amgh

@@ -6,9 +6,11 @@
 #include "host_graph.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
-#include <queue>
 #include <utility>
 
 #ifdef _OPENMP
@@ -18,6 +20,19 @@
 namespace amgh {
 
 namespace {
+
+// phase timings on stderr when AMGH_VERBOSE=1
+struct PhaseClock {
+    bool on;
+    std::chrono::steady_clock::time_point t;
+    PhaseClock() : on(std::getenv("AMGH_VERBOSE") && std::getenv("AMGH_VERBOSE")[0] == '1'), t(std::chrono::steady_clock::now()) {}
+    void mark(const char* what) {
+        if (!on) return;
+        auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[amgh] %-28s %8.1f ms\n", what, std::chrono::duration<double, std::milli>(now - t).count());
+        t = now;
+    }
+};
 
 inline int thread_id() {
 #ifdef _OPENMP
@@ -164,79 +179,105 @@ static HostCSR augment(const HostCSR& G, int& nB) {
 // modes (original columns of G) a Ruge-Stueben strong connection of A_G = G^T A G in either
 // direction, -a_ij >= theta max_{k != i}(-a_ik); any two columns of G~ sharing a row (edge).
 // -------------------------------------------------------------------------------------------
+// CSR from (row, col) pairs: rows sorted and deduplicated
+static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& parts,
+                              int nthreads) {
+    HostCSR M;
+    M.nrows = M.ncols = n;
+    M.ptr.assign(n + 1, 0);
+    for (const auto& p : parts)
+        for (const auto& e : p) M.ptr[e.first + 1]++;
+    for (int r = 0; r < n; ++r) M.ptr[r + 1] += M.ptr[r];
+    M.idx.resize(M.ptr[n]);
+    std::vector<int32_t> cur(M.ptr.begin(), M.ptr.end() - 1);
+    for (const auto& p : parts)
+        for (const auto& e : p) M.idx[cur[e.first]++] = e.second;
+    // sort + unique each row, then compact
+    std::vector<int32_t> newlen(n);
+#pragma omp parallel for schedule(dynamic, 2048) num_threads(nthreads)
+    for (int r = 0; r < n; ++r) {
+        auto b = M.idx.begin() + M.ptr[r], e = M.idx.begin() + M.ptr[r + 1];
+        std::sort(b, e);
+        newlen[r] = (int32_t)(std::unique(b, e) - b);
+    }
+    std::vector<int32_t> ptr(n + 1, 0);
+    for (int r = 0; r < n; ++r) ptr[r + 1] = ptr[r] + newlen[r];
+    std::vector<int32_t> idx(ptr[n]);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < n; ++r) std::copy(M.idx.begin() + M.ptr[r], M.idx.begin() + M.ptr[r] + newlen[r], idx.begin() + ptr[r]);
+    M.ptr.swap(ptr);
+    M.idx.swap(idx);
+    return M;
+}
+
+// -------------------------------------------------------------------------------------------
+// Nodal graph (Section 4.1, reading of Alg. 2's "classical C/F splitting"): between gradient
+// modes (original columns of G) a Ruge-Stueben strong connection of A_G = G^T A G in either
+// direction, -a_ij >= theta max_{k != i}(-a_ik); any two columns of G~ sharing a row (edge).
+// -------------------------------------------------------------------------------------------
 static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt, const HostCSR& GtT,
                            double theta, int nthreads, HostCSR& Minc) {
     const int m = G.ncols, nn = Gt.ncols, ne = A.nrows;
     HostCSR GT = transpose_pattern(G, true);   // CSC of G: rows of column i with values
-    // incidence: columns sharing a row of G~
-    std::vector<std::vector<int32_t>> inc(nn);
-#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads)
-    for (int a = 0; a < nn; ++a) {
-        auto& v = inc[a];
-        for (int32_t t = GtT.ptr[a]; t < GtT.ptr[a + 1]; ++t) {
-            int32_t r = GtT.idx[t];
-            for (int32_t u = Gt.ptr[r]; u < Gt.ptr[r + 1]; ++u)
-                if (Gt.idx[u] != a) v.push_back(Gt.idx[u]);
-        }
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> incp(nthreads), nbp(nthreads);
+    // incidence pairs: columns sharing a row of G~
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < Gt.nrows; ++r) {
+        if (Gt.ptr[r + 1] - Gt.ptr[r] != 2) continue;
+        const int32_t a = Gt.idx[Gt.ptr[r]], b = Gt.idx[Gt.ptr[r] + 1];
+        auto& v = incp[thread_id()];
+        v.push_back({a, b});
+        v.push_back({b, a});
     }
-    Minc = from_rows(nn, nn, inc);
-    // strong connections among gradient modes
-    std::vector<std::vector<int32_t>> strong(m);
+    Minc = csr_from_pairs(nn, incp, nthreads);
+    // strong connections among gradient modes, symmetrised, plus the incidence pairs
     std::vector<std::vector<int32_t>> wmark(nthreads, std::vector<int32_t>(ne, -1));
     std::vector<std::vector<double>> w(nthreads, std::vector<double>(ne, 0.0));
     std::vector<std::vector<int32_t>> amark(nthreads, std::vector<int32_t>(m, -1));
     std::vector<std::vector<double>> acc(nthreads, std::vector<double>(m, 0.0));
-#pragma omp parallel for schedule(dynamic, 256) num_threads(nthreads)
-    for (int i = 0; i < m; ++i) {
-        int tid = thread_id();
+#pragma omp parallel num_threads(nthreads)
+    {
+        const int tid = thread_id();
         auto& wm = wmark[tid];
         auto& wv = w[tid];
         auto& am = amark[tid];
         auto& av = acc[tid];
+        auto& out = nbp[tid];
         std::vector<int32_t> tf, tj;
-        // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
-        for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) {
-            int32_t e = GT.idx[t];
-            double ge = GT.val[t];
-            for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
-                int32_t f = A.idx[q];
-                if (wm[f] != i) { wm[f] = i; wv[f] = 0.0; tf.push_back(f); }
-                wv[f] += ge * A.val[q];
+#pragma omp for schedule(dynamic, 512)
+        for (int i = 0; i < m; ++i) {
+            tf.clear();
+            tj.clear();
+            // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
+            for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) {
+                const int32_t e = GT.idx[t];
+                const double ge = GT.val[t];
+                for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
+                    const int32_t f = A.idx[q];
+                    if (wm[f] != i) { wm[f] = i; wv[f] = 0.0; tf.push_back(f); }
+                    wv[f] += ge * A.val[q];
+                }
             }
-        }
-        // row i of G^T A G
-        for (int32_t f : tf)
-            for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
-                int32_t j = G.idx[u];
-                if (am[j] != i) { am[j] = i; av[j] = 0.0; tj.push_back(j); }
-                av[j] += G.val[u] * wv[f];
-            }
-        double rowmax = -INFINITY;
-        for (int32_t j : tj)
-            if (j != i) rowmax = std::max(rowmax, -av[j]);
-        if (rowmax > 0.0) {
-            auto& s = strong[i];
+            // row i of G^T A G
+            for (int32_t f : tf)
+                for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
+                    const int32_t j = G.idx[u];
+                    if (am[j] != i) { am[j] = i; av[j] = 0.0; tj.push_back(j); }
+                    av[j] += G.val[u] * wv[f];
+                }
+            double rowmax = -INFINITY;
             for (int32_t j : tj)
-                if (j != i && -av[j] >= theta * rowmax) s.push_back(j);
+                if (j != i) rowmax = std::max(rowmax, -av[j]);
+            if (rowmax > 0.0)
+                for (int32_t j : tj)
+                    if (j != i && -av[j] >= theta * rowmax) {
+                        out.push_back({i, j});
+                        out.push_back({j, i});
+                    }
         }
     }
-    // symmetrise and merge with the incidence graph
-    std::vector<std::vector<int32_t>> nb(nn);
-    for (int a = 0; a < nn; ++a) nb[a] = inc[a];
-    for (int i = 0; i < m; ++i)
-        for (int32_t j : strong[i]) {
-            nb[i].push_back(j);
-            nb[j].push_back(i);
-        }
-#pragma omp parallel for schedule(dynamic, 1024) num_threads(nthreads)
-    for (int a = 0; a < nn; ++a) {
-        auto& v = nb[a];
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
-    }
-    return from_rows(nn, nn, nb);
+    for (int t = 0; t < nthreads; ++t) nbp[t].insert(nbp[t].end(), incp[t].begin(), incp[t].end());
+    return csr_from_pairs(nn, nbp, nthreads);
 }
 
 // -------------------------------------------------------------------------------------------
@@ -245,6 +286,55 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
 // index) splits the remaining nodes; nodes without neighbours are F.
 // -------------------------------------------------------------------------------------------
 enum : int8_t { ST_U = 0, ST_C = 1, ST_F = 2 };
+
+// Nodes bucketed by their measure; a bucket is a two-level bitset over the node indices, so that
+// the node of largest measure and, among those, of smallest index is found by scanning a few
+// summary words, and a measure increment moves a node between buckets in O(1).
+class BucketQueue {
+   public:
+    explicit BucketQueue(int n) : n_(n), w_((n + 63) / 64), s_((w_ + 63) / 64) {}
+    void insert(int64_t b, int i) {
+        ensure(b);
+        auto& lo = lo_[b];
+        if (!lo[i >> 6]) hi_[b][i >> 12] |= 1ull << ((i >> 6) & 63);
+        lo[i >> 6] |= 1ull << (i & 63);
+        count_[b]++;
+        if (b > top_) top_ = b;
+    }
+    void erase(int64_t b, int i) {
+        auto& lo = lo_[b];
+        lo[i >> 6] &= ~(1ull << (i & 63));
+        if (!lo[i >> 6]) hi_[b][i >> 12] &= ~(1ull << ((i >> 6) & 63));
+        count_[b]--;
+    }
+    // node of largest measure, smallest index among equals; -1 when empty
+    int top(int64_t* bucket) {
+        while (top_ >= 0 && count_[top_] == 0) --top_;
+        if (top_ < 0) return -1;
+        const auto& hi = hi_[top_];
+        const auto& lo = lo_[top_];
+        for (int s = 0; s < s_; ++s)
+            if (hi[s]) {
+                const int w = s * 64 + __builtin_ctzll(hi[s]);
+                *bucket = top_;
+                return w * 64 + __builtin_ctzll(lo[w]);
+            }
+        return -1;
+    }
+
+   private:
+    void ensure(int64_t b) {
+        while ((int64_t)lo_.size() <= b) {
+            lo_.emplace_back(w_, 0ull);
+            hi_.emplace_back(s_, 0ull);
+            count_.push_back(0);
+        }
+    }
+    int n_, w_, s_;
+    int64_t top_ = -1;
+    std::vector<std::vector<uint64_t>> lo_, hi_;
+    std::vector<int64_t> count_;
+};
 
 static void nodal_cf(const HostCSR& N, int m, std::vector<int8_t>& st) {
     const int nn = N.nrows;
@@ -256,8 +346,7 @@ static void nodal_cf(const HostCSR& N, int m, std::vector<int8_t>& st) {
     for (int i = 0; i < nn; ++i)
         if (st[i] == ST_U && N.ptr[i + 1] == N.ptr[i]) st[i] = ST_F;
     std::vector<int64_t> lam(nn, 0);
-    using Key = std::pair<int64_t, int32_t>;   // (measure, -index): max-heap top is the choice
-    std::priority_queue<Key> heap;
+    BucketQueue q(nn);
     for (int i = 0; i < nn; ++i) {
         if (st[i] != ST_U) continue;
         int64_t l = 0;
@@ -266,25 +355,29 @@ static void nodal_cf(const HostCSR& N, int m, std::vector<int8_t>& st) {
             l += (s == ST_U) ? 1 : (s == ST_F ? 2 : 0);
         }
         lam[i] = l;
-        heap.push({l, -i});
+        q.insert(l, i);
     }
     std::vector<int32_t> newf;
-    while (!heap.empty()) {
-        Key top = heap.top();
-        heap.pop();
-        int32_t i = -top.second;
-        if (st[i] != ST_U || lam[i] != top.first) continue;
+    int64_t b = 0;
+    for (int i = q.top(&b); i >= 0; i = q.top(&b)) {
+        q.erase(b, i);
         st[i] = ST_C;
         newf.clear();
-        for (int32_t t = N.ptr[i]; t < N.ptr[i + 1]; ++t)
-            if (st[N.idx[t]] == ST_U) {
-                st[N.idx[t]] = ST_F;
-                newf.push_back(N.idx[t]);
+        for (int32_t t = N.ptr[i]; t < N.ptr[i + 1]; ++t) {
+            const int32_t j = N.idx[t];
+            if (st[j] == ST_U) {
+                st[j] = ST_F;
+                q.erase(lam[j], j);
+                newf.push_back(j);
             }
+        }
         for (int32_t j : newf)
             for (int32_t t = N.ptr[j]; t < N.ptr[j + 1]; ++t) {
-                int32_t l = N.idx[t];
-                if (st[l] == ST_U) heap.push({++lam[l], -l});
+                const int32_t l = N.idx[t];
+                if (st[l] == ST_U) {
+                    q.erase(lam[l], l);
+                    q.insert(++lam[l], l);
+                }
             }
     }
 }
@@ -352,16 +445,20 @@ static void match(const HostCSR& Gt, const HostCSR& GtT, const HostCSR& N, const
 std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
                           int nthreads) {
     const int n = A.nrows;
+    PhaseClock clk;
     int nB = 0;
     HostCSR Gt = augment(G, nB);
     HostCSR GtT = transpose_pattern(Gt, false);
     HostCSR Minc;
     HostCSR N = nodal_graph(A, G, Gt, GtT, prm.theta, nthreads, Minc);
+    clk.mark("augment + nodal graph");
     out.m = G.ncols;
     out.nB = nB;
     nodal_cf(N, G.ncols, out.state);
+    clk.mark("nodal C/F");
     out.edges.clear();
     match(Gt, GtT, N, Minc, out.state, G.ncols, out.edges);
+    clk.mark("matching");
     const int nc = (int)out.edges.size();
     if (nc == 0) return "";
     for (const auto& e : out.edges)
@@ -435,6 +532,7 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
         for (int r = 0; r < n; ++r)
             if (comp[r] >= 0) cmem[cur[comp[r]]++] = r;   // ascending within a component
     }
+    clk.mark("G_c + components");
     std::vector<std::vector<int32_t>> patches(nc);
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
     for (int c = 0; c < nc; ++c) {
@@ -483,6 +581,7 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     for (int c = 0; c < nc; ++c)
         std::copy(patches[c].begin(), patches[c].end(), out.patch_idx.begin() + out.patch_ptr[c]);
 
+    clk.mark("patches");
     // ---- patterns of P (n x nc) and P^T, with positions of every computed entry -------------
     HostCSR& P = out.P;
     P.nrows = n;
@@ -544,9 +643,11 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
             ++pos;
         }
     }
+    clk.mark("P, P^T patterns");
     // ---- symbolic Galerkin patterns ----------------------------------------------------------
     out.AP = symbolic_rows(A, P, nthreads);
     out.Ac = symbolic_rows(PT, out.AP, nthreads);
+    clk.mark("symbolic AP, PtAP");
     return "";
 }
 
@@ -555,6 +656,7 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
 // stars", and the warp slot layout (stars of one colour packed into 32-lane groups).
 // -------------------------------------------------------------------------------------------
 std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
+    PhaseClock clk;
     HostCSR GT = transpose_pattern(G, false);
     const int ns = G.ncols;
     L.nstars = ns;
@@ -563,32 +665,42 @@ std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
     L.max_block = 0;
     for (int j = 0; j < ns; ++j) L.max_block = std::max(L.max_block, GT.ptr[j + 1] - GT.ptr[j]);
     if (L.max_block > 32) return "smoother star of " + std::to_string(L.max_block) + " DoFs exceeds 32";
-    L.colour.assign(ns, -1);
-    std::vector<int32_t> stamp(ns, -1);
-    std::vector<char> taken;
-    int ncol = 0;
-    std::vector<int32_t> nbrs;
+    // conflict lists in parallel (star j ~ j' when an entry of A couples them), then the greedy
+    // pass in ascending j, which is inherently sequential
+    std::vector<std::vector<int32_t>> nbr(ns);
+    int nthreads = 1;
+#ifdef _OPENMP
+    nthreads = std::max(1, std::min(omp_get_max_threads(), 32));
+#endif
+    std::vector<std::vector<int32_t>> stamps(nthreads, std::vector<int32_t>(ns, -1));
+#pragma omp parallel for schedule(dynamic, 512) num_threads(nthreads)
     for (int j = 0; j < ns; ++j) {
-        nbrs.clear();
+        auto& stamp = stamps[thread_id()];
+        auto& v = nbr[j];
         for (int32_t t = GT.ptr[j]; t < GT.ptr[j + 1]; ++t) {
             int32_t e = GT.idx[t];
             for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
                 int32_t f = A.idx[q];
                 for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
                     int32_t jj = G.idx[u];
-                    if (jj != j && stamp[jj] != j) { stamp[jj] = j; nbrs.push_back(jj); }
+                    if (jj < j && stamp[jj] != j) { stamp[jj] = j; v.push_back(jj); }
                 }
             }
         }
-        taken.assign(ncol + 1, 0);
-        for (int32_t jj : nbrs)
-            if (L.colour[jj] >= 0) taken[L.colour[jj]] = 1;
+    }
+    L.colour.assign(ns, -1);
+    std::vector<int32_t> mark;
+    int ncol = 0;
+    for (int j = 0; j < ns; ++j) {
+        mark.assign(ncol + 1, -1);
+        for (int32_t jj : nbr[j]) mark[L.colour[jj]] = j;
         int c = 0;
-        while (taken[c]) ++c;
+        while (mark[c] == j) ++c;
         L.colour[j] = c;
         ncol = std::max(ncol, c + 1);
     }
     L.ncolours = ncol;
+    clk.mark("stars + colouring");
     // warp slots
     L.colour_warp_begin.assign(ncol + 1, 0);
     L.slot_row.clear(); L.slot_star.clear(); L.slot_base.clear(); L.slot_bsize.clear(); L.slot_pos.clear();

@@ -20,18 +20,9 @@ void launch_ac_numeric(const DevCSR& PT, const DevCSR& AP, DevCSR& Ac, cudaStrea
 template <class T>
 void launch_l1inv(const DevCSR& A, T* out, cudaStream_t s);
 
-// SELL copy of a CSR matrix in storage type V (padding: value 0, column = own row or 0)
+// SELL copy (one lane per row) of a CSR matrix in storage type V, for the outer FP64 SpMV
 template <class V>
 void launch_sell_fill(const DevCSR& M, Sell<V>& S, cudaStream_t s);
-// SELL of the smoother's slot rows (slot_row[w*32 + lane] = DoF or -1)
-template <class V>
-void launch_slot_fill(const DevCSR& A, const int32_t* slot_row, Sell<V>& S, cudaStream_t s);
-
-// Star-block inverses written in the smoother's slot layout (32 x bmax per warp, column-major).
-template <class V>
-void launch_star_inverse(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
-                         const int32_t* star_warp, const int32_t* star_base, int bmax, V* inv,
-                         int* err_flag, cudaStream_t s);
 
 // Dense inverse of the coarsest matrix (Cholesky factor, then inverse of the factor) into inv
 // (n x n, FP64, row-major); work: n*n doubles.
@@ -44,13 +35,10 @@ void launch_to_double(const T* in, double* out, int64_t n, cudaStream_t s);
 
 // ---------------- solve (V-cycle precision V storage, T vectors) ---------------------------
 enum SellMode { SELL_AX = 0, SELL_RESID = 1, SELL_L1 = 2, SELL_ADD = 3 };
-// MODE AX: y = A x; RESID: y = f - A x; L1: y = x + dinv (f - A x); ADD: y += A x
+// outer FP64 SpMV passes.  MODE AX: y = A x; RESID: y = f - A x
 template <class V, class T>
 void launch_sell(int mode, const Sell<V>& A, const T* x, const T* f, const T* dinv, T* y,
                  cudaStream_t s);
-
-template <class V, class T>
-void launch_schwarz_colour(const Smoother<V>& S, int colour, const T* f, T* x, cudaStream_t s);
 
 template <class T>
 void launch_coarse_apply(const T* inv, int n, const T* x, T* y, cudaStream_t s);

@@ -171,83 +171,6 @@ __global__ void sell_fill_kernel(int n, const int32_t* __restrict__ ptr, const i
     }
 }
 
-template <class V>
-__global__ void slot_fill_kernel(int nwarps, const int32_t* __restrict__ slot_row, const int32_t* __restrict__ ptr,
-                                 const int32_t* __restrict__ idx, const double* __restrict__ val,
-                                 const int64_t* __restrict__ sptr, int32_t* __restrict__ scol, V* __restrict__ sval) {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = slot >> 5, lane = slot & 31;
-    if (w >= nwarps) return;
-    const int row = slot_row[slot];
-    const int64_t st = sptr[w];
-    const int width = (int)((sptr[w + 1] - st) >> 5);
-    int b = 0, len = 0;
-    if (row >= 0) { b = ptr[row]; len = ptr[row + 1] - b; }
-    for (int t = 0; t < width; ++t) {
-        const int64_t o = st + 32 * (int64_t)t + lane;
-        if (t < len) { scol[o] = idx[b + t]; sval[o] = from_double<V>(val[b + t]); }
-        else { scol[o] = row >= 0 ? row : 0; sval[o] = from_double<V>(0.0); }
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Star-block inverses: one warp per star, Gauss-Jordan on the SPD block (no pivoting needed),
-// rows of the inverse written to the star's slots (column-major within the warp group).
-// ---------------------------------------------------------------------------------------------
-template <class V>
-__global__ void star_inverse_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
-                                    const double* __restrict__ Aval, int nstars, const int32_t* __restrict__ star_ptr,
-                                    const int32_t* __restrict__ star_idx, const int32_t* __restrict__ star_warp,
-                                    const int32_t* __restrict__ star_base, int bmax, V* __restrict__ inv,
-                                    int* err_flag) {
-    __shared__ double sm[2][2][32 * 33];
-    __shared__ double fac[2][32];
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x * 2 + wl;
-    if (j >= nstars) return;
-    const int b0 = star_ptr[j], b = star_ptr[j + 1] - b0;
-    double* M = sm[wl][0];
-    double* I = sm[wl][1];
-    // gather: lane r handles row r of the block
-    for (int r = 0; r < b; ++r) { if (lane < b) { M[r * 33 + lane] = 0.0; I[r * 33 + lane] = (r == lane); } }
-    __syncwarp();
-    if (lane < b) {
-        const int g = star_idx[b0 + lane];
-        for (int q = Aptr[g]; q < Aptr[g + 1]; ++q) {
-            const int c = bsearch_i32(star_idx, b0, b0 + b, Aidx[q]);
-            if (c >= 0) M[lane * 33 + (c - b0)] = Aval[q];
-        }
-    }
-    __syncwarp();
-    bool bad = false;
-    for (int k = 0; k < b; ++k) {
-        double piv = M[k * 33 + k];
-        if (!(piv > 0.0)) { bad = true; piv = 1.0; }
-        __syncwarp();
-        if (lane < b) { M[k * 33 + lane] /= piv; I[k * 33 + lane] /= piv; }
-        if (lane < b) fac[wl][lane] = M[lane * 33 + k];
-        __syncwarp();
-        if (lane < b) {
-            // after the division row k holds M[k][k] = 1 (fac[k] was read after division)
-            for (int i = 0; i < b; ++i) {
-                if (i == k) continue;
-                const double f = fac[wl][i];
-                M[i * 33 + lane] -= f * M[k * 33 + lane];
-                I[i * 33 + lane] -= f * I[k * 33 + lane];
-            }
-        }
-        __syncwarp();
-    }
-    if (bad && lane == 0) atomicExch(err_flag, 1);
-    const int w = star_warp[j], base = star_base[j];
-    // slot (base + r) row r of the inverse: inv[w*32*bmax + k*32 + base + r] = I[r][k]
-    if (lane < b) {
-        const int r = lane;
-        for (int k = 0; k < b; ++k)
-            inv[(int64_t)w * 32 * bmax + k * 32 + base + r] = from_double<V>(I[r * 33 + k]);
-    }
-}
-
 // Dense inverse of the coarsest matrix, one CTA: gather, Gauss-Jordan (SPD, no pivoting).
 __global__ void coarse_inverse_kernel(int n, const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
                                       const double* __restrict__ Aval, double* __restrict__ inv,
@@ -341,24 +264,6 @@ void launch_sell_fill(const DevCSR& M, Sell<V>& S, cudaStream_t s) {
     AMGH_LAUNCHED();
 }
 
-template <class V>
-void launch_slot_fill(const DevCSR& A, const int32_t* slot_row, Sell<V>& S, cudaStream_t s) {
-    if (S.nslices == 0) return;
-    slot_fill_kernel<V><<<S.nslices, 32, 0, s>>>(S.nslices, slot_row, A.ptr.p, A.idx.p, A.val.p, S.slice_ptr.p,
-                                                 S.col.p, S.val.p);
-    AMGH_LAUNCHED();
-}
-
-template <class V>
-void launch_star_inverse(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
-                         const int32_t* star_warp, const int32_t* star_base, int bmax, V* inv, int* err_flag,
-                         cudaStream_t s) {
-    if (nstars == 0) return;
-    star_inverse_kernel<V><<<(nstars + 1) / 2, 64, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, nstars, star_ptr, star_idx,
-                                                            star_warp, star_base, bmax, inv, err_flag);
-    AMGH_LAUNCHED();
-}
-
 void launch_coarse_inverse(const DevCSR& A, double* inv, double* work, int* err_flag, cudaStream_t s) {
     coarse_inverse_kernel<<<1, 1024, 0, s>>>(A.nrows, A.ptr.p, A.idx.p, A.val.p, inv, work, err_flag);
     AMGH_LAUNCHED();
@@ -371,15 +276,11 @@ void launch_convert(const double* in, T* out, int64_t n, cudaStream_t s) {
     AMGH_LAUNCHED();
 }
 
-#define INST_V(V)                                                                                     \
-    template void launch_sell_fill<V>(const DevCSR&, Sell<V>&, cudaStream_t);                         \
-    template void launch_slot_fill<V>(const DevCSR&, const int32_t*, Sell<V>&, cudaStream_t);         \
-    template void launch_star_inverse<V>(const DevCSR&, int, const int32_t*, const int32_t*,          \
-                                         const int32_t*, const int32_t*, int, V*, int*, cudaStream_t); \
-    template void launch_convert<V>(const double*, V*, int64_t, cudaStream_t);
+#define INST_V(V) template void launch_convert<V>(const double*, V*, int64_t, cudaStream_t);
 INST_V(double)
 INST_V(float)
 INST_V(__nv_bfloat16)
+template void launch_sell_fill<double>(const DevCSR&, Sell<double>&, cudaStream_t);
 template void launch_l1inv<double>(const DevCSR&, double*, cudaStream_t);
 template void launch_l1inv<float>(const DevCSR&, float*, cudaStream_t);
 

@@ -44,36 +44,6 @@ __global__ void __launch_bounds__(256) sell_kernel(SellView<V> A, const T* __res
     else y[row] += s;
 }
 
-// One colour of the multiplicative Schwarz sweep: every slot (one row of one star) forms its
-// residual f_i - (A x)_i; the star's lanes exchange residuals by shuffles and apply their row of
-// A_BB^{-1}; x_B += A_BB^{-1} r_B.  Stars of one colour share no row and no coupling, so the
-// update is order-free; a star never straddles two warps.
-template <class V, class T>
-__global__ void __launch_bounds__(256) schwarz_kernel(SellView<V> S, int warp_begin, int warp_end,
-                                                      const int32_t* __restrict__ slot_row,
-                                                      const int8_t* __restrict__ slot_base,
-                                                      const int8_t* __restrict__ slot_bsize,
-                                                      const V* __restrict__ inv, int bmax,
-                                                      const T* __restrict__ f, T* __restrict__ x) {
-    const int gw = warp_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
-    if (gw >= warp_end) return;                     // uniform over the warp
-    const int64_t slot = (int64_t)gw * 32 + lane;
-    const int row = slot_row[slot];
-    const int base = slot_base[slot], bs = slot_bsize[slot];
-    const int64_t st = S.slice_ptr[gw];
-    const int w = (int)((S.slice_ptr[gw + 1] - st) >> 5);
-    const T s = row_dot<V, T>(S, st, w, lane, x);
-    const T r = row >= 0 ? f[row] - s : T(0);
-    const V* __restrict__ iv = inv + (int64_t)gw * 32 * bmax + lane;
-    T d = T(0);
-    for (int k = 0; k < bmax; ++k) {
-        const T rk = __shfl_sync(0xffffffffu, r, (base + k) & 31);
-        if (k < bs) d = fma(widen<V, T>(iv[32 * k]), rk, d);
-    }
-    if (row >= 0) x[row] += d;
-}
-
 template <class T>
 __global__ void coarse_apply_kernel(const T* __restrict__ inv, int n, const T* __restrict__ x, T* __restrict__ y) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -226,17 +196,6 @@ void launch_sell(int mode, const Sell<V>& A, const T* x, const T* f, const T* di
     AMGH_LAUNCHED();
 }
 
-template <class V, class T>
-void launch_schwarz_colour(const Smoother<V>& S, int colour, const T* f, T* x, cudaStream_t s) {
-    const int wb = S.colour_warp_begin[colour], we = S.colour_warp_begin[colour + 1];
-    if (we <= wb) return;
-    const int threads = 256;
-    const int blocks = ((we - wb) * 32 + threads - 1) / threads;
-    schwarz_kernel<V, T><<<blocks, threads, 0, s>>>(view(S.rows), wb, we, S.slot_row.p, S.slot_base.p,
-                                                    S.slot_bsize.p, S.inv.p, S.bmax, f, x);
-    AMGH_LAUNCHED();
-}
-
 template <class T>
 void launch_coarse_apply(const T* inv, int n, const T* x, T* y, cudaStream_t s) {
     coarse_apply_kernel<T><<<1, 256, 0, s>>>(inv, n, x, y);
@@ -299,11 +258,6 @@ template void launch_to_double<float>(const float*, double*, int64_t, cudaStream
 template void launch_to_double<double>(const double*, double*, int64_t, cudaStream_t);
 
 template void launch_sell<double, double>(int, const Sell<double>&, const double*, const double*, const double*, double*, cudaStream_t);
-template void launch_sell<float, float>(int, const Sell<float>&, const float*, const float*, const float*, float*, cudaStream_t);
-template void launch_sell<__nv_bfloat16, float>(int, const Sell<__nv_bfloat16>&, const float*, const float*, const float*, float*, cudaStream_t);
-template void launch_schwarz_colour<double, double>(const Smoother<double>&, int, const double*, double*, cudaStream_t);
-template void launch_schwarz_colour<float, float>(const Smoother<float>&, int, const float*, float*, cudaStream_t);
-template void launch_schwarz_colour<__nv_bfloat16, float>(const Smoother<__nv_bfloat16>&, int, const float*, float*, cudaStream_t);
 template void launch_coarse_apply<double>(const double*, int, const double*, double*, cudaStream_t);
 template void launch_coarse_apply<float>(const float*, int, const float*, float*, cudaStream_t);
 

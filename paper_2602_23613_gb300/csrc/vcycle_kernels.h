@@ -1,0 +1,36 @@
+// Launchers of the V-cycle kernels with L lanes per row and per-level precisions.
+#pragma once
+#include "layout.h"
+
+namespace amgh {
+
+enum SellModeL { SM_AX = 0, SM_RESID = 1, SM_L1 = 2, SM_ADD = 3 };
+
+// MODE AX: y = M x;  RESID: y = f - M x;  L1: y = x + dinv (f - M x);  ADD: y += M x.
+// V: storage of M; TX: type of x; TY: type of f, dinv and y.  Accumulation in double when either
+// vector type is double, else in float.  Supported L: 1, 2, 4, 8, 16, 32.
+template <class V, class TX, class TY>
+void launch_sellL(int mode, const SellL<V>& M, const TX* x, const TY* f, const TY* dinv, TY* y, cudaStream_t s);
+
+// one colour of the multiplicative Schwarz sweep (chunks [cta_begin, cta_end) of the colour)
+template <class V, class T>
+void launch_schwarz_colourL(const SmootherL<V>& S, int colour, const T* f, T* x, cudaStream_t s);
+// whole symmetric sweep (colours 0..C-1, C-2..0) in one single-CTA launch
+template <class V, class T>
+void launch_schwarz_fused(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s);
+
+// setup: fill the SELL-L copy of a CSR matrix, the smoother's slot rows, and the star inverses
+template <class V>
+void launch_sellL_fill(const DevCSR& M, SellL<V>& S, cudaStream_t s);
+template <class V>
+void launch_slotL_fill(const DevCSR& A, SmootherL<V>& S, cudaStream_t s);
+template <class V>
+void launch_star_inverseL(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
+                          const int32_t* star_cta, const int32_t* star_base, SmootherL<V>& S, int* err_flag,
+                          cudaStream_t s);
+// largest 1-norm condition estimate ||A_BB||_1 ||A_BB^-1||_1 over the stars (FP64), into *kappa
+// (device double, must be zeroed by the caller)
+void launch_star_kappa(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
+                       double* kappa, int* err_flag, cudaStream_t s);
+
+}  // namespace amgh

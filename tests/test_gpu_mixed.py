@@ -35,6 +35,18 @@ def test_mixed_vcycle_and_fcg(amgh, prec, u, case):
     h64 = amgh.amgh_setup(p["A"], p["G"])
     h = amgh.amgh_setup(p["A"], p["G"], precision=code)
     H = O.setup(p["A"], p["G"], coarse_size=100)
+    info = amgh.amgh_info(h)
+    print("mixed %s %s level precisions %s block kappa %s" %
+          (case, prec, info["precision"], ["%.1e" % k for k in info["block_kappa"]]))
+    # the policy: reduced precision only where kappa * u <= 1/4
+    for q, k in zip(info["precision"][:-1], info["block_kappa"][:-1]):
+        if q == amgh.AMGH_BF16:
+            assert k * 2.0 ** -8 <= 0.25
+        elif q == amgh.AMGH_F32:
+            assert k * 2.0 ** -24 <= 0.25
+        else:
+            assert k * 2.0 ** -24 > 0.25 or prec == "f64"
+    assert any(q != amgh.AMGH_F64 for q in info["precision"])
     # same structure in every precision
     s64, s = amgh.amgh_level_structure(h64, 0), amgh.amgh_level_structure(h, 0)
     assert np.array_equal(s64["edges"], s["edges"])
