@@ -49,6 +49,7 @@ typedef enum {
 } amgh_status;
 
 typedef struct amgh_ctx* amgh_handle;
+typedef struct amgh_mlp_ctx* amgh_mlp;
 
 /* A CSR matrix: nrows x ncols, nnz stored entries.  row_ptr has nrows+1 entries with
  * row_ptr[0] = 0 and row_ptr[nrows] = nnz; col and val have nnz entries.  on_device = 1 when the
@@ -67,7 +68,11 @@ typedef struct {
 enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
 
 /* interior extension of the coarse variables (Eq. sparseP): exact local solves on each coarse
- * edge's patch, or the weights predicted by a trained network (amgh_mlp_*) on the same pattern */
+ * edge's patch, or, on the finest level, the values predicted by a trained network (amgh_mlp_*)
+ * on the same pattern.  A learned setup measures the convergence factor rho of 10 stand-alone
+ * V-cycles on A x = 0 (x0 ~ U(-1,1), SplitMix64 stream 8, seed 0) and falls back to the exact
+ * local solves when rho exceeds 1.1 times the exact solves' factor (params.rho_ref, or measured
+ * on an exact setup); amgh_info reports which interpolation was kept. */
 enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1 };
 
 typedef struct {
@@ -83,10 +88,18 @@ typedef struct {
     double theta;         /* strength-of-connection threshold of the nodal C/F split (0.25)    */
     double stall_ratio;   /* stop when n_coarse > stall_ratio * n (0.9)                         */
     void* stream;         /* cudaStream_t for all work of the handle; NULL = a private stream   */
+    int dense_tail;       /* the V-cycle's sub-cycle below the first coarse level (not the
+                             finest) with at most this many DoFs is linear in its right-hand
+                             side; it is computed once at setup, column block by column block,
+                             and applied as one dense FP64 (or FP32) operator.  0 = recurse to
+                             the coarsest level every time.  Default 2048, at most 8192.       */
+    amgh_mlp mlp;         /* network for AMGH_INTERP_LEARNED (see amgh_mlp_*), else NULL        */
+    double rho_ref;       /* reference convergence factor of the exact local solves for the
+                             learned fallback test; <= 0: measure it with an exact setup       */
 } amgh_params;
 
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 2048. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,
@@ -158,6 +171,19 @@ amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* 
 amgh_status amgh_pcg_solve_noalloc(amgh_handle h, const double* f, double* x, double tol, int maxit,
                                    int* iters, double* relres);
 
+/* k right-hand sides with the same matrix (Section 5's PCG per column): F and X are n x k
+ * column-major (column c at F + c n), host or device (same kind), X holds the initial guesses.
+ * The k CG recurrences are independent (their own alpha, beta and stopping test); every matrix
+ * product and V-cycle step is done for all unconverged columns at once, reading each matrix
+ * entry once per step (sparse matrix times a row-major n x k block).  The V-cycle of this entry
+ * is FP64.  iters and relres (may be NULL) receive k entries.  1 <= k <= 4096.  Returns
+ * NOT_CONVERGED if any column reached maxit. */
+amgh_status amgh_pcg_solve_multi(amgh_handle h, const double* F, double* X, int k, double tol, int maxit,
+                                 int* iters, double* relres);
+
+/* Z = B R for k right-hand sides at once (n x k column-major device arrays). */
+amgh_status amgh_vcycle_multi(amgh_handle h, const double* R, double* Z, int k);
+
 /* Stand-alone V-cycle iteration x <- x + B (f - A x) (Section 5, "AMG" counts), same stopping
  * rule and argument conventions as amgh_pcg_solve, on the true residual. */
 amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit,
@@ -180,6 +206,11 @@ typedef struct {
     int fused[32];        /* 1 if the level's whole Schwarz sweep runs as one launch           */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
                                (coarsest level: of its matrix)                                  */
+    int dense_tail;       /* level whose sub-cycle is applied as a dense operator, or -1       */
+    int interp_used;      /* AMGH_INTERP_LOCAL or AMGH_INTERP_LEARNED (after the fallback test) */
+    double rho;           /* measured convergence factor of the kept hierarchy (learned setups)  */
+    double rho_exact;     /* the exact local solves' factor it was compared with               */
+    double interp_ms;     /* wall time of filling the finest level's P values (solves or network) */
 } amgh_hier_info;
 
 /* Hierarchy statistics (levels, sizes, complexities as defined in Section 5, setup time split). */
@@ -225,6 +256,33 @@ amgh_status amgh_kernel_stats(amgh_handle h, int64_t* launches, double* total_ms
 /* Number of kernels the library has launched in this process, over all handles (a CUDA-graph
  * replay counts every kernel it runs); the handle argument may be NULL. */
 int64_t amgh_launch_count(amgh_handle h);
+
+/* ---- learned interpolation weights (a 3-layer perceptron, width 64, FP32, trained on the GPU) ----
+ * Input per finest-level coarse edge: 3 features per patch slot (64 slots) plus 2, from A alone
+ * (signed log magnitudes, normalised by A[DoF1, DoF1], of the slot's diagonal, of the local
+ * right-hand side of Eq. sparseP and of its coupling inside the patch); output: the patch values
+ * of the edge's column of P.  Training target: the exact local solves; loss: masked mean squared
+ * error; optimiser: Adam. */
+amgh_status amgh_mlp_create(uint64_t seed, amgh_mlp* out);   /* Glorot-uniform init, stream 7   */
+/* append the finest-level samples (features, exact patch values) of a hierarchy built with exact
+ * local solves (patches of at most 64 DoFs) to the network's device-resident training set */
+amgh_status amgh_mlp_add_samples(amgh_mlp m, amgh_handle h);
+int64_t amgh_mlp_num_samples(amgh_mlp m);
+/* epochs over the samples in shuffled batches (Fisher-Yates from stream 7, seed + epoch) */
+amgh_status amgh_mlp_train(amgh_mlp m, int epochs, int batch, double lr, uint64_t seed, double* final_loss);
+/* parameters W1 (194x64), b1, W2 (64x64), b2, W3 (64x64), b3, row-major FP32, concatenated:
+ * copy them out (out != NULL) and/or in (in != NULL); count receives their number */
+amgh_status amgh_mlp_params(amgh_mlp m, float* out, float* in, int64_t* count);
+/* loss and gradient (same layout as the parameters) of one batch of host arrays X (nb x 194),
+ * T and M (nb x 64) */
+amgh_status amgh_mlp_loss_grad(amgh_mlp m, const float* X, const float* T, const float* M, int nb, double* loss,
+                               float* grad);
+amgh_status amgh_mlp_predict(amgh_mlp m, const float* X, int64_t n, float* Y);   /* host arrays */
+/* the finest level's features (n x 194), exact targets and masks (n x 64) of a hierarchy, into host
+ * arrays (NULL: skip); n receives the number of coarse edges */
+amgh_status amgh_mlp_features(amgh_handle h, float* X, float* T, float* M, int64_t* n);
+const char* amgh_mlp_last_error(amgh_mlp m);
+void amgh_mlp_destroy(amgh_mlp m);
 
 const char* amgh_last_error(amgh_handle h);
 void amgh_destroy(amgh_handle h);

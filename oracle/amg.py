@@ -587,3 +587,10 @@ def complexities(H):
     nnz = [L["A"].nnz for L in H]
     n = [L["A"].shape[0] for L in H]
     return sum(nnz) / nnz[0], sum(n) / n[0]
+
+
+def probe_factor(H, x0, cycles=10):
+    """Convergence factor of `cycles` stand-alone V-cycles on A x = 0 from x0 (the quantity that
+    decides whether a learned interpolation is kept)."""
+    _, _, hist = amg_iterate(H, np.zeros(H[0]["A"].shape[0]), x0=x0, tol=0.0, maxit=cycles)
+    return convergence_factor(hist)

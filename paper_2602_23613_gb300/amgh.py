@@ -28,7 +28,8 @@ class amgh_csr(ctypes.Structure):
 class amgh_params(ctypes.Structure):
     _fields_ = [("max_levels", ctypes.c_int), ("coarse_size", ctypes.c_int), ("precision", ctypes.c_int),
                 ("interp", ctypes.c_int), ("ring", ctypes.c_int), ("p_max", ctypes.c_int),
-                ("theta", ctypes.c_double), ("stall_ratio", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("theta", ctypes.c_double), ("stall_ratio", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("dense_tail", ctypes.c_int), ("mlp", ctypes.c_void_p), ("rho_ref", ctypes.c_double)]
 
 
 class amgh_hier_info(ctypes.Structure):
@@ -37,14 +38,21 @@ class amgh_hier_info(ctypes.Structure):
                 ("max_patch", ctypes.c_int * 32), ("op_complexity", ctypes.c_double),
                 ("grid_complexity", ctypes.c_double), ("setup_host_ms", ctypes.c_double),
                 ("setup_device_ms", ctypes.c_double), ("precision", ctypes.c_int * 32),
-                ("lanes", ctypes.c_int * 32), ("fused", ctypes.c_int * 32), ("block_kappa", ctypes.c_double * 32)]
+                ("lanes", ctypes.c_int * 32), ("fused", ctypes.c_int * 32), ("block_kappa", ctypes.c_double * 32),
+                ("dense_tail", ctypes.c_int), ("interp_used", ctypes.c_int), ("rho", ctypes.c_double),
+                ("rho_exact", ctypes.c_double), ("interp_ms", ctypes.c_double)]
 
 
 _LIB = None
 EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve",
-           "amgh_batch_pcg_solve", "amgh_pcg_solve_noalloc", "amgh_amg_solve", "amgh_info",
+           "amgh_batch_pcg_solve", "amgh_pcg_solve_noalloc", "amgh_pcg_solve_multi", "amgh_vcycle_multi",
+           "amgh_amg_solve", "amgh_info",
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
-           "amgh_launch_count", "amgh_last_error", "amgh_destroy"]
+           "amgh_launch_count", "amgh_last_error", "amgh_destroy",
+           "amgh_mlp_create", "amgh_mlp_add_samples", "amgh_mlp_num_samples", "amgh_mlp_train", "amgh_mlp_params",
+           "amgh_mlp_loss_grad", "amgh_mlp_predict", "amgh_mlp_features", "amgh_mlp_last_error", "amgh_mlp_destroy"]
+_NOT_STATUS = ("amgh_default_params", "amgh_launch_count", "amgh_last_error", "amgh_destroy", "amgh_mlp_num_samples",
+               "amgh_mlp_last_error", "amgh_mlp_destroy")
 
 
 def lib_path():
@@ -69,6 +77,8 @@ def load():
     L.amgh_pcg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_amg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_pcg_solve_noalloc.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_pcg_solve_multi.argtypes = [P, P, P, I, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    L.amgh_vcycle_multi.argtypes = [P, P, P, I]
     L.amgh_batch_pcg_solve.argtypes = [I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), D, I,
                                        ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_info.argtypes = [P, ctypes.POINTER(amgh_hier_info)]
@@ -83,8 +93,22 @@ def load():
     L.amgh_last_error.restype = ctypes.c_char_p
     L.amgh_destroy.argtypes = [P]
     L.amgh_destroy.restype = None
+    U64 = ctypes.c_uint64
+    L.amgh_mlp_create.argtypes = [U64, ctypes.POINTER(P)]
+    L.amgh_mlp_add_samples.argtypes = [P, P]
+    L.amgh_mlp_num_samples.argtypes = [P]
+    L.amgh_mlp_num_samples.restype = I64
+    L.amgh_mlp_train.argtypes = [P, I, I, D, U64, ctypes.POINTER(D)]
+    L.amgh_mlp_params.argtypes = [P, P, P, ctypes.POINTER(I64)]
+    L.amgh_mlp_loss_grad.argtypes = [P, P, P, P, I, ctypes.POINTER(D), P]
+    L.amgh_mlp_predict.argtypes = [P, P, I64, P]
+    L.amgh_mlp_features.argtypes = [P, P, P, P, ctypes.POINTER(I64)]
+    L.amgh_mlp_last_error.argtypes = [P]
+    L.amgh_mlp_last_error.restype = ctypes.c_char_p
+    L.amgh_mlp_destroy.argtypes = [P]
+    L.amgh_mlp_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("amgh_default_params", "amgh_launch_count", "amgh_last_error", "amgh_destroy"):
+        if name not in _NOT_STATUS:
             getattr(L, name).restype = I
     _LIB = L
     return L
@@ -162,7 +186,7 @@ def amgh_setup(A, G, params=None, **kw):
     L = load()
     p = params if params is not None else amgh_default_params()
     for k, v in kw.items():
-        setattr(p, k, v)
+        setattr(p, k, v.ptr if isinstance(v, Mlp) else v)
     keep = []
     a, g = _csr(A, keep), _csr(G, keep)
     out = ctypes.c_void_p()
@@ -235,6 +259,24 @@ def amgh_pcg_solve_noalloc(h, f, x, tol=1e-8, maxit=500):
     return _solve(load().amgh_pcg_solve_noalloc, h, f, x, tol, maxit)
 
 
+def amgh_pcg_solve_multi(h, F, X, tol=1e-8, maxit=500):
+    """k right-hand sides: F, X are (k, n) float64 arrays/tensors (row c = right-hand side c, i.e.
+    n x k column-major).  Returns (iterations[k], relres[k], converged)."""
+    keep = []
+    k = int(F.shape[0])
+    it = (ctypes.c_int * k)()
+    rel = (ctypes.c_double * k)()
+    st = load().amgh_pcg_solve_multi(h.ptr, _vec_ptr(F, keep), _z_ptr(X), k, tol, maxit, it, rel)
+    if st not in (AMGH_OK, AMGH_ERR_NOT_CONVERGED):
+        _check(st, h.ptr)
+    return list(it), list(rel), st == AMGH_OK
+
+
+def amgh_vcycle_multi(h, R, Z):
+    """Z = B R for (k, n) CUDA tensors."""
+    _check(load().amgh_vcycle_multi(h.ptr, R.data_ptr(), Z.data_ptr(), int(R.shape[0])), h.ptr)
+
+
 def amgh_amg_solve(h, f, x, tol=1e-8, maxit=500):
     """Stand-alone V-cycle iteration.  Returns (iterations, relres, converged)."""
     return _solve(load().amgh_amg_solve, h, f, x, tol, maxit)
@@ -249,7 +291,9 @@ def amgh_info(h):
                 max_patch=list(info.max_patch[:L]), op_complexity=info.op_complexity,
                 grid_complexity=info.grid_complexity, setup_host_ms=info.setup_host_ms,
                 setup_device_ms=info.setup_device_ms, precision=list(info.precision[:L]),
-                lanes=list(info.lanes[:L]), fused=list(info.fused[:L]), block_kappa=list(info.block_kappa[:L]))
+                lanes=list(info.lanes[:L]), fused=list(info.fused[:L]), block_kappa=list(info.block_kappa[:L]),
+                dense_tail=info.dense_tail, interp_used=info.interp_used, rho=info.rho, rho_exact=info.rho_exact,
+                interp_ms=info.interp_ms)
 
 
 def amgh_level_structure(h, l):
@@ -313,3 +357,100 @@ def amgh_destroy(h):
     if h.ptr:
         load().amgh_destroy(h.ptr)
         h.ptr = None
+
+
+# ---- learned interpolation weights ----------------------------------------------------------------
+MLP_SLOTS, MLP_DIN = 64, 3 * 64 + 2
+
+
+class Mlp:
+    """Owns an amgh_mlp; destroyed with amgh_mlp_destroy."""
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            load().amgh_mlp_destroy(self.ptr)
+            self.ptr = None
+
+
+def _mcheck(st, m):
+    if st != AMGH_OK:
+        raise AmghError(st, load().amgh_mlp_last_error(m.ptr if m is not None else None).decode(errors="replace"))
+
+
+def _f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def amgh_mlp_create(seed=0):
+    out = ctypes.c_void_p()
+    _mcheck(load().amgh_mlp_create(seed, ctypes.byref(out)), None)
+    return Mlp(out.value)
+
+
+def amgh_mlp_add_samples(m, h):
+    _mcheck(load().amgh_mlp_add_samples(m.ptr, h.ptr), m)
+
+
+def amgh_mlp_num_samples(m):
+    return int(load().amgh_mlp_num_samples(m.ptr))
+
+
+def amgh_mlp_train(m, epochs, batch=256, lr=1e-3, seed=0):
+    L = ctypes.c_double(0)
+    _mcheck(load().amgh_mlp_train(m.ptr, epochs, batch, lr, seed, ctypes.byref(L)), m)
+    return L.value
+
+
+def amgh_mlp_params(m, new=None):
+    """Current parameters (W1, b1, W2, b2, W3, b3 flattened, FP32); loads `new` first if given."""
+    Lb = load()
+    n = ctypes.c_int64(0)
+    _mcheck(Lb.amgh_mlp_params(m.ptr, None, None, ctypes.byref(n)), m)
+    out = np.zeros(n.value, np.float32)
+    src = None
+    if new is not None:
+        src = _f32(new)
+        if src.size != n.value:
+            raise ValueError("expected %d parameters" % n.value)
+    _mcheck(Lb.amgh_mlp_params(m.ptr, out.ctypes.data, src.ctypes.data if src is not None else None,
+                               ctypes.byref(n)), m)
+    return out
+
+
+def amgh_mlp_loss_grad(m, X, T, M):
+    X, T, M = _f32(X), _f32(T), _f32(M)
+    n = ctypes.c_int64(0)
+    load().amgh_mlp_params(m.ptr, None, None, ctypes.byref(n))
+    g = np.zeros(n.value, np.float32)
+    L = ctypes.c_double(0)
+    _mcheck(load().amgh_mlp_loss_grad(m.ptr, X.ctypes.data, T.ctypes.data, M.ctypes.data, X.shape[0],
+                                      ctypes.byref(L), g.ctypes.data), m)
+    return L.value, g
+
+
+def amgh_mlp_predict(m, X):
+    X = _f32(X)
+    Y = np.zeros((X.shape[0], MLP_SLOTS), np.float32)
+    _mcheck(load().amgh_mlp_predict(m.ptr, X.ctypes.data, X.shape[0], Y.ctypes.data), m)
+    return Y
+
+
+def amgh_mlp_features(h):
+    """Finest-level (features, exact targets, masks) of a hierarchy as numpy FP32 arrays."""
+    Lb = load()
+    n = ctypes.c_int64(0)
+    _check(Lb.amgh_mlp_features(h.ptr, None, None, None, ctypes.byref(n)), h.ptr)
+    X = np.zeros((n.value, MLP_DIN), np.float32)
+    T = np.zeros((n.value, MLP_SLOTS), np.float32)
+    M = np.zeros((n.value, MLP_SLOTS), np.float32)
+    _check(Lb.amgh_mlp_features(h.ptr, X.ctypes.data, T.ctypes.data, M.ctypes.data, ctypes.byref(n)), h.ptr)
+    return X, T, M
+
+
+def amgh_mlp_destroy(m):
+    if m.ptr:
+        load().amgh_mlp_destroy(m.ptr)
+        m.ptr = None

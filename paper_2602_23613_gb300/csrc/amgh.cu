@@ -19,6 +19,9 @@
 
 #include "engine.cuh"
 #include "krylov_scratch.h"
+#include "mlp.cuh"
+#include "multi.cuh"
+#include "splitmix.cuh"
 #include "vcycle_kernels.h"
 
 namespace amgh {
@@ -105,6 +108,9 @@ struct Engine : EngineBase {
     int nlev = 0, nL = 0;
     DevArray<double> cinv_d;
     DevArray<float> cinv_f;
+    int tail = -1;                     // level whose whole sub-cycle is applied as a dense operator
+    DevArray<double> tail_d;
+    DevArray<float> tail_f;
     DevArray<double> io_in, io_out;   // FP64 staging when level 0 stores float vectors
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -201,7 +207,8 @@ struct Engine : EngineBase {
                                   std::visit([](auto& d) { return (int64_t)d.n; }, L[0]), s);
             cnt++;
         }
-        for (int l = 0; l + 1 < nlev; ++l) {
+        const int last = tail >= 0 ? tail : nlev - 1;
+        for (int l = 0; l < last; ++l) {
             std::visit([&](auto& d) {
                 using V = typename std::decay_t<decltype(d)>::VT;
                 using T = typename std::decay_t<decltype(d)>::TT;
@@ -225,13 +232,14 @@ struct Engine : EngineBase {
         std::visit([&](auto& d) {
             using T = typename std::decay_t<decltype(d)>::TT;
             const T* ci;
-            if constexpr (std::is_same<T, double>::value) ci = cinv_d.p;
-            else ci = cinv_f.p;
-            timed(K_COARSE, nlev - 1, (double)nL * nL * sizeof(T), s,
-                  [&] { launch_coarse_apply<T>(ci, nL, d.f.p, d.x.p, s); });
+            if constexpr (std::is_same<T, double>::value) ci = last == nlev - 1 ? cinv_d.p : tail_d.p;
+            else ci = last == nlev - 1 ? cinv_f.p : tail_f.p;
+            const int m = d.n;
+            timed(K_COARSE, last, (double)m * m * sizeof(T), s,
+                  [&] { launch_coarse_apply<T>(ci, m, d.f.p, d.x.p, s); });
             cnt++;
-        }, L[nlev - 1]);
-        for (int l = nlev - 2; l >= 0; --l) {
+        }, L[last]);
+        for (int l = last - 1; l >= 0; --l) {
             std::visit([&](auto& a, auto& b) {
                 using V = typename std::decay_t<decltype(a)>::VT;
                 using Ta = typename std::decay_t<decltype(a)>::TT;
@@ -365,6 +373,131 @@ struct Engine : EngineBase {
     }
 };
 
+// ---------------------------------------------------------------------------------------------
+// Multi-right-hand-side V-cycle (FP64, row-major K-wide vectors) on the hierarchy's FP64 CSR
+// matrices: every level's Schwarz colours, l1-Jacobi, transfers and the coarsest inverse for K
+// right-hand sides at once.
+// ---------------------------------------------------------------------------------------------
+struct MultiEngine {
+    std::vector<MultiLevel> L;
+    int nlev = 0, nL = 0, KP = 0;
+    const double* cinv = nullptr;
+    DevArray<double> partial, colv;     // per-column partial sums / results
+
+    static std::vector<int> colour_sequence(int nc) {
+        std::vector<int> seq;
+        for (int c = 0; c < nc; ++c) seq.push_back(c);
+        for (int c = nc - 2; c >= 0; --c) seq.push_back(c);
+        return seq;
+    }
+
+    void build(const std::vector<LevelHost>& hl, const std::vector<DevCSR>& A64, const std::vector<DevCSR>& P64,
+               const std::vector<DevCSR>& PT64, const double* cinv64, int* err, cudaStream_t s) {
+        nlev = (int)hl.size();
+        L.clear();
+        L.resize(nlev);
+        for (int l = 0; l < nlev; ++l) {
+            MultiLevel& d = L[l];
+            d.n = hl[l].A.nrows;
+            d.A = &A64[l];
+            if (l + 1 == nlev) break;
+            d.P = &P64[l];
+            d.PT = &PT64[l];
+            const StarLayout& st = hl[l].stars;
+            d.ncolours = st.ncolours;
+            d.bmax = std::max(1, st.max_block);
+            std::vector<int32_t> list;
+            d.colour_star_begin.assign(st.ncolours + 1, 0);
+            for (int c = 0; c < st.ncolours; ++c) {
+                d.colour_star_begin[c] = (int32_t)list.size();
+                for (int j = 0; j < st.nstars; ++j)
+                    if (st.colour[j] == c && st.star_ptr[j + 1] > st.star_ptr[j]) list.push_back(j);
+            }
+            d.colour_star_begin[st.ncolours] = (int32_t)list.size();
+            d.star_list.upload(list, s);
+            d.star_ptr.upload(st.star_ptr, s);
+            d.star_idx.upload(st.star_idx, s);
+            std::vector<int64_t> off(st.nstars + 1, 0);
+            for (int j = 0; j < st.nstars; ++j) {
+                const int64_t b = st.star_ptr[j + 1] - st.star_ptr[j];
+                off[j + 1] = off[j] + b * b;
+            }
+            d.inv_off.upload(off, s);
+            d.inv.alloc(std::max<int64_t>(1, off.back()));
+            launch_star_inverse_rowmajor(A64[l], st.nstars, d.star_ptr.p, d.star_idx.p, d.inv_off.p, d.inv.p, err, s);
+            d.l1inv.alloc(d.n);
+            launch_l1inv<double>(A64[l], d.l1inv.p, s);
+        }
+        nL = hl.back().A.nrows;
+        cinv = cinv64;
+        AMGH_CUDA(cudaStreamSynchronize(s));
+    }
+
+    std::vector<int> width;   // allocated width of each level's vectors (0 = none)
+
+    // vectors of levels >= first at width kp (levels above `first` are left alone)
+    void ensure_width(int kp, int first = 0) {
+        if ((int)width.size() != (int)L.size()) width.assign(L.size(), 0);
+        KP = kp;
+        for (size_t l = first; l < L.size(); ++l) {
+            if (width[l] == kp) continue;
+            MultiLevel& d = L[l];
+            d.F.alloc((size_t)d.n * kp);
+            d.X.alloc((size_t)d.n * kp);
+            d.Y.alloc((size_t)d.n * kp);
+            d.R.alloc((size_t)d.n * kp);
+            width[l] = kp;
+        }
+        if (partial.n != (size_t)304 * kp) {
+            partial.alloc((size_t)304 * kp);
+            colv.alloc(kp);
+        }
+    }
+
+    // X_t = (V-cycle restricted to levels t..) F_t, for the KP columns of level t's F
+    int64_t vcycle_from(int t, cudaStream_t s) {
+        int64_t cnt = 0;
+        for (int l = t; l + 1 < nlev; ++l) {
+            MultiLevel& d = L[l];
+            AMGH_CUDA(cudaMemsetAsync(d.X.p, 0, sizeof(double) * d.n * KP, s));
+            for (int c : colour_sequence(d.ncolours)) { launch_schwarz_multi(d, c, KP, d.F.p, d.X.p, s); cnt++; }
+            launch_spmm(MM_L1, *d.A, KP, d.X.p, d.F.p, d.l1inv.p, d.Y.p, s);
+            launch_spmm(MM_RESID, *d.A, KP, d.Y.p, d.F.p, nullptr, d.R.p, s);
+            launch_spmm(MM_AX, *d.PT, KP, d.R.p, nullptr, nullptr, L[l + 1].F.p, s);
+            cnt += 3;
+        }
+        launch_dense_apply_multi(cinv, nL, KP, L[nlev - 1].F.p, L[nlev - 1].X.p, s);
+        cnt++;
+        for (int l = nlev - 2; l >= t; --l) {
+            MultiLevel& d = L[l];
+            launch_spmm(MM_ADD, *d.P, KP, L[l + 1].X.p, nullptr, nullptr, d.Y.p, s);
+            launch_spmm(MM_L1, *d.A, KP, d.Y.p, d.F.p, d.l1inv.p, d.X.p, s);
+            cnt += 2;
+            for (int c : colour_sequence(d.ncolours)) { launch_schwarz_multi(d, c, KP, d.F.p, d.X.p, s); cnt++; }
+        }
+        return cnt;
+    }
+
+    // dense operator of the V-cycle restricted to levels t.. (row-major n_t x n_t), column blocks
+    void dense_tail(int t, DevArray<double>& B, cudaStream_t s) {
+        const int nt = L[t].n;
+        B.alloc((size_t)nt * nt);
+        const int kp = std::min(2048, ((nt + 31) / 32) * 32);
+        ensure_width(kp, t);
+        std::vector<double> eye((size_t)nt * kp);
+        for (int c0 = 0; c0 < nt; c0 += kp) {
+            const int cnt = std::min(kp, nt - c0);
+            std::fill(eye.begin(), eye.end(), 0.0);
+            for (int c = 0; c < cnt; ++c) eye[(size_t)(c0 + c) * kp + c] = 1.0;
+            AMGH_CUDA(cudaMemcpyAsync(L[t].F.p, eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, s));
+            vcycle_from(t, s);
+            AMGH_CUDA(cudaMemcpy2DAsync(B.p + c0, sizeof(double) * nt, L[t].X.p, sizeof(double) * kp,
+                                        sizeof(double) * cnt, nt, cudaMemcpyDeviceToDevice, s));
+            AMGH_CUDA(cudaStreamSynchronize(s));
+        }
+    }
+};
+
 }  // namespace amgh
 
 using namespace amgh;
@@ -377,6 +510,9 @@ struct amgh_ctx {
     std::vector<DevCSR> A64, P64, PT64;
     DevArray<double> cinv64;
     std::unique_ptr<EngineBase> eng;
+    std::unique_ptr<MultiEngine> meng;   // built on the first multi-RHS call (or for a dense tail)
+    DevArray<double> dense_tail_B;       // dense operator of the V-cycle below the tail level
+    int dense_tail_level = -1;
     Sell<double> A0;   // outer FP64 SpMV
     int64_t nnzA0 = 0;
     DevArray<double> kp, kq, kro, partial, scal, stage_f, stage_x;
@@ -406,12 +542,24 @@ struct amgh_ctx {
     std::vector<int> max_patch;
     bool own_stream = false;
     bool structure_only = false;
+    int interp_used = AMGH_INTERP_LOCAL;
+    double rho_used = 0.0, rho_exact = 0.0, interp_ms = 0.0;
     bool host_loop = false;   // force the host-driven Krylov loop
     ~amgh_ctx() {
         drop_solve_graph();
         eng.reset();
+        meng.reset();
         if (hscal) cudaFreeHost(hscal);
         if (own_stream && s) cudaStreamDestroy(s);
+    }
+};
+
+struct amgh_mlp_ctx {
+    MlpNet net;
+    cudaStream_t s = nullptr;
+    std::string err;
+    ~amgh_mlp_ctx() {
+        if (s) cudaStreamDestroy(s);
     }
 };
 
@@ -831,10 +979,12 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
 static void check_params(const amgh_params& prm) {
     if (prm.max_levels < 1 || prm.max_levels > 32 || prm.coarse_size < 1 || prm.ring < 1 || prm.p_max < 1 ||
         prm.p_max > 256 || prm.precision < 0 || prm.precision > 2 || !(prm.theta >= 0.0 && prm.theta <= 1.0) ||
-        !(prm.stall_ratio > 0.0))
+        !(prm.stall_ratio > 0.0) || prm.dense_tail < 0 || prm.dense_tail > 8192)
         throw StatusError{AMGH_ERR_INVALID_ARG, "parameter out of range"};
-    if (prm.interp != AMGH_INTERP_LOCAL)
-        throw StatusError{AMGH_ERR_UNSUPPORTED, "only exact local interpolation is available through amgh_setup"};
+    if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "unknown interpolation mode"};
+    if (prm.interp == AMGH_INTERP_LEARNED && !prm.mlp)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "learned interpolation needs a network (params.mlp)"};
 }
 
 static void check_inputs(const HostCSR& A, const HostCSR& G) {
@@ -945,9 +1095,33 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             dpi.upload(cz.patch_idx, s);
             dpos.upload(cz.patch_pos_P, s);
             dpost.upload(cz.patch_pos_PT, s);
-            launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
-                               h->errflag.p, s);
-            check_flag(h, "a local harmonic-extension solve");
+            double ti = 0.0;
+            if (l == 0) {
+                AMGH_CUDA(cudaStreamSynchronize(s));
+                ti = now_ms();
+            }
+            auto* net = static_cast<amgh_mlp_ctx*>(prm.mlp);
+            if (l == 0 && prm.interp == AMGH_INTERP_LEARNED && net && maxp <= MLP_SLOTS) {
+                // the network predicts the interior values of every column of P on its patch
+                DevArray<float> X, Y;
+                X.alloc((size_t)nc * MLP_DIN);
+                Y.alloc((size_t)nc * MLP_SLOTS);
+                launch_mlp_features(h->A64[l], 0, nc, de4.p, dpp.p, dpi.p, nullptr, nullptr, X.p, nullptr, nullptr, s);
+                AMGH_CUDA(cudaStreamSynchronize(s));
+                AMGH_CUDA(cudaStreamSynchronize(net->s));
+                mlp_forward(net->net, X.p, nc, Y.p, s);
+                launch_mlp_scatter(0, nc, dpp.p, Y.p, dpos.p, dpost.p, P.val.p, PT.val.p, s);
+                AMGH_CUDA(cudaStreamSynchronize(s));
+                h->interp_used = AMGH_INTERP_LEARNED;
+            } else {
+                launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
+                                   h->errflag.p, s);
+                check_flag(h, "a local harmonic-extension solve");
+            }
+            if (l == 0) {
+                AMGH_CUDA(cudaStreamSynchronize(s));
+                h->interp_ms = now_ms() - ti;
+            }
         }
         DevCSR AP, Ac;
         upload_csr(cz.AP, AP, s, false);
@@ -979,6 +1153,30 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         h->eng.reset(e);
         e->prof = &h->prof;
         build_engine(h, e);
+        // the sub-cycle below the first small level is linear in its right-hand side: apply it as
+        // one dense operator, computed column block by column block with the multi-RHS V-cycle
+        const int nlev = (int)h->hl.size();
+        int t = -1;
+        for (int l = 1; l + 1 < nlev && prm.dense_tail > 0; ++l)
+            if (h->hl[l].A.nrows <= prm.dense_tail) { t = l; break; }
+        if (t > 0) {
+            h->meng.reset(new MultiEngine());
+            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
+            h->meng->dense_tail(t, h->dense_tail_B, s);
+            check_flag(h, "a smoother block of the dense tail");
+            h->dense_tail_level = t;
+            e->tail = t;
+            const int nt = h->hl[t].A.nrows;
+            if (std::holds_alternative<LevelX<double, double>>(e->L[t])) {
+                e->tail_d.alloc((size_t)nt * nt);
+                AMGH_CUDA(cudaMemcpyAsync(e->tail_d.p, h->dense_tail_B.p, sizeof(double) * nt * nt,
+                                          cudaMemcpyDeviceToDevice, s));
+            } else {
+                e->tail_f.alloc((size_t)nt * nt);
+                launch_convert<float>(h->dense_tail_B.p, e->tail_f.p, (int64_t)nt * nt, s);
+            }
+            AMGH_CUDA(cudaStreamSynchronize(s));
+        }
     }
     check_flag(h, "a smoother block");
     build_sell<double>(h->hl[0].A, h->A64[0], h->A0, s);
@@ -1366,6 +1564,124 @@ static amgh_status pcg_scratch_impl(amgh_ctx* h, const double* f, double* x, dou
 
 }  // namespace amgh
 
+namespace amgh {
+// convergence factor of 10 stand-alone V-cycles on A x = 0 from x0 ~ U(-1,1) (probe stream, seed 0):
+// (||r_10|| / ||r_0||)^(1/10)
+static double measure_rho(amgh_ctx* h) {
+    const int64_t n = h->hl[0].A.nrows;
+    std::vector<double> x0(n), zero(n, 0.0);
+    for (int64_t i = 0; i < n; ++i) x0[i] = 2.0 * splitmix_u01(STREAM_PROBE, 0, (uint64_t)i) - 1.0;
+    DevArray<double> f, x;
+    f.upload(zero, h->s);
+    x.upload(x0, h->s);
+    int it = 0;
+    double rel = 0.0;
+    amg_impl(h, f.p, x.p, 0.0, 10, &it, &rel);   // runs all 10 cycles and reports "not converged"
+    h->err.clear();
+    return it > 0 && rel > 0 ? std::pow(rel, 1.0 / it) : 0.0;
+}
+
+static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in, int k, double tol, int maxit,
+                                  int* iters, double* relres) {
+    if (k < 1 || k > 4096 || maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad k, tol or maxit"};
+    cudaStream_t s = h->s;
+    const int64_t n = h->hl[0].A.nrows;
+    const int KP = ((k + 31) / 32) * 32;
+    if (!h->meng) {
+        h->meng.reset(new MultiEngine());
+        h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
+    }
+    MultiEngine& M = *h->meng;
+    M.ensure_width(KP);
+    const bool df = is_device_ptr(F_in), dx = is_device_ptr(X_in);
+    if (df != dx) throw StatusError{AMGH_ERR_INVALID_ARG, "F and X must both be host or both be device pointers"};
+    DevArray<double> Fs, Xs;
+    const double* F = F_in;
+    double* X = X_in;
+    if (!df) {
+        Fs.alloc((size_t)n * k);
+        Xs.alloc((size_t)n * k);
+        AMGH_CUDA(cudaMemcpyAsync(Fs.p, F_in, sizeof(double) * n * k, cudaMemcpyHostToDevice, s));
+        AMGH_CUDA(cudaMemcpyAsync(Xs.p, X_in, sizeof(double) * n * k, cudaMemcpyHostToDevice, s));
+        F = Fs.p;
+        X = Xs.p;
+    }
+    DevArray<double> MF, MX, MP, MQ, alpha, beta;
+    MF.alloc((size_t)n * KP);
+    MX.alloc((size_t)n * KP);
+    MP.alloc((size_t)n * KP);
+    MQ.alloc((size_t)n * KP);
+    alpha.alloc(KP);
+    beta.alloc(KP);
+    double* R = M.L[0].F.p;   // the V-cycle reads its right-hand side from level 0's F
+    double* Z = M.L[0].X.p;   // and leaves its result in level 0's X
+    launch_to_rowmajor(F, n, k, KP, MF.p, s);
+    launch_to_rowmajor(X, n, k, KP, MX.p, s);
+    launch_spmm(MM_RESID, h->A64[0], KP, MX.p, MF.p, nullptr, R, s);
+    std::vector<double> rr0(KP), rr(KP), rz(KP), rzn(KP), pq(KP), al(KP, 0.0), be(KP, 0.0);
+    auto coldot = [&](const double* a, const double* b, std::vector<double>& out) {
+        launch_coldot(a, b, n, KP, M.partial.p, M.colv.p, s);
+        AMGH_CUDA(cudaMemcpyAsync(out.data(), M.colv.p, sizeof(double) * KP, cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+    };
+    coldot(R, R, rr0);
+    std::vector<char> active(KP, 0);
+    std::vector<int> it_c(k, 0);
+    std::vector<double> rel_c(k, 0.0);
+    int nact = 0;
+    for (int c = 0; c < k; ++c) {
+        active[c] = rr0[c] > 0.0;
+        nact += active[c];
+    }
+    int it = 0;
+    if (nact) {
+        M.vcycle_from(0, s);
+        coldot(R, Z, rz);
+        AMGH_CUDA(cudaMemcpyAsync(MP.p, Z, sizeof(double) * n * KP, cudaMemcpyDeviceToDevice, s));
+        for (it = 1; it <= maxit && nact; ++it) {
+            launch_spmm(MM_AX, h->A64[0], KP, MP.p, nullptr, nullptr, MQ.p, s);
+            coldot(MP.p, MQ.p, pq);
+            for (int c = 0; c < KP; ++c) al[c] = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
+            AMGH_CUDA(cudaMemcpyAsync(alpha.p, al.data(), sizeof(double) * KP, cudaMemcpyHostToDevice, s));
+            launch_mcg_update(n, KP, MX.p, R, nullptr, MP.p, MQ.p, alpha.p, s);
+            coldot(R, R, rr);
+            for (int c = 0; c < k; ++c) {
+                if (!active[c]) continue;
+                const double rel = std::sqrt(rr[c] / rr0[c]);
+                it_c[c] = it;
+                rel_c[c] = rel;
+                if (!(rel == rel)) throw StatusError{AMGH_ERR_NOT_CONVERGED, "residual became NaN"};
+                if (rel <= tol) { active[c] = 0; nact--; }
+            }
+            if (!nact) break;
+            M.vcycle_from(0, s);
+            coldot(R, Z, rzn);
+            for (int c = 0; c < KP; ++c) {
+                be[c] = active[c] && rz[c] != 0.0 ? rzn[c] / rz[c] : 0.0;
+                rz[c] = rzn[c];
+            }
+            AMGH_CUDA(cudaMemcpyAsync(beta.p, be.data(), sizeof(double) * KP, cudaMemcpyHostToDevice, s));
+            launch_mp_update(n, KP, MP.p, Z, beta.p, s);
+        }
+    }
+    launch_to_colmajor(MX.p, n, k, KP, X, s);
+    if (!df) AMGH_CUDA(cudaMemcpyAsync(X_in, X, sizeof(double) * n * k, cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int c = 0; c < k; ++c) {
+        if (iters) iters[c] = it_c[c];
+        if (relres) relres[c] = rel_c[c];
+        if (rr0[c] > 0.0 && rel_c[c] > tol) all = false;
+    }
+    if (!all) {
+        h->err = "a right-hand side reached maxit before the tolerance";
+        return AMGH_ERR_NOT_CONVERGED;
+    }
+    return AMGH_OK;
+}
+
+}  // namespace amgh
+
 // =============================================================================================
 // C-ABI
 // =============================================================================================
@@ -1393,6 +1709,22 @@ static amgh_status guarded(amgh_ctx* h, F&& fn) {
     }
 }
 
+template <class F>
+static amgh_status mlp_guarded(amgh_mlp m, F&& fn) {
+    try {
+        return fn();
+    } catch (const StatusError& e) {
+        m->err = e.msg;
+        return e.st;
+    } catch (const CudaError& e) {
+        m->err = std::string("CUDA error ") + cudaGetErrorString(e.code) + " in " + e.where;
+        return AMGH_ERR_CUDA;
+    } catch (const std::bad_alloc&) {
+        m->err = "host allocation failed";
+        return AMGH_ERR_OOM;
+    }
+}
+
 extern "C" {
 
 void amgh_default_params(amgh_params* p) {
@@ -1406,6 +1738,9 @@ void amgh_default_params(amgh_params* p) {
     p->theta = 0.25;
     p->stall_ratio = 0.9;
     p->stream = nullptr;
+    p->dense_tail = 2048;
+    p->mlp = nullptr;
+    p->rho_ref = 0.0;
 }
 
 amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params, amgh_handle* out) {
@@ -1430,10 +1765,72 @@ amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* 
         setup_impl(h, A, G);
         return AMGH_OK;
     });
+    if (st == AMGH_ERR_NOT_SPD && h->interp_used == AMGH_INTERP_LEARNED) {
+        // a predicted P whose coarse levels lost definiteness: the exact local solves instead
+        amgh_params pe = h->prm;
+        pe.interp = AMGH_INTERP_LOCAL;
+        pe.mlp = nullptr;
+        delete h;
+        return amgh_setup(A, G, &pe, out);
+    }
     if (st != AMGH_OK) {
         g_setup_error = h->err;
         delete h;
         return st;
+    }
+    if (h->interp_used == AMGH_INTERP_LEARNED) {
+        // keep the learned interpolation only while its measured convergence factor stays within
+        // 10% of the exact local solves' (a stored reference, or an exact setup measured here)
+        st = guarded(h, [&] {
+            h->rho_used = measure_rho(h);
+            return AMGH_OK;
+        });
+        double rho_ex = h->prm.rho_ref;
+        amgh_ctx* ex = nullptr;
+        if (st == AMGH_OK && !(rho_ex > 0.0)) {
+            amgh_params pe = h->prm;
+            pe.interp = AMGH_INTERP_LOCAL;
+            pe.mlp = nullptr;
+            amgh_handle eh = nullptr;
+            st = amgh_setup(A, G, &pe, &eh);
+            ex = eh;
+            if (st == AMGH_OK) {
+                st = guarded(ex, [&] {
+                    rho_ex = measure_rho(ex);
+                    return AMGH_OK;
+                });
+            }
+        }
+        if (st != AMGH_OK) {
+            g_setup_error = ex ? ex->err : h->err;
+            delete ex;
+            delete h;
+            return st;
+        }
+        h->rho_exact = rho_ex;
+        if (h->rho_used > 1.1 * rho_ex) {
+            if (!ex) {
+                amgh_params pe = h->prm;
+                pe.interp = AMGH_INTERP_LOCAL;
+                pe.mlp = nullptr;
+                amgh_handle eh = nullptr;
+                st = amgh_setup(A, G, &pe, &eh);
+                if (st != AMGH_OK) {
+                    delete h;
+                    return st;
+                }
+                ex = eh;
+                ex->rho_used = measure_rho(ex);
+            } else {
+                ex->rho_used = rho_ex;
+            }
+            ex->rho_exact = rho_ex;
+            ex->interp_used = AMGH_INTERP_LOCAL;
+            delete h;
+            *out = ex;
+            return AMGH_OK;
+        }
+        delete ex;
     }
     *out = h;
     return AMGH_OK;
@@ -1540,6 +1937,34 @@ amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol
     return guarded(h, [&] { return amg_impl(h, f, x, tol, maxit, iters, relres); });
 }
 
+amgh_status amgh_pcg_solve_multi(amgh_handle h, const double* F, double* X, int k, double tol, int maxit, int* iters,
+                                 double* relres) {
+    if (!h || !F || !X || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] { return pcg_multi_impl(h, F, X, k, tol, maxit, iters, relres); });
+}
+
+amgh_status amgh_vcycle_multi(amgh_handle h, const double* Rin, double* Zout, int k) {
+    if (!h || !Rin || !Zout || h->structure_only || k < 1 || k > 4096) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        if (!is_device_ptr(Rin) || !is_device_ptr(Zout))
+            throw StatusError{AMGH_ERR_INVALID_ARG, "multi-RHS V-cycle takes device pointers"};
+        cudaStream_t s = h->s;
+        const int64_t n = h->hl[0].A.nrows;
+        const int KP = ((k + 31) / 32) * 32;
+        if (!h->meng) {
+            h->meng.reset(new MultiEngine());
+            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
+        }
+        MultiEngine& M = *h->meng;
+        M.ensure_width(KP);
+        launch_to_rowmajor(Rin, n, k, KP, M.L[0].F.p, s);
+        M.vcycle_from(0, s);
+        launch_to_colmajor(M.L[0].X.p, n, k, KP, Zout, s);
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return AMGH_OK;
+    });
+}
+
 amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
     if (!h || !info || h->structure_only) return AMGH_ERR_INVALID_ARG;
     return guarded(h, [&] {
@@ -1563,6 +1988,11 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
         info->setup_host_ms = h->host_ms;
         info->setup_device_ms = h->dev_ms;
         auto* e = static_cast<Engine*>(h->eng.get());
+        info->dense_tail = h->dense_tail_level;
+        info->interp_used = h->interp_used;
+        info->rho = h->rho_used;
+        info->rho_exact = h->rho_exact;
+        info->interp_ms = h->interp_ms;
         for (int l = 0; l < nlev && l < 32 && l < (int)e->choice.size(); ++l) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
@@ -1672,6 +2102,158 @@ amgh_status amgh_kernel_stats(amgh_handle h, int64_t* launches, double* total_ms
 }
 
 int64_t amgh_launch_count(amgh_handle) { return launch_counter().load(); }
+
+amgh_status amgh_mlp_create(uint64_t seed, amgh_mlp* out) {
+    if (!out) return AMGH_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto* m = new (std::nothrow) amgh_mlp_ctx();
+    if (!m) return AMGH_ERR_OOM;
+    try {
+        AMGH_CUDA(cudaStreamCreate(&m->s));
+        mlp_init(m->net, seed, m->s);
+        AMGH_CUDA(cudaStreamSynchronize(m->s));
+    } catch (const CudaError& e) {
+        g_setup_error = std::string("CUDA error ") + cudaGetErrorString(e.code) + " in " + e.where;
+        delete m;
+        return AMGH_ERR_CUDA;
+    }
+    *out = m;
+    return AMGH_OK;
+}
+
+amgh_status amgh_mlp_add_samples(amgh_mlp m, amgh_handle h) {
+    if (!m || !h || h->structure_only || h->hl.size() < 2) return AMGH_ERR_INVALID_ARG;
+    amgh_status st = guarded(h, [&] {
+        if (h->interp_used != AMGH_INTERP_LOCAL)
+            throw StatusError{AMGH_ERR_INVALID_ARG, "samples come from a hierarchy built with exact local solves"};
+        const Coarsening& cz = h->hl[0].cz;
+        const int nc = (int)cz.edges.size();
+        int maxp = 0;
+        std::vector<int32_t> e4(4 * (size_t)nc);
+        for (int c = 0; c < nc; ++c) {
+            e4[4 * c] = cz.edges[c].d1;
+            e4[4 * c + 1] = cz.edges[c].s1;
+            e4[4 * c + 2] = cz.edges[c].d2;
+            e4[4 * c + 3] = cz.edges[c].s2;
+            maxp = std::max(maxp, cz.patch_ptr[c + 1] - cz.patch_ptr[c]);
+        }
+        if (maxp > MLP_SLOTS) throw StatusError{AMGH_ERR_UNSUPPORTED, "patches larger than the network's 64 slots"};
+        cudaStream_t s = h->s;
+        DevArray<int32_t> de4, dpp, dpi;
+        DevArray<int64_t> dpos;
+        de4.upload(e4, s);
+        dpp.upload(cz.patch_ptr, s);
+        dpi.upload(cz.patch_idx, s);
+        dpos.upload(cz.patch_pos_P, s);
+        AMGH_CUDA(cudaStreamSynchronize(m->s));
+        MlpNet& net = m->net;
+        mlp_reserve(net, net.nsamples + nc, s);
+        launch_mlp_features(h->A64[0], 0, nc, de4.p, dpp.p, dpi.p, h->P64[0].val.p, dpos.p,
+                            net.X.p + net.nsamples * MLP_DIN, net.T.p + net.nsamples * MLP_SLOTS,
+                            net.M.p + net.nsamples * MLP_SLOTS, s);
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        net.nsamples += nc;
+        return AMGH_OK;
+    });
+    if (st != AMGH_OK) m->err = h->err;
+    return st;
+}
+
+int64_t amgh_mlp_num_samples(amgh_mlp m) { return m ? m->net.nsamples : 0; }
+
+amgh_status amgh_mlp_train(amgh_mlp m, int epochs, int batch, double lr, uint64_t seed, double* final_loss) {
+    if (!m || epochs < 0 || batch < 1 || !(lr > 0)) return AMGH_ERR_INVALID_ARG;
+    return mlp_guarded(m, [&] {
+        double L = 0.0;
+        for (int e = 0; e < epochs; ++e) L = mlp_epoch(m->net, batch, (float)lr, seed + (uint64_t)e, m->s);
+        if (final_loss) *final_loss = L;
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_mlp_params(amgh_mlp m, float* out, float* in, int64_t* count) {
+    if (!m) return AMGH_ERR_INVALID_ARG;
+    return mlp_guarded(m, [&] {
+        const int64_t n = m->net.count();
+        if (count) *count = n;
+        if (in) AMGH_CUDA(cudaMemcpyAsync(m->net.params.p, in, sizeof(float) * n, cudaMemcpyHostToDevice, m->s));
+        if (out) AMGH_CUDA(cudaMemcpyAsync(out, m->net.params.p, sizeof(float) * n, cudaMemcpyDeviceToHost, m->s));
+        AMGH_CUDA(cudaStreamSynchronize(m->s));
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_mlp_loss_grad(amgh_mlp m, const float* X, const float* T, const float* M, int nb, double* loss,
+                               float* grad) {
+    if (!m || !X || !T || !M || nb < 1) return AMGH_ERR_INVALID_ARG;
+    return mlp_guarded(m, [&] {
+        cudaStream_t s = m->s;
+        MlpNet& net = m->net;
+        DevArray<float> dX, dT, dM;
+        dX.upload(X, (size_t)nb * net.d_in, s);
+        dT.upload(T, (size_t)nb * net.d_out, s);
+        dM.upload(M, (size_t)nb * net.d_out, s);
+        const double L = mlp_loss_grad(net, dX.p, dT.p, dM.p, nb, s);
+        if (loss) *loss = L;
+        if (grad) AMGH_CUDA(cudaMemcpyAsync(grad, net.grads.p, sizeof(float) * net.count(), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_mlp_predict(amgh_mlp m, const float* X, int64_t n, float* Y) {
+    if (!m || !X || !Y || n < 0) return AMGH_ERR_INVALID_ARG;
+    return mlp_guarded(m, [&] {
+        cudaStream_t s = m->s;
+        DevArray<float> dX, dY;
+        dX.upload(X, (size_t)n * m->net.d_in, s);
+        dY.alloc((size_t)n * m->net.d_out);
+        mlp_forward(m->net, dX.p, n, dY.p, s);
+        AMGH_CUDA(cudaMemcpyAsync(Y, dY.p, sizeof(float) * n * m->net.d_out, cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return AMGH_OK;
+    });
+}
+
+amgh_status amgh_mlp_features(amgh_handle h, float* X, float* T, float* M, int64_t* n) {
+    if (!h || h->structure_only || h->hl.size() < 2) return AMGH_ERR_INVALID_ARG;
+    return guarded(h, [&] {
+        const Coarsening& cz = h->hl[0].cz;
+        const int nc = (int)cz.edges.size();
+        if (n) *n = nc;
+        if (!X && !T && !M) return AMGH_OK;
+        cudaStream_t s = h->s;
+        std::vector<int32_t> e4(4 * (size_t)nc);
+        for (int c = 0; c < nc; ++c) {
+            e4[4 * c] = cz.edges[c].d1;
+            e4[4 * c + 1] = cz.edges[c].s1;
+            e4[4 * c + 2] = cz.edges[c].d2;
+            e4[4 * c + 3] = cz.edges[c].s2;
+            if (cz.patch_ptr[c + 1] - cz.patch_ptr[c] > MLP_SLOTS)
+                throw StatusError{AMGH_ERR_UNSUPPORTED, "patches larger than the network's 64 slots"};
+        }
+        DevArray<int32_t> de4, dpp, dpi;
+        DevArray<int64_t> dpos;
+        de4.upload(e4, s);
+        dpp.upload(cz.patch_ptr, s);
+        dpi.upload(cz.patch_idx, s);
+        dpos.upload(cz.patch_pos_P, s);
+        DevArray<float> dX, dT, dM;
+        dX.alloc((size_t)nc * MLP_DIN);
+        dT.alloc((size_t)nc * MLP_SLOTS);
+        dM.alloc((size_t)nc * MLP_SLOTS);
+        launch_mlp_features(h->A64[0], 0, nc, de4.p, dpp.p, dpi.p, h->P64[0].val.p, dpos.p, dX.p, dT.p, dM.p, s);
+        if (X) AMGH_CUDA(cudaMemcpyAsync(X, dX.p, sizeof(float) * dX.n, cudaMemcpyDeviceToHost, s));
+        if (T) AMGH_CUDA(cudaMemcpyAsync(T, dT.p, sizeof(float) * dT.n, cudaMemcpyDeviceToHost, s));
+        if (M) AMGH_CUDA(cudaMemcpyAsync(M, dM.p, sizeof(float) * dM.n, cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return AMGH_OK;
+    });
+}
+
+const char* amgh_mlp_last_error(amgh_mlp m) { return m ? m->err.c_str() : g_setup_error.c_str(); }
+
+void amgh_mlp_destroy(amgh_mlp m) { delete m; }
 
 const char* amgh_last_error(amgh_handle h) {
     if (!h) return g_setup_error.c_str();

@@ -1,0 +1,300 @@
+// Multi-right-hand-side kernels (FP64): K systems that share the matrix, vectors row-major with a
+// padded width KP (a multiple of 32).  A warp owns a matrix row; its lanes own KP/32 consecutive
+// columns each, so every gathered vector row is one coalesced read and each nonzero is read once
+// for all K right-hand sides.
+#include <algorithm>
+
+#include "multi.cuh"
+#include "star_invert.cuh"
+
+namespace amgh {
+
+namespace {
+
+// row entries are read 32 at a time by the lanes and broadcast by shuffles, so that the gathers
+// of several entries are in flight together
+template <int KPL>
+__device__ __forceinline__ void row_times_block(int rb, int re, const int32_t* __restrict__ idx,
+                                                const double* __restrict__ val, int KP, int cb, int lane,
+                                                const double* X, double (&acc)[KPL]) {
+    for (int e0 = rb; e0 < re; e0 += 32) {
+        const int e = e0 + lane;
+        const int myc = e < re ? idx[e] : 0;
+        const double myv = e < re ? val[e] : 0.0;
+        const int cnt = min(32, re - e0);
+#pragma unroll 8
+        for (int q = 0; q < cnt; ++q) {
+            const int c = __shfl_sync(0xffffffffu, myc, q);
+            const double v = __shfl_sync(0xffffffffu, myv, q);
+            const double* xr = X + (int64_t)c * KP + cb + lane * KPL;
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) acc[j] = fma(v, xr[j], acc[j]);
+        }
+    }
+}
+
+template <int KPL, int MODE>
+__global__ void __launch_bounds__(256) spmm_kernel(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                                   const double* __restrict__ val, int KP, const double* __restrict__ X,
+                                                   const double* __restrict__ F, const double* __restrict__ dinv,
+                                                   double* __restrict__ Y) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int cb = blockIdx.y * 32 * KPL;
+    double acc[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) acc[j] = 0.0;
+    row_times_block<KPL>(ptr[row], ptr[row + 1], idx, val, KP, cb, lane, X, acc);
+    const int64_t o = (int64_t)row * KP + cb + lane * KPL;
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) {
+        if (MODE == MM_AX) Y[o + j] = acc[j];
+        else if (MODE == MM_RESID) Y[o + j] = F[o + j] - acc[j];
+        else if (MODE == MM_L1) Y[o + j] = X[o + j] + dinv[row] * (F[o + j] - acc[j]);
+        else Y[o + j] += acc[j];
+    }
+}
+
+// columns per lane: the largest of 8, 4, 2, 1 that divides KP / 32
+inline int lane_width(int KP) {
+    const int m = KP / 32;
+    for (int k : {8, 4, 2}) if (m % k == 0) return k;
+    return 1;
+}
+
+template <int MODE>
+void spmm_mode(const DevCSR& M, int KP, const double* X, const double* F, const double* dinv, double* Y, cudaStream_t s) {
+    const int kpl = lane_width(KP);
+    dim3 grid((unsigned)(((int64_t)M.nrows * 32 + 255) / 256), (unsigned)(KP / (32 * kpl)));
+    switch (kpl) {
+        case 1: spmm_kernel<1, MODE><<<grid, 256, 0, s>>>(M.nrows, M.ptr.p, M.idx.p, M.val.p, KP, X, F, dinv, Y); break;
+        case 2: spmm_kernel<2, MODE><<<grid, 256, 0, s>>>(M.nrows, M.ptr.p, M.idx.p, M.val.p, KP, X, F, dinv, Y); break;
+        case 4: spmm_kernel<4, MODE><<<grid, 256, 0, s>>>(M.nrows, M.ptr.p, M.idx.p, M.val.p, KP, X, F, dinv, Y); break;
+        default: spmm_kernel<8, MODE><<<grid, 256, 0, s>>>(M.nrows, M.ptr.p, M.idx.p, M.val.p, KP, X, F, dinv, Y); break;
+    }
+}
+
+// One colour of the multi-RHS Schwarz sweep: a CTA per (star, chunk of 32 KPL columns), a warp
+// per row of the star.  Each warp forms F - A X for its row on the chunk into shared memory; after
+// a barrier each warp adds its row of A_BB^{-1} applied to the star's residuals.
+template <int KPL>
+__global__ void __launch_bounds__(256) schwarz_multi_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                                            const double* __restrict__ Aval, const int32_t* __restrict__ stars,
+                                                            const int32_t* __restrict__ sptr, const int32_t* __restrict__ sidx,
+                                                            const int64_t* __restrict__ ioff, const double* __restrict__ inv,
+                                                            int KP, const double* __restrict__ F, double* __restrict__ X) {
+    extern __shared__ double R[];   // b x (32 KPL)
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = stars[blockIdx.x];
+    const int cb = blockIdx.y * 32 * KPL;
+    const int b0 = sptr[j], b = sptr[j + 1] - b0;
+    for (int q = wl; q < b; q += MR_WARPS) {
+        const int row = sidx[b0 + q];
+        double acc[KPL];
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) acc[t] = 0.0;
+        row_times_block<KPL>(Aptr[row], Aptr[row + 1], Aidx, Aval, KP, cb, lane, X, acc);
+        const double* fr = F + (int64_t)row * KP + cb + lane * KPL;
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) R[q * 32 * KPL + lane * KPL + t] = fr[t] - acc[t];
+    }
+    __syncthreads();
+    const double* iv = inv + ioff[j];
+    for (int q = wl; q < b; q += MR_WARPS) {
+        const int row = sidx[b0 + q];
+        double d[KPL];
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) d[t] = 0.0;
+        for (int k = 0; k < b; ++k) {
+            const double a = iv[q * b + k];
+#pragma unroll
+            for (int t = 0; t < KPL; ++t) d[t] = fma(a, R[k * 32 * KPL + lane * KPL + t], d[t]);
+        }
+        double* xr = X + (int64_t)row * KP + cb + lane * KPL;
+#pragma unroll
+        for (int t = 0; t < KPL; ++t) xr[t] += d[t];
+    }
+}
+
+__global__ void star_inverse_rm_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                       const double* __restrict__ Aval, int nstars, const int32_t* __restrict__ star_ptr,
+                                       const int32_t* __restrict__ star_idx, const int64_t* __restrict__ ioff,
+                                       double* __restrict__ inv, int* err_flag) {
+    __shared__ double sm[2][2][32 * 33];
+    __shared__ double fac[2][32];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 2 + wl;
+    if (j >= nstars) return;
+    const int b0 = star_ptr[j], b = star_ptr[j + 1] - b0;
+    if (b == 0) return;
+    const bool ok = star_invert(Aptr, Aidx, Aval, star_idx, b0, b, sm[wl][0], sm[wl][1], fac[wl]);
+    if (!ok && lane == 0) atomicExch(err_flag, 1);
+    if (lane < b)
+        for (int k = 0; k < b; ++k) inv[ioff[j] + lane * b + k] = sm[wl][1][lane * 33 + k];
+}
+
+__global__ void dense_apply_multi_kernel(const double* __restrict__ Ainv, int n, int KP, const double* __restrict__ X,
+                                         double* __restrict__ Y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * KP) return;
+    const int i = (int)(t / KP), c = (int)(t % KP);
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s = fma(Ainv[(int64_t)i * n + k], X[(int64_t)k * KP + c], s);
+    Y[t] = s;
+}
+
+__global__ void to_rowmajor_kernel(const double* __restrict__ in, int64_t n, int k, int KP, double* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * KP) return;
+    const int64_t i = t / KP;
+    const int c = (int)(t % KP);
+    out[t] = c < k ? in[(int64_t)c * n + i] : 0.0;
+}
+
+__global__ void to_colmajor_kernel(const double* __restrict__ in, int64_t n, int k, int KP, double* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * (int64_t)k) return;
+    const int c = (int)(t / n);
+    const int64_t i = t % n;
+    out[t] = in[i * KP + c];
+}
+
+constexpr int CD_BLOCKS = 304;
+
+// per-column partial sums over a fixed set of row ranges (deterministic order)
+__global__ void coldot_partial_kernel(const double* __restrict__ a, const double* __restrict__ b, int64_t n, int KP,
+                                      double* __restrict__ partial) {
+    extern __shared__ double sh[];
+    const int tid = threadIdx.x;
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = blockIdx.x * rows_per, r1 = std::min<int64_t>(n, r0 + rows_per);
+    for (int c0 = 0; c0 < KP; c0 += blockDim.x) {
+        const int c = c0 + tid;
+        double s = 0.0;
+        if (c < KP)
+            for (int64_t r = r0; r < r1; ++r) s = fma(a[r * KP + c], b[r * KP + c], s);
+        if (c < KP) partial[(int64_t)blockIdx.x * KP + c] = s;
+    }
+    (void)sh;
+}
+
+__global__ void coldot_final_kernel(const double* __restrict__ partial, int nb, int KP, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= KP) return;
+    double s = 0.0;
+    for (int q = 0; q < nb; ++q) s += partial[(int64_t)q * KP + c];
+    out[c] = s;
+}
+
+__global__ void mcg_update_kernel(int64_t total, int KP, double* __restrict__ X, double* __restrict__ R,
+                                  double* __restrict__ Rold, const double* __restrict__ P, const double* __restrict__ Q,
+                                  const double* __restrict__ alpha) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const double a = alpha[t % KP];
+        X[t] = fma(a, P[t], X[t]);
+        const double r = R[t];
+        if (Rold) Rold[t] = r;
+        R[t] = fma(-a, Q[t], r);
+    }
+}
+
+__global__ void mp_update_kernel(int64_t total, int KP, double* __restrict__ P, const double* __restrict__ Z,
+                                 const double* __restrict__ beta) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        P[t] = fma(beta[t % KP], P[t], Z[t]);
+}
+
+__global__ void axpy_multi_kernel(int64_t total, double* __restrict__ X, const double* __restrict__ Z) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        X[t] += Z[t];
+}
+
+}  // namespace
+
+void launch_spmm(int mode, const DevCSR& M, int KP, const double* X, const double* F, const double* dinv, double* Y,
+                 cudaStream_t s) {
+    if (M.nrows == 0) return;
+    switch (mode) {
+        case MM_AX: spmm_mode<MM_AX>(M, KP, X, F, dinv, Y, s); break;
+        case MM_RESID: spmm_mode<MM_RESID>(M, KP, X, F, dinv, Y, s); break;
+        case MM_L1: spmm_mode<MM_L1>(M, KP, X, F, dinv, Y, s); break;
+        default: spmm_mode<MM_ADD>(M, KP, X, F, dinv, Y, s); break;
+    }
+    AMGH_LAUNCHED();
+}
+
+void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double* F, double* X, cudaStream_t s) {
+    const int sb = L.colour_star_begin[colour], se = L.colour_star_begin[colour + 1];
+    const int nst = se - sb;
+    if (nst <= 0) return;
+    const int kpl = lane_width(KP);
+    const size_t shm = (size_t)L.bmax * 32 * kpl * 8;   // <= 32 x 256 doubles = 64 KB
+    dim3 grid((unsigned)nst, (unsigned)(KP / (32 * kpl)));
+    const int32_t* stars = L.star_list.p + sb;
+#define AMGH_SM(K)                                                                                                     \
+    AMGH_CUDA(cudaFuncSetAttribute(schwarz_multi_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm)); \
+    schwarz_multi_kernel<K><<<grid, 256, shm, s>>>(L.A->ptr.p, L.A->idx.p, L.A->val.p, stars, L.star_ptr.p,           \
+                                                   L.star_idx.p, L.inv_off.p, L.inv.p, KP, F, X);
+    switch (kpl) {
+        case 1: AMGH_SM(1) break;
+        case 2: AMGH_SM(2) break;
+        case 4: AMGH_SM(4) break;
+        default: AMGH_SM(8) break;
+    }
+#undef AMGH_SM
+    AMGH_LAUNCHED();
+}
+
+void launch_star_inverse_rowmajor(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
+                                  const int64_t* inv_off, double* inv, int* err_flag, cudaStream_t s) {
+    if (nstars == 0) return;
+    star_inverse_rm_kernel<<<(nstars + 1) / 2, 64, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, nstars, star_ptr, star_idx, inv_off,
+                                                           inv, err_flag);
+    AMGH_LAUNCHED();
+}
+
+void launch_dense_apply_multi(const double* Ainv, int n, int KP, const double* X, double* Y, cudaStream_t s) {
+    const int64_t total = (int64_t)n * KP;
+    if (total == 0) return;
+    dense_apply_multi_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Ainv, n, KP, X, Y);
+    AMGH_LAUNCHED();
+}
+
+void launch_to_rowmajor(const double* in, int64_t n, int k, int KP, double* out, cudaStream_t s) {
+    const int64_t total = n * KP;
+    if (total == 0) return;
+    to_rowmajor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(in, n, k, KP, out);
+    AMGH_LAUNCHED();
+}
+
+void launch_to_colmajor(const double* in, int64_t n, int k, int KP, double* out, cudaStream_t s) {
+    const int64_t total = n * k;
+    if (total == 0) return;
+    to_colmajor_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(in, n, k, KP, out);
+    AMGH_LAUNCHED();
+}
+
+void launch_coldot(const double* a, const double* b, int64_t n, int KP, double* partial, double* out, cudaStream_t s) {
+    coldot_partial_kernel<<<CD_BLOCKS, 256, 0, s>>>(a, b, n, KP, partial);
+    AMGH_LAUNCHED();
+    coldot_final_kernel<<<(KP + 255) / 256, 256, 0, s>>>(partial, CD_BLOCKS, KP, out);
+    AMGH_LAUNCHED();
+}
+
+void launch_mcg_update(int64_t n, int KP, double* X, double* R, double* Rold, const double* P, const double* Q,
+                       const double* alpha, cudaStream_t s) {
+    mcg_update_kernel<<<608, 256, 0, s>>>(n * KP, KP, X, R, Rold, P, Q, alpha);
+    AMGH_LAUNCHED();
+}
+
+void launch_mp_update(int64_t n, int KP, double* P, const double* Z, const double* beta, cudaStream_t s) {
+    mp_update_kernel<<<608, 256, 0, s>>>(n * KP, KP, P, Z, beta);
+    AMGH_LAUNCHED();
+}
+
+void launch_axpy_multi(int64_t n, int KP, double* X, const double* Z, cudaStream_t s) {
+    axpy_multi_kernel<<<608, 256, 0, s>>>(n * KP, X, Z);
+    AMGH_LAUNCHED();
+}
+
+}  // namespace amgh

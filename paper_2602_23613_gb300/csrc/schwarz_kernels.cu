@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include "star_invert.cuh"
 #include "vcycle_kernels.h"
 
 namespace amgh {
@@ -96,53 +97,6 @@ __global__ void slotL_fill_kernel(int nctas, int L, const int32_t* __restrict__ 
     }
 }
 
-__device__ __forceinline__ int bsearch_i32(const int32_t* a, int lo, int hi, int key) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int v = a[mid];
-        if (v == key) return mid;
-        if (v < key) lo = mid + 1; else hi = mid;
-    }
-    return -1;
-}
-
-// gather A_BB into M (b x b, stride 33) and invert it by Gauss-Jordan (SPD: no pivoting) into I;
-// one warp per star.  Returns false (on every lane) if a pivot was not positive.
-__device__ bool star_invert(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
-                            const double* __restrict__ Aval, const int32_t* __restrict__ sidx, int b0, int b,
-                            double* M, double* I, double* fac) {
-    const int lane = threadIdx.x & 31;
-    for (int r = 0; r < b; ++r)
-        if (lane < b) { M[r * 33 + lane] = 0.0; I[r * 33 + lane] = (r == lane); }
-    __syncwarp();
-    if (lane < b) {
-        const int g = sidx[b0 + lane];
-        for (int q = Aptr[g]; q < Aptr[g + 1]; ++q) {
-            const int c = bsearch_i32(sidx, b0, b0 + b, Aidx[q]);
-            if (c >= 0) M[lane * 33 + (c - b0)] = Aval[q];
-        }
-    }
-    __syncwarp();
-    bool ok = true;
-    for (int k = 0; k < b; ++k) {
-        double piv = M[k * 33 + k];
-        if (!(piv > 0.0)) { ok = false; piv = 1.0; }
-        __syncwarp();
-        if (lane < b) { M[k * 33 + lane] /= piv; I[k * 33 + lane] /= piv; }
-        if (lane < b) fac[lane] = M[lane * 33 + k];
-        __syncwarp();
-        if (lane < b)
-            for (int i = 0; i < b; ++i) {
-                if (i == k) continue;
-                const double fi = fac[i];
-                M[i * 33 + lane] -= fi * M[k * 33 + lane];
-                I[i * 33 + lane] -= fi * I[k * 33 + lane];
-            }
-        __syncwarp();
-    }
-    return ok;
-}
-
 template <class V>
 __global__ void star_inverseL_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
                                      const double* __restrict__ Aval, int nstars, const int32_t* __restrict__ star_ptr,
@@ -176,10 +130,9 @@ __global__ void star_kappa_kernel(const int32_t* __restrict__ Aptr, const int32_
     if (b == 0) return;
     double* M = sm[wl][0];
     double* I = sm[wl][1];
-    // ||A_BB||_1 before the elimination overwrites M: lane c sums column c
     const bool ok = star_invert(Aptr, Aidx, Aval, star_idx, b0, b, M, I, fac[wl]);
     if (!ok && lane == 0) atomicExch(err_flag, 1);
-    // re-gather the block for its norm (M now holds the identity)
+    // 1-norms: lane c sums column c of the inverse, and of A_BB re-read from A (M now holds I)
     double acol = 0.0, icol = 0.0;
     if (lane < b) {
         for (int r = 0; r < b; ++r) icol += fabs(I[r * 33 + lane]);

@@ -44,13 +44,17 @@ __global__ void __launch_bounds__(256) sell_kernel(SellView<V> A, const T* __res
     else y[row] += s;
 }
 
+// y = inv x for a dense n x n operator (the coarsest inverse or the dense tail): a warp per row,
+// lanes over the row (coalesced), shuffle reduction
 template <class T>
 __global__ void coarse_apply_kernel(const T* __restrict__ inv, int n, const T* __restrict__ x, T* __restrict__ y) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T s = T(0);
-        for (int k = 0; k < n; ++k) s = fma(inv[(int64_t)i * n + k], x[k], s);
-        y[i] = s;
-    }
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const T* r = inv + (int64_t)row * n;
+    T s = T(0);
+    for (int k = lane; k < n; k += 32) s = fma(r[k], x[k], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[row] = s;
 }
 
 // ---------------- FP64 Krylov vector kernels (fixed grid, deterministic) -----------------------
@@ -198,7 +202,7 @@ void launch_sell(int mode, const Sell<V>& A, const T* x, const T* f, const T* di
 
 template <class T>
 void launch_coarse_apply(const T* inv, int n, const T* x, T* y, cudaStream_t s) {
-    coarse_apply_kernel<T><<<1, 256, 0, s>>>(inv, n, x, y);
+    coarse_apply_kernel<T><<<(n + 7) / 8, 256, 0, s>>>(inv, n, x, y);
     AMGH_LAUNCHED();
 }
 
