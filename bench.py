@@ -37,6 +37,12 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--profile-setup", action="store_true",
+                    help="set up once, then once more between cudaProfilerStart/Stop and exit (for ncu "
+                         "--profile-from-start off); prints no bench line")
+    ap.add_argument("--profile-vcycles", type=int, default=0,
+                    help="set up once, then run this many V-cycles between cudaProfilerStart/Stop and exit "
+                         "(for ncu --profile-from-start off); prints no bench line")
     return ap.parse_args()
 
 
@@ -102,7 +108,7 @@ def peaks():
 def traffic_for(kernel, workload):
     """dram bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "solve_kernels.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "schwarz_kernels.cu"), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -186,7 +192,29 @@ def run_gpu(args, rank, world, local_rank):
     Ad, Gd = dcsr(A), dcsr(G)
     fd = torch.tensor(f, device=dev)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
-    stats = {}
+
+    if args.profile_setup:
+        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        amgh.amgh_destroy(h)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profiled one setup of %s (%d DoFs)" % (args.workload, n), flush=True)
+        return 0
+
+    if args.profile_vcycles > 0:
+        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        amgh.amgh_vcycle(h, fd, xd)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.profile_vcycles):
+            amgh.amgh_vcycle(h, fd, xd)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profiled %d V-cycles of %s (%d DoFs)" % (args.profile_vcycles, args.workload, n), flush=True)
+        return 0
 
     def step(profile):
         h = amgh.amgh_setup(Ad, Gd, precision=prec)

@@ -203,7 +203,13 @@ typedef struct {
     double setup_device_ms; /* device numerics (patch solves, Galerkin product, inverses, tuning) */
     int precision[32];    /* storage precision each level ended up with (AMGH_F64/F32/BF16)   */
     int lanes[32];        /* lanes per row of the level's smoother layout (autotuned)          */
-    int fused[32];        /* 1 if the level's whole Schwarz sweep runs as one launch           */
+    int fused[32];        /* launch mode of the level's Schwarz sweep: 0 one launch per colour
+                             step, 1 one single-CTA launch, 2 one cooperative launch with grid
+                             barriers, 3 the same with chunks staged in shared memory, 4 one
+                             streaming launch per colour step (chunks staged by bulk copies).
+                             The autotuner picks the fastest; AMGH_TUNE=0 disables tuning and
+                             AMGH_SMOOTHER_MODE=colour|stream1|stream2|fused|persistent|staged
+                             restricts it to one mode where the level supports it.            */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
                                (coarsest level: of its matrix)                                  */
     int dense_tail;       /* level whose sub-cycle is applied as a dense operator, or -1       */

@@ -14,6 +14,7 @@
 
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <variant>
 
@@ -99,6 +100,10 @@ struct LevelChoice {
     int prec = AMGH_F64;
     int L_A = 1, L_P = 1, L_PT = 1, L_sm = 1;
     bool fused = false;
+    int persist = 0;   // grid of the cooperative whole-sweep launch, 0: not used
+    bool staged = false;   // that launch stages its chunks in shared memory
+    int stream = 0;        // per-colour streaming launches of at most this many CTAs, 0: not used
+    int stream_bufs = 2;   // their stage buffers per CTA
     double kappa = 0.0;
 };
 
@@ -119,6 +124,12 @@ struct Engine : EngineBase {
     int64_t launches_vc = 0;
 
     ~Engine() override { release_graph(); }
+    void reset_barriers(cudaStream_t s) override {
+        for (auto& v : L)
+            std::visit([&](auto& d) {
+                if (d.sm.bar.p) d.sm.bar.zero(s);
+            }, v);
+    }
 
     bool level0_double() const { return std::holds_alternative<LevelX<double, double>>(L[0]); }
     double* in64() override {
@@ -167,10 +178,13 @@ struct Engine : EngineBase {
     void sweep(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
         using V = typename Lv::VT;
         using T = typename Lv::TT;
-        if (d.sm.fused) {
+        if (d.sm.fused || d.sm.persist > 0) {
             double by = 0;
             for (int c : colour_sequence(d.sm.ncolours)) by += bytes_colour(d, c);
-            timed(K_SCHWARZ, l, by, s, [&] { launch_schwarz_fused<V, T>(d.sm, d.f.p, d.x.p, s); });
+            timed(K_SCHWARZ, l, by, s, [&] {
+                if (d.sm.fused) launch_schwarz_fused<V, T>(d.sm, d.f.p, d.x.p, s);
+                else launch_schwarz_persistent<V, T>(d.sm, d.f.p, d.x.p, s);
+            });
             cnt++;
             return;
         }
@@ -535,6 +549,9 @@ struct amgh_ctx {
     }
     double* hscal = nullptr;
     DevArray<int> errflag;
+    DevArray<int> waitflag;          // raised by a device-side barrier wait that gave up
+    DevArray<int> symflag;           // overflow flag of the symbolic product
+    int nsm = 0;
     Profiler prof;
     int64_t launches = 0;
     double host_ms = 0, dev_ms = 0;
@@ -643,9 +660,27 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
     launch_sellL_fill<V>(dev, S, s);
 }
 
+// name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
+static std::string smoother_mode_name(const LevelChoice& m) {
+    if (m.fused) return "fused";
+    if (m.persist > 0) return m.staged ? "staged" : "persistent";
+    if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
+    return "colour";
+}
+
+// launch mode of a built smoother (the layout is the same for every mode)
 template <class V>
-static void build_smoother(amgh_ctx* h, int l, int L, bool fused, SmootherL<V>& sm, std::vector<int64_t>* cn,
-                           std::vector<int64_t>* ci, std::vector<int64_t>* cr) {
+static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
+    sm.fused = m.fused;
+    sm.persist = m.fused ? 0 : m.persist;
+    sm.staged = sm.persist > 0 && m.staged;
+    sm.stream_grid = (m.fused || sm.persist > 0) ? 0 : m.stream;
+    sm.stream_bufs = m.stream_bufs;
+}
+
+template <class V>
+static void build_smoother(amgh_ctx* h, int l, int L, bool fused, int persist, bool staged, SmootherL<V>& sm,
+                           std::vector<int64_t>* cn, std::vector<int64_t>* ci, std::vector<int64_t>* cr) {
     cudaStream_t s = h->s;
     const LevelHost& hl = h->hl[l];
     const StarLayout& st = hl.stars;
@@ -656,6 +691,10 @@ static void build_smoother(amgh_ctx* h, int l, int L, bool fused, SmootherL<V>& 
     sm.bmax = std::max(1, st.max_block);
     sm.ncolours = st.ncolours;
     sm.fused = fused;
+    sm.persist = fused ? 0 : persist;
+    sm.bar.alloc(4);
+    sm.bar.zero(s);
+    sm.wait_err = h->waitflag.p;
     sm.colour_cta_begin = pk.colour_cta_begin;
     sm.colour_cta_begin_d.upload(pk.colour_cta_begin, s);
     std::vector<int32_t> seq;
@@ -673,6 +712,9 @@ static void build_smoother(amgh_ctx* h, int l, int L, bool fused, SmootherL<V>& 
     sm.rows.nslices = (int)(sp.size() - 1);
     sm.rows.stored = sp.back();
     sm.rows.slice_ptr.upload(sp, s);
+    sm.wmax = 0;
+    for (size_t q = 0; q + 1 < sp.size(); ++q) sm.wmax = std::max<int>(sm.wmax, (int)((sp[q + 1] - sp[q]) / 32));
+    sm.staged = staged && sm.persist > 0;
     sm.rows.col.alloc(sm.rows.stored);
     sm.rows.val.alloc(sm.rows.stored);
     launch_slotL_fill<V>(h->A64[l], sm, s);
@@ -724,6 +766,56 @@ static float time_best(cudaStream_t s, int reps, F&& fn) {
     return best;
 }
 
+// cooperative whole-sweep launches need the device's support, inside captured graphs too
+static bool cooperative_ok(amgh_ctx* h) {
+    static std::mutex mu;
+    static std::map<int, bool> known;
+    int dev = 0;
+    AMGH_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = known.find(dev);
+    if (it == known.end()) it = known.emplace(dev, cooperative_capture_works()).first;
+    (void)h;
+    return it->second;
+}
+
+// read and clear the flag a device-side barrier wait raises when it gives up
+static bool take_wait_flag(amgh_ctx* h) {
+    int flag = 0;
+    AMGH_CUDA(cudaMemcpyAsync(&flag, h->waitflag.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+    if (flag) h->waitflag.zero(h->s);
+    return flag != 0;
+}
+
+// after a solve: a barrier wait that gave up invalidates the result; reset the barriers and report
+static void check_wait(amgh_ctx* h) {
+    if (!take_wait_flag(h)) return;
+    if (h->eng) h->eng->reset_barriers(h->s);
+    AMGH_CUDA(cudaStreamSynchronize(h->s));
+    throw StatusError{AMGH_ERR_TIMEOUT, "a grid barrier of the Schwarz sweep gave up waiting; the result is invalid"};
+}
+
+// time fn() as it runs in the V-cycle: captured once into a graph, best of `reps` replays after
+// one warm-up replay, in ms
+template <class F>
+static float time_best_graph(cudaStream_t s, int reps, F&& fn) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    AMGH_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    fn();
+    AMGH_CUDA(cudaStreamEndCapture(s, &g));
+    const cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+    if (ie != cudaSuccess) {
+        cudaGraphDestroy(g);
+        throw CudaError{ie, "instantiating a tuning graph"};
+    }
+    const float ms = time_best(s, reps, [&] { AMGH_CUDA(cudaGraphLaunch(ge, s)); });
+    cudaGraphExecDestroy(ge);
+    cudaGraphDestroy(g);
+    return ms;
+}
+
 static bool tuning_enabled() {
     const char* e = std::getenv("AMGH_TUNE");
     return !(e && std::string(e) == "0");
@@ -764,7 +856,9 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
     const double avg = d.n ? (double)d.nnzA / d.n : 1.0;
     const double avgPT = hl.cz.PT.nrows ? (double)hl.cz.PT.nnz() / hl.cz.PT.nrows : 1.0;
-    const std::string key = std::to_string(sizeof(V)) + "|" + std::to_string(d.n) + "|" + std::to_string(d.nnzA) +
+    const char* forced = std::getenv("AMGH_SMOOTHER_MODE");
+    const std::string key = std::string(forced ? forced : "") + "|" + std::to_string(sizeof(V)) + "|" +
+                            std::to_string(d.n) + "|" + std::to_string(d.nnzA) +
                             "|" + std::to_string(hl.stars.ncolours) + "|" + std::to_string(hl.cz.P.nnz());
     bool cached = false;
     if (tuning_enabled()) {
@@ -822,28 +916,101 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     build_sellL<V>(hl.cz.P, h->P64[l], ch.L_P, d.P, s);
     build_sellL<V>(hl.cz.PT, h->PT64[l], ch.L_PT, d.PT, s);
     // ---- smoother ----
+    // Each lane count is built once; its launch modes only differ in how the same layout is
+    // swept: per-colour launches, per-colour streaming launches (chunks staged in shared memory),
+    // one single-CTA launch (small levels), one cooperative launch over several grid sizes, and
+    // one cooperative launch with staged chunks (levels with many colours).  Every candidate is
+    // timed as a captured graph, the way the V-cycle runs it.
     if (tune) {
         float best = 1e30f;
         const bool small = d.nnzA <= 3000000 && d.n <= 60000;
         for (int Lc : lane_candidates(avg, d.n, hl.stars.max_block)) {
-            for (int fz = 0; fz <= (small ? 1 : 0); ++fz) {
-                SmootherL<V> cand;
-                build_smoother<V>(h, l, Lc, fz != 0, cand, nullptr, nullptr, nullptr);
-                const float ms = time_best(s, 2, [&] {
+            SmootherL<V> cand;
+            build_smoother<V>(h, l, Lc, false, 0, false, cand, nullptr, nullptr, nullptr);
+            int maxc = 1;
+            for (int c = 0; c < cand.ncolours; ++c)
+                maxc = std::max(maxc, cand.colour_cta_begin[c + 1] - cand.colour_cta_begin[c]);
+            std::vector<LevelChoice> modes;
+            LevelChoice m0 = ch;
+            m0.L_sm = Lc;
+            m0.fused = false;
+            m0.persist = 0;
+            m0.staged = false;
+            m0.stream = 0;
+            modes.push_back(m0);
+            for (int nb : {2, 1}) {
+                const int scap = schwarz_stream_cap<V, T>(cand, nb);
+                for (int g : {scap, 2 * h->nsm, h->nsm}) {
+                    LevelChoice m = m0;
+                    m.stream = std::min(g, scap);
+                    m.stream_bufs = nb;
+                    if (m.stream > 0 && std::none_of(modes.begin(), modes.end(), [&](const LevelChoice& q) {
+                            return q.stream == m.stream && q.stream_bufs == nb;
+                        }))
+                        modes.push_back(m);
+                }
+            }
+            if (small) {
+                LevelChoice m = m0;
+                m.fused = true;
+                modes.push_back(m);
+            }
+            if (cand.ncolours >= 4 && cooperative_ok(h)) {
+                const int cap = schwarz_persistent_cap<V, T>(Lc);
+                std::vector<int> grids;
+                for (int g : {maxc, 4 * h->nsm, 2 * h->nsm, h->nsm, h->nsm / 2, h->nsm / 4}) {
+                    g = std::min(g, std::min(cap, maxc));
+                    if (g >= 1 && std::find(grids.begin(), grids.end(), g) == grids.end()) grids.push_back(g);
+                }
+                for (int g : grids) {
+                    LevelChoice m = m0;
+                    m.persist = g;
+                    modes.push_back(m);
+                }
+                cand.persist = maxc;
+                if (schwarz_staged_cap<V, T>(cand) >= maxc) {
+                    LevelChoice m = m0;
+                    m.persist = maxc;
+                    m.staged = true;
+                    modes.push_back(m);
+                }
+            }
+            const char* force = std::getenv("AMGH_SMOOTHER_MODE");
+            for (const LevelChoice& m : modes) {
+                if (force && *force && std::string(force) != smoother_mode_name(m)) continue;
+                set_smoother_mode(cand, m);
+                const float ms = time_best_graph(s, 5, [&] {
                     if (cand.fused) {
                         launch_schwarz_fused<V, T>(cand, d.f.p, d.x.p, s);
+                    } else if (cand.persist > 0) {
+                        launch_schwarz_persistent<V, T>(cand, d.f.p, d.x.p, s);
                     } else {
                         for (int c : Engine::colour_sequence(cand.ncolours))
                             launch_schwarz_colourL<V, T>(cand, c, d.f.p, d.x.p, s);
                     }
                 });
-                if (ms < best) { best = ms; ch.L_sm = Lc; ch.fused = fz != 0; }
+                if (take_wait_flag(h)) {   // a bounded wait gave up: never choose this mode
+                    cand.bar.zero(s);
+                    continue;
+                }
+                if (ms < best) {
+                    best = ms;
+                    const double kap = ch.kappa;
+                    ch = m;
+                    ch.kappa = kap;
+                }
             }
         }
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = ch;
     }
-    build_smoother<V>(h, l, ch.L_sm, ch.fused, d.sm, &d.col_nnz, &d.col_inv, &d.col_rows);
+    build_smoother<V>(h, l, ch.L_sm, false, 0, false, d.sm, &d.col_nnz, &d.col_inv, &d.col_rows);
+    // a mode whose shared-memory staging no longer fits (another device) falls back to per-colour
+    // launches; the capacity queries also raise the kernels' shared-memory limits
+    d.sm.persist = ch.persist;
+    if (ch.staged && schwarz_staged_cap<V, T>(d.sm) < ch.persist) ch.staged = false;
+    if (ch.stream > 0) ch.stream = std::min(ch.stream, schwarz_stream_cap<V, T>(d.sm, ch.stream_bufs));
+    set_smoother_mode(d.sm, ch);
     AMGH_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1030,7 +1197,22 @@ static void host_structure_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr
     if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
 }
 
+// wall time of setup phases on stderr when AMGH_VERBOSE=1 (the stream is synchronised only then)
+struct DevPhases {
+    bool on = std::getenv("AMGH_VERBOSE") != nullptr;
+    double t = now_ms();
+    void mark(cudaStream_t s, const char* what, int l = -1) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const double now = now_ms();
+        if (l >= 0) std::fprintf(stderr, "[amgh] L%d %-25s %8.1f ms\n", l, what, now - t);
+        else std::fprintf(stderr, "[amgh] %-28s %8.1f ms\n", what, now - t);
+        t = now;
+    }
+};
+
 static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
+    DevPhases ph;
     cudaStream_t s = h->s;
     const auto& prm = h->prm;
     check_params(prm);
@@ -1041,6 +1223,15 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     Params gp = graph_params(prm);
     h->errflag.alloc(1);
     h->errflag.zero(s);
+    h->waitflag.alloc(1);
+    h->waitflag.zero(s);
+    h->symflag.alloc(1);
+    gp.symbolic_galerkin = false;
+    {
+        int dev = 0;
+        AMGH_CUDA(cudaGetDevice(&dev));
+        AMGH_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     DevCSR dA;
     upload_csr(A, dA, s, true);
     for (int l = 0;; ++l) {
@@ -1067,6 +1258,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
         }
         h->host_ms += now_ms() - t0;
+        ph.mark(s, "host graph steps", l);
         if (coarsest) break;
         t0 = now_ms();
         Coarsening& cz = cur.cz;
@@ -1123,16 +1315,40 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 h->interp_ms = now_ms() - ti;
             }
         }
+        ph.mark(s, "P upload + patch solves", l);
+        // Galerkin product: symbolic patterns on the device (the host's when a row overflows the
+        // kernel's set), then the numeric products with their fixed summation order
         DevCSR AP, Ac;
-        upload_csr(cz.AP, AP, s, false);
+        if (!spgemm_symbolic(h->A64[l], P, AP, h->symflag.p, s)) {
+            HostCSR hp = symbolic_product(cur.A, cz.P, nthreads);
+            upload_csr(hp, AP, s, false);
+        }
         launch_ap_numeric(h->A64[l], P, AP, s);
-        upload_csr(cz.Ac, Ac, s, false);
+        if (!spgemm_symbolic(PT, AP, Ac, h->symflag.p, s)) {
+            HostCSR hap;
+            hap.nrows = AP.nrows;
+            hap.ncols = AP.ncols;
+            hap.ptr.resize(AP.nrows + 1);
+            hap.idx.resize(AP.nnz);
+            AMGH_CUDA(cudaMemcpyAsync(hap.ptr.data(), AP.ptr.p, sizeof(int32_t) * (AP.nrows + 1), cudaMemcpyDeviceToHost, s));
+            AMGH_CUDA(cudaMemcpyAsync(hap.idx.data(), AP.idx.p, sizeof(int32_t) * AP.nnz, cudaMemcpyDeviceToHost, s));
+            AMGH_CUDA(cudaStreamSynchronize(s));
+            HostCSR hc = symbolic_product(cz.PT, hap, nthreads);
+            upload_csr(hc, Ac, s, false);
+        }
         launch_ac_numeric(PT, AP, Ac, s);
-        HostCSR An = cz.Ac;   // pattern of the next level
-        An.val.resize(An.nnz());
-        AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * An.nnz(), cudaMemcpyDeviceToHost, s));
+        HostCSR An;   // the next level's matrix, on the host for its graph steps
+        An.nrows = Ac.nrows;
+        An.ncols = Ac.ncols;
+        An.ptr.resize(Ac.nrows + 1);
+        An.idx.resize(Ac.nnz);
+        An.val.resize(Ac.nnz);
+        AMGH_CUDA(cudaMemcpyAsync(An.ptr.data(), Ac.ptr.p, sizeof(int32_t) * (Ac.nrows + 1), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaMemcpyAsync(An.idx.data(), Ac.idx.p, sizeof(int32_t) * Ac.nnz, cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaStreamSynchronize(s));
         h->dev_ms += now_ms() - t0;
+        ph.mark(s, "Galerkin + download", l);
         A = std::move(An);
         G = cz.Gc;
         G.val = cz.Gc.val;
@@ -1148,11 +1364,13 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         launch_coarse_inverse(h->A64.back(), h->cinv64.p, work.p, h->errflag.p, s);
         check_flag(h, "the coarsest factorisation");
     }
+    ph.mark(s, "coarsest inverse");
     {
         auto* e = new Engine();
         h->eng.reset(e);
         e->prof = &h->prof;
         build_engine(h, e);
+        ph.mark(s, "V-cycle engine");
         // the sub-cycle below the first small level is linear in its right-hand side: apply it as
         // one dense operator, computed column block by column block with the multi-RHS V-cycle
         const int nlev = (int)h->hl.size();
@@ -1176,6 +1394,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 launch_convert<float>(h->dense_tail_B.p, e->tail_f.p, (int64_t)nt * nt, s);
             }
             AMGH_CUDA(cudaStreamSynchronize(s));
+            ph.mark(s, "dense tail");
         }
     }
     check_flag(h, "a smoother block");
@@ -1194,6 +1413,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     h->eng->capture(s);
     AMGH_CUDA(cudaStreamSynchronize(s));
     h->dev_ms += now_ms() - t0;
+    ph.mark(s, "outer SpMV + graph capture");
 }
 
 static bool is_device_ptr(const void* p) {
@@ -1877,6 +2097,7 @@ amgh_status amgh_vcycle(amgh_handle h, const double* r, double* z) {
         AMGH_CUDA(cudaStreamSynchronize(h->s));
         harvest(h);
         h->prof.used = 0;
+        check_wait(h);
         return AMGH_OK;
     });
 }
@@ -1887,8 +2108,11 @@ amgh_status amgh_pcg_solve(amgh_handle h, const double* f, double* x, double tol
     return guarded(h, [&] {
         if (maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad tol or maxit"};
         // kernel timing needs the host-driven loop (event nodes cannot sit in conditional bodies)
-        if (h->prof.enabled || maxit < 1 || h->host_loop) return pcg_impl(h, f, x, tol, maxit, iters, relres);
-        return pcg_device_impl(h, f, x, tol, maxit, iters, relres);
+        const amgh_status st = (h->prof.enabled || maxit < 1 || h->host_loop)
+                                   ? pcg_impl(h, f, x, tol, maxit, iters, relres)
+                                   : pcg_device_impl(h, f, x, tol, maxit, iters, relres);
+        check_wait(h);
+        return st;
     });
 }
 
@@ -1914,6 +2138,7 @@ amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* 
         AMGH_CUDA(cudaGraphInstantiate(&GE, G, 0));
         AMGH_CUDA(cudaGraphLaunch(GE, h0->s));
         AMGH_CUDA(cudaStreamSynchronize(h0->s));
+        for (int i = 0; i < nsys; ++i) check_wait(hs[i]);
         amgh_status all = AMGH_OK;
         for (int i = 0; i < nsys; ++i) {
             int it = 0;
@@ -1934,7 +2159,11 @@ amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* 
 amgh_status amgh_amg_solve(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
                            double* relres) {
     if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
-    return guarded(h, [&] { return amg_impl(h, f, x, tol, maxit, iters, relres); });
+    return guarded(h, [&] {
+        const amgh_status st = amg_impl(h, f, x, tol, maxit, iters, relres);
+        check_wait(h);
+        return st;
+    });
 }
 
 amgh_status amgh_pcg_solve_multi(amgh_handle h, const double* F, double* X, int k, double tol, int maxit, int* iters,
@@ -1996,7 +2225,8 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
         for (int l = 0; l < nlev && l < 32 && l < (int)e->choice.size(); ++l) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
-            info->fused[l] = e->choice[l].fused ? 1 : 0;
+            const LevelChoice& cl = e->choice[l];
+            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.staged ? 3 : 2) : cl.stream > 0 ? 4 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
         }
         return AMGH_OK;
@@ -2039,7 +2269,10 @@ amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, i
     if ((which == 1 || which == 3) && !has_coarse) return AMGH_ERR_INVALID_ARG;
     return guarded(h, [&] {
         const auto& L = h->hl[l];
-        const HostCSR& M = which == 0 ? L.A : (which == 1 ? L.cz.P : (which == 2 ? L.G : L.cz.Ac));
+        const HostCSR& M = which == 0 ? L.A
+                           : which == 1 ? L.cz.P
+                           : which == 2 ? L.G
+                           : (h->structure_only ? L.cz.Ac : h->hl[l + 1].A);
         if (nrows) *nrows = M.nrows;
         if (ncols) *ncols = M.ncols;
         if (nnz) *nnz = M.nnz();
@@ -2074,6 +2307,7 @@ amgh_status amgh_level_apply(amgh_handle h, int l, int op, const double* f, cons
         }
         h->prof.enabled = was;
         AMGH_CUDA(cudaStreamSynchronize(h->s));
+        check_wait(h);
         return AMGH_OK;
     });
 }
@@ -2273,7 +2507,11 @@ namespace amgh {
 amgh_status pcg_with_scratch(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
                              double* relres, const KrylovScratch& ks, int64_t max_rows) {
     if (!h || !f || !x || h->structure_only) return AMGH_ERR_INVALID_ARG;
-    return guarded(h, [&] { return pcg_scratch_impl(h, f, x, tol, maxit, iters, relres, ks, max_rows); });
+    return guarded(h, [&] {
+        const amgh_status st = pcg_scratch_impl(h, f, x, tol, maxit, iters, relres, ks, max_rows);
+        check_wait(h);
+        return st;
+    });
 }
 
 }  // namespace amgh

@@ -68,6 +68,8 @@ class EngineBase {
     virtual void level_apply(int l, int op, const double* f, const double* x, double* y, cudaStream_t s) = 0;
     virtual void capture(cudaStream_t s) = 0;
     virtual void release_graph() = 0;
+    // zero the words of every grid barrier (after a barrier wait gave up)
+    virtual void reset_barriers(cudaStream_t s) = 0;
     Profiler* prof = nullptr;
     size_t prof_pairs = 0;   // event pairs one V-cycle records
 };

@@ -42,6 +42,14 @@ inline int thread_id() {
 #endif
 }
 
+inline int omp_threads() {
+#ifdef _OPENMP
+    return omp_get_num_threads();
+#else
+    return 1;
+#endif
+}
+
 inline bool has(const HostCSR& M, int r, int c) {
     auto b = M.idx.begin() + M.ptr[r], e = M.idx.begin() + M.ptr[r + 1];
     return std::binary_search(b, e, c);
@@ -99,6 +107,8 @@ HostCSR symbolic_rows(const HostCSR& X, const HostCSR& Y, int nthreads) {
 }
 
 }  // namespace
+
+HostCSR symbolic_product(const HostCSR& X, const HostCSR& Y, int nthreads) { return symbolic_rows(X, Y, nthreads); }
 
 HostCSR transpose_pattern(const HostCSR& M, bool with_values) {
     HostCSR T;
@@ -218,9 +228,10 @@ static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int
 static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt, const HostCSR& GtT,
                            double theta, int nthreads, HostCSR& Minc) {
     const int m = G.ncols, nn = Gt.ncols, ne = A.nrows;
+    (void)GtT;
     HostCSR GT = transpose_pattern(G, true);   // CSC of G: rows of column i with values
-    std::vector<std::vector<std::pair<int32_t, int32_t>>> incp(nthreads), nbp(nthreads);
     // incidence pairs: columns sharing a row of G~
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> incp(nthreads);
 #pragma omp parallel for schedule(static) num_threads(nthreads)
     for (int r = 0; r < Gt.nrows; ++r) {
         if (Gt.ptr[r + 1] - Gt.ptr[r] != 2) continue;
@@ -230,22 +241,22 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
         v.push_back({b, a});
     }
     Minc = csr_from_pairs(nn, incp, nthreads);
-    // strong connections among gradient modes, symmetrised, plus the incidence pairs
-    std::vector<std::vector<int32_t>> wmark(nthreads, std::vector<int32_t>(ne, -1));
-    std::vector<std::vector<double>> w(nthreads, std::vector<double>(ne, 0.0));
-    std::vector<std::vector<int32_t>> amark(nthreads, std::vector<int32_t>(m, -1));
-    std::vector<std::vector<double>> acc(nthreads, std::vector<double>(m, 0.0));
+    PhaseClock nclk;
+    // S: row i holds the strong connections of gradient mode i in A_G = G^T A G (sorted).  Each
+    // thread takes one contiguous range of rows, so the threads' outputs concatenate into CSR.
+    HostCSR S;
+    S.nrows = S.ncols = nn;
+    S.ptr.assign(nn + 1, 0);
+    std::vector<std::vector<int32_t>> sidx(nthreads);
+    std::vector<int32_t> slen(nn, 0);
 #pragma omp parallel num_threads(nthreads)
     {
-        const int tid = thread_id();
-        auto& wm = wmark[tid];
-        auto& wv = w[tid];
-        auto& am = amark[tid];
-        auto& av = acc[tid];
-        auto& out = nbp[tid];
-        std::vector<int32_t> tf, tj;
-#pragma omp for schedule(dynamic, 512)
-        for (int i = 0; i < m; ++i) {
+        const int tid = thread_id(), nt = omp_threads();
+        const int i0 = (int)((int64_t)m * tid / nt), i1 = (int)((int64_t)m * (tid + 1) / nt);
+        std::vector<int32_t> wm(ne, -1), am(m, -1), tf, tj;
+        std::vector<double> wv(ne, 0.0), av(m, 0.0);
+        auto& out = sidx[tid];
+        for (int i = i0; i < i1; ++i) {
             tf.clear();
             tj.clear();
             // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
@@ -268,16 +279,54 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
             double rowmax = -INFINITY;
             for (int32_t j : tj)
                 if (j != i) rowmax = std::max(rowmax, -av[j]);
+            const size_t b = out.size();
             if (rowmax > 0.0)
                 for (int32_t j : tj)
-                    if (j != i && -av[j] >= theta * rowmax) {
-                        out.push_back({i, j});
-                        out.push_back({j, i});
-                    }
+                    if (j != i && -av[j] >= theta * rowmax) out.push_back(j);
+            std::sort(out.begin() + b, out.end());
+            slen[i] = (int32_t)(out.size() - b);
         }
     }
-    for (int t = 0; t < nthreads; ++t) nbp[t].insert(nbp[t].end(), incp[t].begin(), incp[t].end());
-    return csr_from_pairs(nn, nbp, nthreads);
+    for (int i = 0; i < nn; ++i) S.ptr[i + 1] = S.ptr[i] + slen[i];
+    for (const auto& v : sidx) S.idx.insert(S.idx.end(), v.begin(), v.end());
+    nclk.mark("  strong connections");
+    HostCSR ST = transpose_pattern(S, false);
+    // N = S + S^T + incidence, row by row as sorted unions
+    HostCSR N;
+    N.nrows = N.ncols = nn;
+    N.ptr.assign(nn + 1, 0);
+    auto merged = [&](int r, int32_t* dst) {
+        const HostCSR* M3[3] = {&S, &ST, &Minc};
+        int32_t pos[3], end[3];
+        for (int k = 0; k < 3; ++k) {
+            pos[k] = M3[k]->ptr[r];
+            end[k] = M3[k]->ptr[r + 1];
+        }
+        int cnt = 0;
+        int32_t last = -1;
+        for (;;) {
+            int32_t best = INT32_MAX;
+            for (int k = 0; k < 3; ++k)
+                if (pos[k] < end[k]) best = std::min(best, M3[k]->idx[pos[k]]);
+            if (best == INT32_MAX) break;
+            for (int k = 0; k < 3; ++k)
+                if (pos[k] < end[k] && M3[k]->idx[pos[k]] == best) pos[k]++;
+            if (best != last) {
+                if (dst) dst[cnt] = best;
+                cnt++;
+                last = best;
+            }
+        }
+        return cnt;
+    };
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < nn; ++r) N.ptr[r + 1] = merged(r, nullptr);
+    for (int r = 0; r < nn; ++r) N.ptr[r + 1] += N.ptr[r];
+    N.idx.resize(N.ptr[nn]);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < nn; ++r) merged(r, N.idx.data() + N.ptr[r]);
+    nclk.mark("  transpose + union");
+    return N;
 }
 
 // -------------------------------------------------------------------------------------------
@@ -449,9 +498,10 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     int nB = 0;
     HostCSR Gt = augment(G, nB);
     HostCSR GtT = transpose_pattern(Gt, false);
+    clk.mark("augment");
     HostCSR Minc;
     HostCSR N = nodal_graph(A, G, Gt, GtT, prm.theta, nthreads, Minc);
-    clk.mark("augment + nodal graph");
+    clk.mark("nodal graph");
     out.m = G.ncols;
     out.nB = nB;
     nodal_cf(N, G.ncols, out.state);
@@ -582,36 +632,8 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
         std::copy(patches[c].begin(), patches[c].end(), out.patch_idx.begin() + out.patch_ptr[c]);
 
     clk.mark("patches");
-    // ---- patterns of P (n x nc) and P^T, with positions of every computed entry -------------
-    HostCSR& P = out.P;
-    P.nrows = n;
-    P.ncols = nc;
-    P.ptr.assign(n + 1, 0);
-    for (int c = 0; c < nc; ++c) {
-        P.ptr[out.edges[c].d1 + 1]++;
-        P.ptr[out.edges[c].d2 + 1]++;
-        for (int32_t t = out.patch_ptr[c]; t < out.patch_ptr[c + 1]; ++t) P.ptr[out.patch_idx[t] + 1]++;
-    }
-    for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
-    P.idx.assign(P.ptr[n], 0);
-    P.val.assign(P.ptr[n], 0.0);
-    out.patch_pos_P.assign(out.patch_idx.size(), 0);
-    out.ext_pos_P.assign(2 * (size_t)nc, 0);
-    {
-        std::vector<int32_t> cur(P.ptr.begin(), P.ptr.end() - 1);
-        for (int c = 0; c < nc; ++c) {   // columns visited in ascending order: rows stay sorted
-            const auto& e = out.edges[c];
-            int32_t p1 = cur[e.d1]++, p2 = cur[e.d2]++;
-            P.idx[p1] = c; P.val[p1] = e.s1; out.ext_pos_P[2 * c] = p1;
-            P.idx[p2] = c; P.val[p2] = e.s2; out.ext_pos_P[2 * c + 1] = p2;
-            for (int32_t t = out.patch_ptr[c]; t < out.patch_ptr[c + 1]; ++t) {
-                int32_t r = out.patch_idx[t];
-                int32_t pp = cur[r]++;
-                P.idx[pp] = c;
-                out.patch_pos_P[t] = pp;
-            }
-        }
-    }
+    // ---- patterns of P^T (row c: the patch and the two exterior DoFs, ascending) and of P (its
+    // transpose), with the positions of every computed entry in both -------------------------
     HostCSR& PT = out.PT;
     PT.nrows = nc;
     PT.ncols = n;
@@ -643,11 +665,76 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
             ++pos;
         }
     }
-    clk.mark("P, P^T patterns");
+    clk.mark("P^T pattern");
+    HostCSR& P = out.P;
+    P.nrows = n;
+    P.ncols = nc;
+    P.ptr.assign(n + 1, 0);
+    const int64_t nzp = PT.ptr[nc];
+    std::vector<int32_t> fromPT(nzp);   // P position -> P^T position
+    std::vector<int32_t> toP(nzp);      // P^T position -> P position
+    {
+        // counting sort of the P^T entries by row of P; each thread scatters one contiguous range
+        // of coarse edges, and per-thread offsets keep every row in ascending column order
+        const int nt = std::max(1, nthreads);
+        std::vector<std::vector<int32_t>> cnt(nt);
+#pragma omp parallel num_threads(nt)
+        {
+            const int tid = thread_id(), ntr = omp_threads();
+            const int c0 = (int)((int64_t)nc * tid / ntr), c1 = (int)((int64_t)nc * (tid + 1) / ntr);
+            auto& v = cnt[tid];
+            v.assign(n, 0);
+            for (int32_t q = PT.ptr[c0]; q < PT.ptr[c1]; ++q) v[PT.idx[q]]++;
+#pragma omp barrier
+#pragma omp for schedule(static)
+            for (int r = 0; r < n; ++r) {
+                int32_t s = 0;
+                for (int t = 0; t < ntr; ++t) s += cnt[t][r];
+                P.ptr[r + 1] = s;
+            }
+#pragma omp single
+            for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
+#pragma omp for schedule(static)
+            for (int r = 0; r < n; ++r) {
+                int32_t off = P.ptr[r];
+                for (int t = 0; t < ntr; ++t) {
+                    const int32_t k = cnt[t][r];
+                    cnt[t][r] = off;
+                    off += k;
+                }
+            }
+            for (int c = c0; c < c1; ++c)
+                for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
+                    const int32_t pp = v[PT.idx[q]]++;
+                    fromPT[pp] = q;
+                    toP[q] = pp;
+                }
+        }
+    }
+    P.idx.resize(nzp);
+    P.val.resize(nzp);
+    int32_t* cidx = P.idx.data();
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int c = 0; c < nc; ++c)
+        for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
+            cidx[toP[q]] = c;
+            P.val[toP[q]] = PT.val[q];
+        }
+    out.patch_pos_P.assign(out.patch_idx.size(), 0);
+    out.ext_pos_P.assign(2 * (size_t)nc, 0);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t t = 0; t < (int64_t)out.patch_idx.size(); ++t) out.patch_pos_P[t] = toP[out.patch_pos_PT[t]];
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int64_t t = 0; t < 2 * (int64_t)nc; ++t) out.ext_pos_P[t] = toP[out.ext_pos_PT[t]];
+
     // ---- symbolic Galerkin patterns ----------------------------------------------------------
-    out.AP = symbolic_rows(A, P, nthreads);
-    out.Ac = symbolic_rows(PT, out.AP, nthreads);
-    clk.mark("symbolic AP, PtAP");
+    clk.mark("P pattern");
+    if (prm.symbolic_galerkin) {
+        out.AP = symbolic_rows(A, P, nthreads);
+        clk.mark("symbolic AP");
+        out.Ac = symbolic_rows(PT, out.AP, nthreads);
+        clk.mark("symbolic PtAP");
+    }
     return "";
 }
 

@@ -43,7 +43,11 @@ struct Params {
     double theta = 0.25;
     int ring = 1;
     int p_max = 128;
+    bool symbolic_galerkin = true;   // also form the symbolic AP and P^T A P patterns on the host
 };
+
+// pattern of X Y with sorted columns per row (values left empty)
+HostCSR symbolic_product(const HostCSR& X, const HostCSR& Y, int nthreads);
 
 // Validate G (rows with 1 or 2 entries of +-1; two entries of opposite sign).  Returns "" if ok.
 std::string check_gradient(const HostCSR& G);

@@ -13,6 +13,9 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
                         double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s);
 
 // Galerkin product A_c = P^T (A P) on given symbolic patterns (Eq. tl), FP64, deterministic order.
+// symbolic Z = X Y on the device (sorted columns per row); false when a row overflows the
+// kernel's shared-memory set (the caller then computes the pattern on the host)
+bool spgemm_symbolic(const DevCSR& X, const DevCSR& Y, DevCSR& Z, int* flag, cudaStream_t s);
 void launch_ap_numeric(const DevCSR& A, const DevCSR& P, DevCSR& AP, cudaStream_t s);
 void launch_ac_numeric(const DevCSR& PT, const DevCSR& AP, DevCSR& Ac, cudaStream_t s);
 

@@ -33,6 +33,14 @@ inline SellLView<V> view(const SellL<V>& s) {
     return {s.nrows, s.nslices, s.slice_ptr.p, s.col.p, s.val.p};
 }
 
+// words of a grid barrier (count, generation, abort) and the error flag its waits raise
+struct GridBarrier {
+    unsigned* count;
+    unsigned* gen;
+    unsigned* abort;
+    int* err;
+};
+
 // Schwarz smoother of one level.  Stars of one colour are packed, without being split, into
 // chunks of SLOTS = 256/L row slots; a chunk is processed by one CTA (L lanes per row slot).  The
 // chunk's rows form 8 SELL slices (one per warp); the block inverses are stored per chunk as
@@ -41,6 +49,14 @@ template <class V>
 struct SmootherL {
     int L = 1, slots = CTA_THREADS, nctas = 0, bmax = 1, ncolours = 0;
     bool fused = false;                       // whole sweep in one single-CTA launch
+    int persist = 0;                          // > 0: whole sweep in one cooperative launch of this many CTAs
+    bool staged = false;                      // persistent sweep with chunks staged by bulk copies
+    int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
+    int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches
+    int wmax = 0;                             // longest slice (in 32-wide steps), for the staging buffers
+    DevArray<unsigned> bar;                   // count, generation, abort (persistent sweep)
+    int* wait_err = nullptr;                  // raised when a barrier wait gives up
+    GridBarrier barrier() const { return {bar.p, bar.p + 1, bar.p + 2, wait_err}; }
     std::vector<int32_t> colour_cta_begin;    // host, ncolours + 1
     DevArray<int32_t> colour_cta_begin_d;     // device copy (fused sweep)
     DevArray<int32_t> sweep_d;                // colour sequence 0..C-1, C-2..0 (fused sweep)

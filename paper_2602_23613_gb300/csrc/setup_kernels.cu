@@ -227,6 +227,109 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
     }
 }
 
+// Symbolic sparse product Z = X Y, one CTA per row of Z: the candidate columns (Y's rows selected
+// by the row of X) go into a shared-memory hash set; the count pass writes each row's number of
+// distinct columns, the fill pass writes them in ascending order (each key's rank is the number of
+// smaller keys), so the pattern does not depend on the order of insertion.  A row whose distinct
+// columns exceed the set's load limit raises *overflow and is left to the caller.
+constexpr int SYM_THREADS = 256, SYM_SLOTS = 4096, SYM_LIMIT = 3 * SYM_SLOTS / 4;
+
+template <bool FILL>
+__global__ void __launch_bounds__(SYM_THREADS) spgemm_symbolic_kernel(
+    int nrows, const int32_t* __restrict__ Xptr, const int32_t* __restrict__ Xidx, const int32_t* __restrict__ Yptr,
+    const int32_t* __restrict__ Yidx, int32_t* __restrict__ len, const int32_t* __restrict__ Zptr,
+    int32_t* __restrict__ Zidx, int* overflow) {
+    __shared__ int32_t tab[SYM_SLOTS];
+    __shared__ int32_t keys[SYM_LIMIT];
+    __shared__ int nkeys, full;
+    const int r = blockIdx.x;
+    if (r >= nrows) return;
+    for (int q = threadIdx.x; q < SYM_SLOTS; q += SYM_THREADS) tab[q] = -1;
+    if (threadIdx.x == 0) {
+        nkeys = 0;
+        full = 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = Xptr[r] + warp; t < Xptr[r + 1]; t += SYM_THREADS / 32) {
+        const int y = Xidx[t];
+        for (int u = Yptr[y] + lane; u < Yptr[y + 1]; u += 32) {
+            const int32_t k = Yidx[u];
+            uint32_t hsh = ((uint32_t)k * 2654435761u) & (SYM_SLOTS - 1);
+            for (int probe = 0; probe < SYM_SLOTS; ++probe) {
+                const int32_t old = atomicCAS(&tab[hsh], -1, k);
+                if (old == k) break;
+                if (old == -1) {
+                    const int slot = atomicAdd(&nkeys, 1);
+                    if (slot < SYM_LIMIT) keys[slot] = k;
+                    else full = 1;
+                    break;
+                }
+                hsh = (hsh + 1) & (SYM_SLOTS - 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (full) {
+        if (threadIdx.x == 0) {
+            atomicExch(overflow, 1);
+            if (!FILL) len[r] = 0;
+        }
+        return;
+    }
+    const int m = nkeys;
+    if (!FILL) {
+        if (threadIdx.x == 0) len[r] = m;
+        return;
+    }
+    int32_t* out = Zidx + Zptr[r];
+    for (int i = threadIdx.x; i < m; i += SYM_THREADS) {
+        const int32_t k = keys[i];
+        int rank = 0;
+        for (int j = 0; j < m; ++j) rank += keys[j] < k;
+        out[rank] = k;
+    }
+}
+
+// Z = X Y symbolically on the device: Z.ptr, Z.idx filled and Z.val allocated.  Returns false (and
+// leaves Z empty) when a row has more distinct columns than the shared-memory set holds.
+bool spgemm_symbolic(const DevCSR& X, const DevCSR& Y, DevCSR& Z, int* flag, cudaStream_t s) {
+    const int n = X.nrows;
+    Z.nrows = n;
+    Z.ncols = Y.ncols;
+    DevArray<int32_t> len;
+    len.alloc(std::max(1, n));
+    AMGH_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    if (n > 0) {
+        spgemm_symbolic_kernel<false><<<n, SYM_THREADS, 0, s>>>(n, X.ptr.p, X.idx.p, Y.ptr.p, Y.idx.p, len.p, nullptr,
+                                                               nullptr, flag);
+        AMGH_LAUNCHED();
+    }
+    std::vector<int32_t> hl(n);
+    int of = 0;
+    if (n > 0) AMGH_CUDA(cudaMemcpyAsync(hl.data(), len.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaMemcpyAsync(&of, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    if (of) return false;
+    std::vector<int32_t> ptr(n + 1, 0);
+    int64_t tot = 0;
+    for (int r = 0; r < n; ++r) {
+        tot += hl[r];
+        if (tot >= INT32_MAX) return false;
+        ptr[r + 1] = (int32_t)tot;
+    }
+    Z.nnz = tot;
+    Z.ptr.upload(ptr, s);
+    Z.idx.alloc(std::max<int64_t>(1, tot));
+    Z.val.alloc(std::max<int64_t>(1, tot));
+    if (n > 0) {
+        spgemm_symbolic_kernel<true><<<n, SYM_THREADS, 0, s>>>(n, X.ptr.p, X.idx.p, Y.ptr.p, Y.idx.p, nullptr, Z.ptr.p,
+                                                              Z.idx.p, flag);
+        AMGH_LAUNCHED();
+    }
+    return true;
+}
+
 void launch_ap_numeric(const DevCSR& A, const DevCSR& P, DevCSR& AP, cudaStream_t s) {
     const int n = AP.nrows;
     if (n == 0) return;

@@ -12,12 +12,32 @@ enum SellModeL { SM_AX = 0, SM_RESID = 1, SM_L1 = 2, SM_ADD = 3 };
 template <class V, class TX, class TY>
 void launch_sellL(int mode, const SellL<V>& M, const TX* x, const TY* f, const TY* dinv, TY* y, cudaStream_t s);
 
-// one colour of the multiplicative Schwarz sweep (chunks [cta_begin, cta_end) of the colour)
+// one colour of the multiplicative Schwarz sweep (chunks [cta_begin, cta_end) of the colour); with
+// S.stream_grid > 0 as a streaming launch of at most that many CTAs
 template <class V, class T>
 void launch_schwarz_colourL(const SmootherL<V>& S, int colour, const T* f, T* x, cudaStream_t s);
 // whole symmetric sweep (colours 0..C-1, C-2..0) in one single-CTA launch
 template <class V, class T>
 void launch_schwarz_fused(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s);
+
+// whole symmetric sweep in one cooperative launch of S.persist CTAs (grid barriers between colours;
+// a barrier wait that gives up sets *S.wait_err and the sweep ends early)
+template <class V, class T>
+void launch_schwarz_persistent(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s);
+// largest grid of the persistent sweep that is co-resident on this device for L lanes per row
+template <class V, class T>
+int schwarz_persistent_cap(int L);
+// largest co-resident grid of the staged persistent sweep (chunks staged in shared memory by
+// bulk async copies; needs S.wmax), 0 when its two stage buffers do not fit
+template <class V, class T>
+int schwarz_staged_cap(const SmootherL<V>& S);
+// largest co-resident grid of the streaming colour step (chunks staged in shared memory by bulk
+// async copies, nbuf = 1 or 2 buffers per CTA; S.stream_grid > 0 selects it), 0 when it cannot
+// run for this smoother
+template <class V, class T>
+int schwarz_stream_cap(const SmootherL<V>& S, int nbuf);
+// whether a cooperative launch can be captured into a graph and replayed on the current device
+bool cooperative_capture_works();
 
 // setup: fill the SELL-L copy of a CSR matrix, the smoother's slot rows, and the star inverses
 template <class V>
