@@ -211,7 +211,8 @@ typedef struct {
                              AMGH_SMOOTHER_MODE=colour|stream1|stream2|fused|persistent|staged
                              restricts it to one mode where the level supports it.            */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
-                               (coarsest level: of its matrix)                                  */
+                               (coarsest level: of its matrix); estimated only when a reduced
+                               precision is requested, else 0 (coarsest level: always)          */
     int dense_tail;       /* level whose sub-cycle is applied as a dense operator, or -1       */
     int interp_used;      /* AMGH_INTERP_LOCAL or AMGH_INTERP_LEARNED (after the fallback test) */
     double rho;           /* measured convergence factor of the kept hierarchy (learned setups)  */

@@ -405,9 +405,14 @@ struct MultiEngine {
         return seq;
     }
 
+    int first_built = 0;   // levels below it carry no smoother (built for a dense tail only)
+
+    // smoother structures of levels >= first (a dense tail needs only its own sub-cycle)
     void build(const std::vector<LevelHost>& hl, const std::vector<DevCSR>& A64, const std::vector<DevCSR>& P64,
-               const std::vector<DevCSR>& PT64, const double* cinv64, int* err, cudaStream_t s) {
+               const std::vector<DevCSR>& PT64, const double* cinv64, int* err, cudaStream_t s, int first = 0) {
         nlev = (int)hl.size();
+        first_built = first;
+        width.clear();
         L.clear();
         L.resize(nlev);
         for (int l = 0; l < nlev; ++l) {
@@ -417,6 +422,7 @@ struct MultiEngine {
             if (l + 1 == nlev) break;
             d.P = &P64[l];
             d.PT = &PT64[l];
+            if (l < first) continue;
             const StarLayout& st = hl[l].stars;
             d.ncolours = st.ncolours;
             d.bmax = std::max(1, st.max_block);
@@ -744,6 +750,20 @@ static void build_smoother(amgh_ctx* h, int l, int L, bool fused, int persist, b
     }
 }
 
+// wall time of setup phases on stderr when AMGH_VERBOSE=1 (the stream is synchronised only then)
+struct DevPhases {
+    bool on = std::getenv("AMGH_VERBOSE") != nullptr;
+    double t = now_ms();
+    void mark(cudaStream_t s, const char* what, int l = -1) {
+        if (!on) return;
+        cudaStreamSynchronize(s);
+        const double now = now_ms();
+        if (l >= 0) std::fprintf(stderr, "[amgh] L%d %-25s %8.1f ms\n", l, what, now - t);
+        else std::fprintf(stderr, "[amgh] %-28s %8.1f ms\n", what, now - t);
+        t = now;
+    }
+};
+
 // time fn() (enqueued on s): best of `reps` after one warm-up, in ms
 template <class F>
 static float time_best(cudaStream_t s, int reps, F&& fn) {
@@ -841,6 +861,7 @@ template <class V, class T>
 static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     cudaStream_t s = h->s;
     const LevelHost& hl = h->hl[l];
+    DevPhases ph;
     d.n = hl.A.nrows;
     d.nnzA = hl.A.nnz();
     d.nnzP = hl.cz.P.nnz();
@@ -891,6 +912,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
         }
     }
     build_sellL<V>(hl.A, h->A64[l], ch.L_A, d.A, s);
+    ph.mark(s, "  A layout", l);
     // ---- P (prolongation) and P^T (restriction) ----
     if (tune) {
         float best = 1e30f;
@@ -915,6 +937,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     }
     build_sellL<V>(hl.cz.P, h->P64[l], ch.L_P, d.P, s);
     build_sellL<V>(hl.cz.PT, h->PT64[l], ch.L_PT, d.PT, s);
+    ph.mark(s, "  P, P^T layouts", l);
     // ---- smoother ----
     // Each lane count is built once; its launch modes only differ in how the same layout is
     // swept: per-colour launches, per-colour streaming launches (chunks staged in shared memory),
@@ -1011,6 +1034,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     if (ch.staged && schwarz_staged_cap<V, T>(d.sm) < ch.persist) ch.staged = false;
     if (ch.stream > 0) ch.stream = std::min(ch.stream, schwarz_stream_cap<V, T>(d.sm, ch.stream_bufs));
     set_smoother_mode(d.sm, ch);
+    ph.mark(s, "  smoother", l);
     AMGH_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1047,9 +1071,12 @@ static void build_engine(amgh_ctx* h, Engine* e) {
     e->nlev = nlev;
     e->L.clear();
     e->choice.assign(nlev, LevelChoice());
+    DevPhases ph;
     for (int l = 0; l + 1 < nlev; ++l) {
+        if (l > 0) ph.mark(s, "engine level", l - 1);
         LevelChoice& ch = e->choice[l];
-        ch.kappa = level_kappa(h, l);
+        // the condition estimate only decides a reduced precision; an FP64 request skips it
+        ch.kappa = h->prm.precision == AMGH_F64 ? 0.0 : level_kappa(h, l);
         ch.prec = level_precision(h->prm.precision, ch.kappa);
         if (ch.prec == AMGH_F64) {
             e->L.emplace_back(std::in_place_type<LevelX<double, double>>);
@@ -1197,20 +1224,6 @@ static void host_structure_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr
     if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
 }
 
-// wall time of setup phases on stderr when AMGH_VERBOSE=1 (the stream is synchronised only then)
-struct DevPhases {
-    bool on = std::getenv("AMGH_VERBOSE") != nullptr;
-    double t = now_ms();
-    void mark(cudaStream_t s, const char* what, int l = -1) {
-        if (!on) return;
-        cudaStreamSynchronize(s);
-        const double now = now_ms();
-        if (l >= 0) std::fprintf(stderr, "[amgh] L%d %-25s %8.1f ms\n", l, what, now - t);
-        else std::fprintf(stderr, "[amgh] %-28s %8.1f ms\n", what, now - t);
-        t = now;
-    }
-};
-
 static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     DevPhases ph;
     cudaStream_t s = h->s;
@@ -1233,7 +1246,20 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         AMGH_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
     }
     DevCSR dA;
-    upload_csr(A, dA, s, true);
+    if (Ain->on_device) {
+        // the caller's device copy is copied on the device, not sent back from the host
+        dA.nrows = A.nrows;
+        dA.ncols = A.ncols;
+        dA.nnz = A.nnz();
+        dA.ptr.alloc(A.nrows + 1);
+        dA.idx.alloc(std::max<int64_t>(1, dA.nnz));
+        dA.val.alloc(std::max<int64_t>(1, dA.nnz));
+        AMGH_CUDA(cudaMemcpyAsync(dA.ptr.p, Ain->row_ptr, sizeof(int32_t) * (A.nrows + 1), cudaMemcpyDeviceToDevice, s));
+        AMGH_CUDA(cudaMemcpyAsync(dA.idx.p, Ain->col, sizeof(int32_t) * dA.nnz, cudaMemcpyDeviceToDevice, s));
+        AMGH_CUDA(cudaMemcpyAsync(dA.val.p, Ain->val, sizeof(double) * dA.nnz, cudaMemcpyDeviceToDevice, s));
+    } else {
+        upload_csr(A, dA, s, true);
+    }
     for (int l = 0;; ++l) {
         h->hl.emplace_back();
         LevelHost& cur = h->hl.back();
@@ -1267,8 +1293,12 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         h->PT64.emplace_back();
         DevCSR& P = h->P64.back();
         DevCSR& PT = h->PT64.back();
-        upload_csr(cz.P, P, s, true);
-        upload_csr(cz.PT, PT, s, true);
+        // patterns from the host; values: zero, the exterior +-1 of R^T scattered on the device,
+        // the interior filled below by the local solves (or the network)
+        upload_csr(cz.P, P, s, false);
+        upload_csr(cz.PT, PT, s, false);
+        AMGH_CUDA(cudaMemsetAsync(P.val.p, 0, sizeof(double) * P.nnz, s));
+        AMGH_CUDA(cudaMemsetAsync(PT.val.p, 0, sizeof(double) * PT.nnz, s));
         std::vector<int32_t> e4(4 * (size_t)nc);
         int maxp = 0;
         for (int c = 0; c < nc; ++c) {
@@ -1287,6 +1317,13 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             dpi.upload(cz.patch_idx, s);
             dpos.upload(cz.patch_pos_P, s);
             dpost.upload(cz.patch_pos_PT, s);
+            {
+                DevArray<int64_t> dex, dext;
+                dex.upload(cz.ext_pos_P, s);
+                dext.upload(cz.ext_pos_PT, s);
+                launch_ext_scatter(nc, de4.p, dex.p, dext.p, P.val.p, PT.val.p, s);
+                AMGH_CUDA(cudaStreamSynchronize(s));
+            }
             double ti = 0.0;
             if (l == 0) {
                 AMGH_CUDA(cudaStreamSynchronize(s));
@@ -1379,7 +1416,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             if (h->hl[l].A.nrows <= prm.dense_tail) { t = l; break; }
         if (t > 0) {
             h->meng.reset(new MultiEngine());
-            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
+            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s, t);
             h->meng->dense_tail(t, h->dense_tail_B, s);
             check_flag(h, "a smoother block of the dense tail");
             h->dense_tail_level = t;
@@ -1807,7 +1844,7 @@ static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in,
     cudaStream_t s = h->s;
     const int64_t n = h->hl[0].A.nrows;
     const int KP = ((k + 31) / 32) * 32;
-    if (!h->meng) {
+    if (!h->meng || h->meng->first_built > 0) {
         h->meng.reset(new MultiEngine());
         h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
     }
@@ -2180,7 +2217,7 @@ amgh_status amgh_vcycle_multi(amgh_handle h, const double* Rin, double* Zout, in
         cudaStream_t s = h->s;
         const int64_t n = h->hl[0].A.nrows;
         const int KP = ((k + 31) / 32) * 32;
-        if (!h->meng) {
+        if (!h->meng || h->meng->first_built > 0) {
             h->meng.reset(new MultiEngine());
             h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
         }

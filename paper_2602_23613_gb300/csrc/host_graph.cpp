@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -129,31 +130,56 @@ HostCSR transpose_pattern(const HostCSR& M, bool with_values) {
     return T;
 }
 
-std::string check_csr(const HostCSR& M, bool square) {
-    if (M.nrows < 0 || M.ncols < 0) return "negative dimension";
-    if (square && M.nrows != M.ncols) return "matrix is not square";
-    if ((int64_t)M.ptr.size() != (int64_t)M.nrows + 1 || M.ptr[0] != 0) return "bad row_ptr";
-    for (int r = 0; r < M.nrows; ++r) {
-        if (M.ptr[r + 1] < M.ptr[r]) return "row_ptr not monotone";
-        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
-            int32_t c = M.idx[e];
-            if (c < 0 || c >= M.ncols) return "column index out of range in row " + std::to_string(r);
-            if (e > M.ptr[r] && M.idx[e - 1] >= c) return "columns not strictly ascending in row " + std::to_string(r);
-        }
+static std::string csr_row_error(const HostCSR& M, int r) {
+    if (M.ptr[r + 1] < M.ptr[r]) return "row_ptr not monotone";
+    if ((int64_t)M.ptr[r + 1] > (int64_t)M.idx.size()) return "row_ptr beyond nnz";
+    for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+        const int32_t c = M.idx[e];
+        if (c < 0 || c >= M.ncols) return "column index out of range in row " + std::to_string(r);
+        if (e > M.ptr[r] && M.idx[e - 1] >= c) return "columns not strictly ascending in row " + std::to_string(r);
     }
     return "";
 }
 
-std::string check_gradient(const HostCSR& G) {
-    for (int r = 0; r < G.nrows; ++r) {
-        int32_t n = G.ptr[r + 1] - G.ptr[r];
-        // 0 entries: an interior edge joining two boundary nodes (e.g. a corner diagonal)
-        if (n > 2) return "G row " + std::to_string(r) + " has " + std::to_string(n) + " entries (at most 2)";
-        for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e)
-            if (G.val[e] != 1.0 && G.val[e] != -1.0) return "G entry other than +-1 in row " + std::to_string(r);
-        if (n == 2 && G.val[G.ptr[r]] == G.val[G.ptr[r] + 1]) return "G row " + std::to_string(r) + " entries share a sign";
+// the first failing row is found in parallel and then described
+std::string check_csr(const HostCSR& M, bool square) {
+    if (M.nrows < 0 || M.ncols < 0) return "negative dimension";
+    if (square && M.nrows != M.ncols) return "matrix is not square";
+    if ((int64_t)M.ptr.size() != (int64_t)M.nrows + 1 || M.ptr[0] != 0) return "bad row_ptr";
+    int bad = INT32_MAX;
+#pragma omp parallel for schedule(static) reduction(min : bad)
+    for (int r = 0; r < M.nrows; ++r) {
+        if (M.ptr[r + 1] < M.ptr[r] || (int64_t)M.ptr[r + 1] > (int64_t)M.idx.size()) {
+            bad = std::min(bad, r);
+            continue;
+        }
+        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+            const int32_t c = M.idx[e];
+            if (c < 0 || c >= M.ncols || (e > M.ptr[r] && M.idx[e - 1] >= c)) {
+                bad = std::min(bad, r);
+                break;
+            }
+        }
     }
+    return bad == INT32_MAX ? std::string() : csr_row_error(M, bad);
+}
+
+static std::string gradient_row_error(const HostCSR& G, int r) {
+    const int32_t n = G.ptr[r + 1] - G.ptr[r];
+    // 0 entries: an interior edge joining two boundary nodes (e.g. a corner diagonal)
+    if (n > 2) return "G row " + std::to_string(r) + " has " + std::to_string(n) + " entries (at most 2)";
+    for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e)
+        if (G.val[e] != 1.0 && G.val[e] != -1.0) return "G entry other than +-1 in row " + std::to_string(r);
+    if (n == 2 && G.val[G.ptr[r]] == G.val[G.ptr[r] + 1]) return "G row " + std::to_string(r) + " entries share a sign";
     return "";
+}
+
+std::string check_gradient(const HostCSR& G) {
+    int bad = INT32_MAX;
+#pragma omp parallel for schedule(static) reduction(min : bad)
+    for (int r = 0; r < G.nrows; ++r)
+        if (!gradient_row_error(G, r).empty()) bad = std::min(bad, r);
+    return bad == INT32_MAX ? std::string() : gradient_row_error(G, bad);
 }
 
 // -------------------------------------------------------------------------------------------

@@ -8,6 +8,10 @@ namespace amgh {
 // Local interior harmonic extension (Eq. sparseP): for coarse edge c with exterior pair
 // (d1, s1), (d2, s2) and sorted patch p, solve A_pp x = -(A_{p,d1} s1 + A_{p,d2} s2) by dense
 // Cholesky and scatter x into P (positions pos_P) and P^T (positions pos_PT).
+// exterior values of P and P^T (R^T: s1 at DoF1, s2 at DoF2 of every coarse edge) at the given
+// positions; the other entries are left as they are
+void launch_ext_scatter(int nc, const int32_t* edges4, const int64_t* ext_P, const int64_t* ext_PT, double* Pval,
+                        double* PTval, cudaStream_t s);
 void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const int32_t* patch_ptr,
                         const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
                         double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s);

@@ -38,7 +38,7 @@ __device__ __forceinline__ void schwarz_chunk(const SmootherLView<V>& S, int cta
     const int32_t* c = S.rows.col + st + lane;
     const V* v = S.rows.val + st + lane;
     T s = T(0);
-#pragma unroll 4
+#pragma unroll 8
     for (int t = 0; t < w; ++t) s = fma(widen<T>(v[32 * t]), x[c[32 * t]], s);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -54,8 +54,10 @@ __device__ __forceinline__ void schwarz_chunk(const SmootherLView<V>& S, int cta
     __syncthreads();
 }
 
+// at most 40 registers per thread: six CTAs per SM, so a colour of the finest level (about 780
+// chunks) fits in one wave
 template <class V, class T, int L>
-__global__ void __launch_bounds__(CTA_THREADS) schwarz_cta_kernel(SmootherLView<V> S, int cta_begin, const T* f, T* x) {
+__global__ void __launch_bounds__(CTA_THREADS, 6) schwarz_cta_kernel(SmootherLView<V> S, int cta_begin, const T* f, T* x) {
     __shared__ T smem_r[CTA_THREADS];
     schwarz_chunk<V, T, L>(S, cta_begin + blockIdx.x, f, x, smem_r);
 }

@@ -27,9 +27,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(
 }
 
 // ---------------------------------------------------------------------------------------------
-// One CTA per coarse edge: gather A_pp and the right-hand side -(A_{p,d1} s1 + A_{p,d2} s2) into
-// shared memory, Cholesky-factor A_pp in place (right-looking), two triangular solves, scatter.
+// One CTA per coarse edge: gather the lower triangle of A_pp (packed, row i at i(i+1)/2) and the
+// right-hand side -(A_{p,d1} s1 + A_{p,d2} s2) into shared memory; factor A_pp = L D L^T in place
+// by right-looking elimination with one barrier per pivot (step k reads column k and updates the
+// trailing lower triangle, so no entry is read and written in the same step); then one warp runs
+// the two triangular solves and the diagonal scaling; scatter into P and P^T.
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int tri(int i) { return i * (i + 1) / 2; }
+
 __global__ void patch_solve_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
                                    const double* __restrict__ Aval, int c0, int nc,
                                    const int32_t* __restrict__ edges4, const int32_t* __restrict__ patch_ptr,
@@ -42,22 +47,23 @@ __global__ void patch_solve_kernel(const int32_t* __restrict__ Aptr, const int32
     const int p0 = patch_ptr[c];
     const int m = patch_ptr[c + 1] - p0;
     if (m == 0) return;
-    double* L = smem;                               // m x m, row-major
-    double* y = smem + (size_t)max_patch * max_patch;
-    int* pidx = reinterpret_cast<int*>(y + max_patch);
+    double* L = smem;                                // packed lower triangle, tri(max_patch) entries
+    double* y = smem + tri(max_patch);
+    double* dinv = y + max_patch;
+    int* pidx = reinterpret_cast<int*>(dinv + max_patch);
     __shared__ int bad;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     if (tid == 0) bad = 0;
     for (int a = tid; a < m; a += nt) pidx[a] = patch_idx[p0 + a];
-    for (int e = tid; e < m * m; e += nt) L[e] = 0.0;
+    for (int e = tid; e < tri(m); e += nt) L[e] = 0.0;
     __syncthreads();
     const int d1 = edges4[4 * c], s1 = edges4[4 * c + 1], d2 = edges4[4 * c + 2], s2 = edges4[4 * c + 3];
     for (int a = tid; a < m; a += nt) {
         const int g = pidx[a];
         const int rb = Aptr[g], re = Aptr[g + 1];
         for (int q = rb; q < re; ++q) {
-            const int b = bsearch_i32(pidx, 0, m, Aidx[q]);
-            if (b >= 0) L[a * m + b] = Aval[q];
+            const int b = bsearch_i32(pidx, 0, a + 1, Aidx[q]);
+            if (b >= 0) L[tri(a) + b] = Aval[q];
         }
         const int q1 = bsearch_i32(Aidx, rb, re, d1);
         const int q2 = bsearch_i32(Aidx, rb, re, d2);
@@ -66,44 +72,60 @@ __global__ void patch_solve_kernel(const int32_t* __restrict__ Aptr, const int32
         if (q2 >= 0) rhs -= Aval[q2] * (double)s2;
         y[a] = rhs;
     }
-    // Cholesky (lower) in place
+    // L D L^T: after step k, L[k][k] = d_k and L[i][k] = l_ik d_k for i > k
     for (int k = 0; k < m; ++k) {
         __syncthreads();
-        if (tid == 0) {
-            double piv = L[k * m + k];
-            if (!(piv > 0.0)) { bad = 1; piv = 1.0; }
-            L[k * m + k] = sqrt(piv);
+        const double piv = L[tri(k) + k];
+        if (!(piv > 0.0)) {
+            if (tid == 0) bad = 1;
+            continue;
         }
-        __syncthreads();
-        const double dkk = L[k * m + k];
-        for (int i = k + 1 + tid; i < m; i += nt) L[i * m + k] /= dkk;
-        __syncthreads();
-        const int w = m - k - 1;
-        for (int e = tid; e < w * w; e += nt) {
-            const int i = k + 1 + e / w, j = k + 1 + e % w;
-            if (j <= i) L[i * m + j] -= L[i * m + k] * L[j * m + k];
+        const double inv = 1.0 / piv;
+        if (tid == 0) dinv[k] = inv;
+        for (int i = k + 1 + warp; i < m; i += nw) {
+            const double lik = L[tri(i) + k] * inv;
+            double* Li = L + tri(i);
+            for (int j = k + 1 + lane; j <= i; j += 32) Li[j] -= lik * L[tri(j) + k];
         }
-    }
-    // L z = y
-    for (int k = 0; k < m; ++k) {
-        __syncthreads();
-        if (tid == 0) y[k] /= L[k * m + k];
-        __syncthreads();
-        for (int i = k + 1 + tid; i < m; i += nt) y[i] -= L[i * m + k] * y[k];
-    }
-    // L^T x = z
-    for (int k = m - 1; k >= 0; --k) {
-        __syncthreads();
-        if (tid == 0) y[k] /= L[k * m + k];
-        __syncthreads();
-        for (int i = tid; i < k; i += nt) y[i] -= L[k * m + i] * y[k];
     }
     __syncthreads();
-    if (bad && tid == 0) atomicExch(err_flag, 1);
-    for (int a = tid; a < m; a += nt) {
-        Pval[pos_P[p0 + a]] = y[a];
-        PTval[pos_PT[p0 + a]] = y[a];
+    if (bad) {
+        if (tid == 0) atomicExch(err_flag, 1);
+        return;
     }
+    if (warp == 0) {
+        // L' z = y with L'[i][k] = L[i][k] d_k^-1, then w = D^-1 z, then L'^T x = w
+        for (int k = 0; k < m; ++k) {
+            __syncwarp();
+            const double zk = y[k] * dinv[k];
+            for (int i = k + 1 + lane; i < m; i += 32) y[i] -= L[tri(i) + k] * zk;
+        }
+        __syncwarp();
+        for (int k = lane; k < m; k += 32) y[k] *= dinv[k];
+        for (int k = m - 1; k >= 0; --k) {
+            __syncwarp();
+            const double xk = y[k];
+            for (int i = lane; i < k; i += 32) y[i] -= L[tri(k) + i] * dinv[i] * xk;
+        }
+        __syncwarp();
+        for (int a = lane; a < m; a += 32) {
+            Pval[pos_P[p0 + a]] = y[a];
+            PTval[pos_PT[p0 + a]] = y[a];
+        }
+    }
+}
+
+// exterior entries of column c of P (and row c of P^T): s1 at DoF1, s2 at DoF2 (R^T of Alg. 3)
+__global__ void ext_scatter_kernel(int nc, const int32_t* __restrict__ edges4, const int64_t* __restrict__ ext_P,
+                                   const int64_t* __restrict__ ext_PT, double* __restrict__ Pval,
+                                   double* __restrict__ PTval) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    const double s1 = (double)edges4[4 * c + 1], s2 = (double)edges4[4 * c + 3];
+    Pval[ext_P[2 * c]] = s1;
+    Pval[ext_P[2 * c + 1]] = s2;
+    PTval[ext_PT[2 * c]] = s1;
+    PTval[ext_PT[2 * c + 1]] = s2;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -211,17 +233,25 @@ __global__ void coarse_inverse_kernel(int n, const int32_t* __restrict__ Aptr, c
 
 }  // namespace
 
+void launch_ext_scatter(int nc, const int32_t* edges4, const int64_t* ext_P, const int64_t* ext_PT, double* Pval,
+                        double* PTval, cudaStream_t s) {
+    if (nc == 0) return;
+    ext_scatter_kernel<<<(nc + 255) / 256, 256, 0, s>>>(nc, edges4, ext_P, ext_PT, Pval, PTval);
+    AMGH_LAUNCHED();
+}
+
 void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const int32_t* patch_ptr,
                         const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
                         double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s) {
     if (nc == 0 || max_patch == 0) return;
-    const size_t shm = (size_t)max_patch * max_patch * 8 + (size_t)max_patch * 8 + (size_t)max_patch * 4;
+    const size_t tri_n = (size_t)max_patch * (max_patch + 1) / 2;
+    const size_t shm = tri_n * 8 + 2 * (size_t)max_patch * 8 + (size_t)max_patch * 4;
     static_assert(sizeof(int) == 4, "int");
     AMGH_CUDA(cudaFuncSetAttribute(patch_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     const int chunk = 65535;
     for (int c0 = 0; c0 < nc; c0 += chunk) {
         const int cnt = std::min(chunk, nc - c0);
-        patch_solve_kernel<<<cnt, 128, shm, s>>>(A.ptr.p, A.idx.p, A.val.p, c0, nc, edges4, patch_ptr, patch_idx,
+        patch_solve_kernel<<<cnt, 256, shm, s>>>(A.ptr.p, A.idx.p, A.val.p, c0, nc, edges4, patch_ptr, patch_idx,
                                                  pos_P, pos_PT, Pval, PTval, max_patch, err_flag);
         AMGH_LAUNCHED();
     }
