@@ -105,8 +105,9 @@ def peaks():
         return None
 
 
-def traffic_for(kernel, workload):
-    """dram bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def traffic_for(kernel, workload, mode):
+    """dram bytes per launch from the committed ncu summary, if the kernel source and its launch
+    mode are the ones that were captured."""
     import hashlib
     src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "schwarz_kernels.cu"), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
@@ -115,7 +116,8 @@ def traffic_for(kernel, workload):
         return None
     for line in open(path):
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
-        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("sha") == sha:
+        if (kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("sha") == sha
+                and kv.get("mode") == mode):
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -262,7 +264,8 @@ def run_gpu(args, rank, world, local_rank):
     achieved = ks_bytes / (ks_ms / 1000.0) / 1e9 if ks_ms > 0 else None
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
-    traffic = traffic_for("schwarz", args.workload)
+    modes = {0: "colour", 1: "fused", 2: "persistent", 3: "staged", 4: "stream"}
+    traffic = traffic_for("schwarz", args.workload, modes.get(res[-1]["info"]["fused"][0]))
     last = res[-1]
 
     # end to end through the same API with host buffers (copies inside the timed region)

@@ -45,6 +45,8 @@ static void upload_csr(const HostCSR& h, DevCSR& d, cudaStream_t s, bool values)
     d.nrows = h.nrows;
     d.ncols = h.ncols;
     d.nnz = h.nnz();
+    d.max_row = 0;
+    for (int r = 0; r < h.nrows; ++r) d.max_row = std::max(d.max_row, h.ptr[r + 1] - h.ptr[r]);
     d.ptr.upload(h.ptr, s);
     d.idx.upload(h.idx, s);
     if (values) d.val.upload(h.val, s);
@@ -102,6 +104,7 @@ struct LevelChoice {
     bool fused = false;
     int persist = 0;   // grid of the cooperative whole-sweep launch, 0: not used
     bool staged = false;   // that launch stages its chunks in shared memory
+    bool cluster = false;  // ... and runs as one thread-block cluster (hardware barrier)
     int stream = 0;        // per-colour streaming launches of at most this many CTAs, 0: not used
     int stream_bufs = 2;   // their stage buffers per CTA
     double kappa = 0.0;
@@ -280,10 +283,30 @@ struct Engine : EngineBase {
     int64_t vcycle(cudaStream_t s) override {
         const bool want_prof = prof && prof->enabled;
         if (!gexec || want_prof != prof_in_graph || (want_prof && prof_gen != prof->gen)) capture(s);
+        if (want_prof && prof_pairs) {
+            // every replay records into fresh event pairs, so that a solve harvests them once at
+            // its end instead of synchronising after every V-cycle
+            const size_t base = prof->used;
+            for (size_t i = 0; i < prof_pairs; ++i) prof->next();
+            prof->bytes_used.resize(prof->used);
+            for (size_t i = 0; i < prof_pairs; ++i) prof->bytes_used[base + i] = prof_bytes[i];
+            for (const auto& pn : prof_nodes) {
+                const auto& pr = prof->pool[base + pn.pair];
+                AMGH_CUDA(cudaGraphExecEventRecordNodeSetEvent(gexec, pn.node, pn.second ? pr.second : pr.first));
+            }
+        }
         AMGH_CUDA(cudaGraphLaunch(gexec, s));
         launch_counter().fetch_add(launches_vc);
         return launches_vc;
     }
+
+    struct ProfNode {
+        cudaGraphNode_t node;
+        size_t pair;
+        bool second;
+    };
+    std::vector<ProfNode> prof_nodes;   // event-record nodes of the captured V-cycle, by pair
+    std::vector<double> prof_bytes;     // algorithmic bytes of each pair
 
     void capture(cudaStream_t s) override {
         release_graph();
@@ -305,7 +328,31 @@ struct Engine : EngineBase {
         }
         AMGH_CUDA(cudaStreamEndCapture(s, &graph));
         launch_counter().store(before);
-        if (prof) { prof->capturing = false; prof_pairs = prof->used; prof->used = 0; }
+        prof_nodes.clear();
+        prof_bytes.clear();
+        if (prof) {
+            prof->capturing = false;
+            prof_pairs = prof->used;
+            prof_bytes.assign(prof->bytes_used.begin(), prof->bytes_used.begin() + prof_pairs);
+            if (prof_pairs) {
+                size_t nn = 0;
+                AMGH_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+                std::vector<cudaGraphNode_t> nodes(nn);
+                AMGH_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+                for (cudaGraphNode_t nd : nodes) {
+                    cudaGraphNodeType ty;
+                    AMGH_CUDA(cudaGraphNodeGetType(nd, &ty));
+                    if (ty != cudaGraphNodeTypeEventRecord) continue;
+                    cudaEvent_t ev = nullptr;
+                    AMGH_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+                    for (size_t i = 0; i < prof_pairs; ++i) {
+                        if (prof->pool[i].first == ev) prof_nodes.push_back({nd, i, false});
+                        if (prof->pool[i].second == ev) prof_nodes.push_back({nd, i, true});
+                    }
+                }
+            }
+            prof->used = 0;
+        }
         AMGH_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
         launches_vc = cnt;
     }
@@ -435,6 +482,32 @@ struct MultiEngine {
             }
             d.colour_star_begin[st.ncolours] = (int32_t)list.size();
             d.star_list.upload(list, s);
+            // long rows: colour steps in split-K form over the rows of the colour's stars
+            d.splitk = hl[l].A.nrows > 0 && hl[l].A.nnz() >= 64 * (int64_t)hl[l].A.nrows;
+            if (d.splitk) {
+                std::vector<int32_t> crow, cstar, cq, cbase;
+                d.colour_row_begin.assign(st.ncolours + 1, 0);
+                d.max_colour_rows = 0;
+                for (int c = 0; c < st.ncolours; ++c) {
+                    d.colour_row_begin[c] = (int32_t)crow.size();
+                    for (int u = d.colour_star_begin[c]; u < d.colour_star_begin[c + 1]; ++u) {
+                        const int j = list[u];
+                        const int base = (int)crow.size() - d.colour_row_begin[c];
+                        for (int q = 0; q < st.star_ptr[j + 1] - st.star_ptr[j]; ++q) {
+                            crow.push_back(st.star_idx[st.star_ptr[j] + q]);
+                            cstar.push_back(j);
+                            cq.push_back(q);
+                            cbase.push_back(base);
+                        }
+                    }
+                    d.max_colour_rows = std::max(d.max_colour_rows, (int)crow.size() - d.colour_row_begin[c]);
+                }
+                d.colour_row_begin[st.ncolours] = (int32_t)crow.size();
+                d.crow.upload(crow, s);
+                d.cstar.upload(cstar, s);
+                d.cq.upload(cq, s);
+                d.cbase.upload(cbase, s);
+            }
             d.star_ptr.upload(st.star_ptr, s);
             d.star_idx.upload(st.star_idx, s);
             std::vector<int64_t> off(st.nstars + 1, 0);
@@ -466,6 +539,7 @@ struct MultiEngine {
             d.X.alloc((size_t)d.n * kp);
             d.Y.alloc((size_t)d.n * kp);
             d.R.alloc((size_t)d.n * kp);
+            if (d.splitk) d.Rc.alloc((size_t)std::max(1, d.max_colour_rows) * kp);
             width[l] = kp;
         }
         if (partial.n != (size_t)304 * kp) {
@@ -502,7 +576,8 @@ struct MultiEngine {
     void dense_tail(int t, DevArray<double>& B, cudaStream_t s) {
         const int nt = L[t].n;
         B.alloc((size_t)nt * nt);
-        const int kp = std::min(2048, ((nt + 31) / 32) * 32);
+        // a multiple of 256 columns: eight per lane in the multi-RHS kernels
+        const int kp = std::min(2048, ((nt + 255) / 256) * 256);
         ensure_width(kp, t);
         std::vector<double> eye((size_t)nt * kp);
         for (int c0 = 0; c0 < nt; c0 += kp) {
@@ -669,7 +744,7 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
 // name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
 static std::string smoother_mode_name(const LevelChoice& m) {
     if (m.fused) return "fused";
-    if (m.persist > 0) return m.staged ? "staged" : "persistent";
+    if (m.persist > 0) return m.cluster ? "cluster" : m.staged ? "staged" : "persistent";
     if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
     return "colour";
 }
@@ -680,6 +755,7 @@ static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
     sm.fused = m.fused;
     sm.persist = m.fused ? 0 : m.persist;
     sm.staged = sm.persist > 0 && m.staged;
+    sm.cluster = sm.staged && m.cluster;
     sm.stream_grid = (m.fused || sm.persist > 0) ? 0 : m.stream;
     sm.stream_bufs = m.stream_bufs;
 }
@@ -945,7 +1021,8 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     // one cooperative launch with staged chunks (levels with many colours).  Every candidate is
     // timed as a captured graph, the way the V-cycle runs it.
     if (tune) {
-        float best = 1e30f;
+        float best = 1e30f, best_colour = 1e30f;
+        LevelChoice colour_choice = ch;
         const bool small = d.nnzA <= 3000000 && d.n <= 60000;
         for (int Lc : lane_candidates(avg, d.n, hl.stars.max_block)) {
             SmootherL<V> cand;
@@ -998,20 +1075,41 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                     modes.push_back(m);
                 }
             }
+            if (cand.ncolours >= 4 && maxc <= 8 && schwarz_cluster_ok<V, T>(cand, maxc)) {
+                LevelChoice m = m0;
+                m.persist = maxc;
+                m.staged = true;
+                m.cluster = true;
+                modes.push_back(m);
+            }
             const char* force = std::getenv("AMGH_SMOOTHER_MODE");
             for (const LevelChoice& m : modes) {
                 if (force && *force && std::string(force) != smoother_mode_name(m)) continue;
                 set_smoother_mode(cand, m);
-                const float ms = time_best_graph(s, 5, [&] {
-                    if (cand.fused) {
-                        launch_schwarz_fused<V, T>(cand, d.f.p, d.x.p, s);
-                    } else if (cand.persist > 0) {
-                        launch_schwarz_persistent<V, T>(cand, d.f.p, d.x.p, s);
-                    } else {
-                        for (int c : Engine::colour_sequence(cand.ncolours))
-                            launch_schwarz_colourL<V, T>(cand, c, d.f.p, d.x.p, s);
+                float ms = 0.f;
+                try {
+                    ms = time_best_graph(s, 5, [&] {
+                        if (cand.fused) {
+                            launch_schwarz_fused<V, T>(cand, d.f.p, d.x.p, s);
+                        } else if (cand.persist > 0) {
+                            launch_schwarz_persistent<V, T>(cand, d.f.p, d.x.p, s);
+                        } else {
+                            for (int c : Engine::colour_sequence(cand.ncolours))
+                                launch_schwarz_colourL<V, T>(cand, c, d.f.p, d.x.p, s);
+                        }
+                    });
+                } catch (const CudaError& e) {
+                    // a launch configuration the driver refuses (not a device fault): skip it
+                    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                        cudaGraph_t g = nullptr;
+                        cudaStreamEndCapture(s, &g);
+                        if (g) cudaGraphDestroy(g);
                     }
-                });
+                    cudaGetLastError();
+                    if (cudaStreamSynchronize(s) != cudaSuccess) throw;
+                    continue;
+                }
                 if (take_wait_flag(h)) {   // a bounded wait gave up: never choose this mode
                     cand.bar.zero(s);
                     continue;
@@ -1022,7 +1120,17 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                     ch = m;
                     ch.kappa = kap;
                 }
+                if (smoother_mode_name(m) == "colour" && ms < best_colour) {
+                    best_colour = ms;
+                    colour_choice = m;
+                }
             }
+        }
+        // plain per-colour launches (no waits between CTAs) unless another mode is clearly faster
+        if (best_colour < 1e30f && best_colour <= 1.03f * best) {
+            const double kap = ch.kappa;
+            ch = colour_choice;
+            ch.kappa = kap;
         }
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = ch;
@@ -1031,7 +1139,12 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     // a mode whose shared-memory staging no longer fits (another device) falls back to per-colour
     // launches; the capacity queries also raise the kernels' shared-memory limits
     d.sm.persist = ch.persist;
-    if (ch.staged && schwarz_staged_cap<V, T>(d.sm) < ch.persist) ch.staged = false;
+    if (ch.cluster && !schwarz_cluster_ok<V, T>(d.sm, ch.persist)) {
+        ch.cluster = false;
+        ch.staged = false;
+        ch.persist = 0;
+    }
+    if (ch.staged && !ch.cluster && schwarz_staged_cap<V, T>(d.sm) < ch.persist) ch.staged = false;
     if (ch.stream > 0) ch.stream = std::min(ch.stream, schwarz_stream_cap<V, T>(d.sm, ch.stream_bufs));
     set_smoother_mode(d.sm, ch);
     ph.mark(s, "  smoother", l);
@@ -1231,7 +1344,9 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     check_params(prm);
     HostCSR A = to_host(Ain, s);
     HostCSR G = to_host(Gin, s);
+    ph.mark(s, "inputs to host");
     check_inputs(A, G);
+    ph.mark(s, "input checks");
     const int nthreads = host_threads();
     Params gp = graph_params(prm);
     h->errflag.alloc(1);
@@ -1473,7 +1588,8 @@ static double read_scalar(amgh_ctx* h, int slot) {
 static void harvest(amgh_ctx* h) {
     if (!h->prof.enabled) { h->vc_pending = false; return; }
     if (h->vc_pending) {
-        if (h->eng->prof_pairs) h->prof.harvest(h->eng->prof_pairs);
+        // every V-cycle since the last harvest recorded its own pairs (pool entries [0, used))
+        if (h->eng->prof_pairs) h->prof.harvest(h->prof.used);
         h->vc_pending = false;
     }
     if (h->prof.kind == K_SPMV) {
@@ -1562,9 +1678,7 @@ static amgh_status pcg_impl(amgh_ctx* h, const double* f_in, double* x_in, doubl
             launch_cg_update(n, x, r, flexible ? h->kro.p : nullptr, p, q, h->scal.p, h->partial.p, s);
             launch_reduce(h->partial.p, RED_BLOCKS, h->scal.p, SC_STORE, s);
             h->launches += 4;
-            const double rr = read_scalar(h, S_TMP);
-            harvest(h);
-            h->prof.used = 0;
+            const double rr = read_scalar(h, S_TMP);   // the V-cycles' event pairs wait for the end
             rel = std::sqrt(rr) / r0;
             if (!(rel == rel)) throw StatusError{AMGH_ERR_NOT_CONVERGED, "residual became NaN"};
             if (rel <= tol) { conv = true; break; }
@@ -2263,7 +2377,7 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
             const LevelChoice& cl = e->choice[l];
-            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.staged ? 3 : 2) : cl.stream > 0 ? 4 : 0;
+            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
         }
         return AMGH_OK;

@@ -72,6 +72,7 @@ struct DevArray {
 struct DevCSR {
     int nrows = 0, ncols = 0;
     int64_t nnz = 0;
+    int max_row = -1;   // longest row, when known (-1: unknown)
     DevArray<int32_t> ptr, idx;
     DevArray<double> val;
 };

@@ -51,6 +51,7 @@ struct SmootherL {
     bool fused = false;                       // whole sweep in one single-CTA launch
     int persist = 0;                          // > 0: whole sweep in one cooperative launch of this many CTAs
     bool staged = false;                      // persistent sweep with chunks staged by bulk copies
+    bool cluster = false;                     // ... launched as one thread-block cluster
     int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
     int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches
     int wmax = 0;                             // longest slice (in 32-wide steps), for the staging buffers

@@ -20,6 +20,13 @@ struct MultiLevel {
     DevArray<double> inv;
     DevArray<double> l1inv;
     DevArray<double> F, X, Y, R;              // n x Kp
+    // split-K colour steps (levels with long rows): the rows of each colour's stars in order, with
+    // their star, position in the star and the star's first position in the colour's list
+    bool splitk = false;
+    int max_colour_rows = 0;
+    std::vector<int32_t> colour_row_begin;    // host, ncolours + 1 (into crow)
+    DevArray<int32_t> crow, cstar, cq, cbase;
+    DevArray<double> Rc;                      // max_colour_rows x Kp
 };
 
 // kernels (multi_kernels.cu); KP = padded width, x/y row-major with leading dimension KP

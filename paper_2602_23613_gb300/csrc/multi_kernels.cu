@@ -116,6 +116,80 @@ __global__ void __launch_bounds__(256) schwarz_multi_kernel(const int32_t* __res
     }
 }
 
+// Split-K form of one colour step for levels with long rows: a CTA per (row of the colour, column
+// chunk); its 8 warps take every 8th group of 32 entries of the row, and the partial sums meet in
+// shared memory in a fixed order.  R_c[t] = F[row_t] - A[row_t, :] X on the chunk.
+template <int KPL>
+__global__ void __launch_bounds__(256) multi_resid_splitk_kernel(const int32_t* __restrict__ Aptr,
+                                                                 const int32_t* __restrict__ Aidx,
+                                                                 const double* __restrict__ Aval,
+                                                                 const int32_t* __restrict__ rows, int KP,
+                                                                 const double* __restrict__ F,
+                                                                 const double* __restrict__ X, double* __restrict__ Rc) {
+    __shared__ double part[MR_WARPS][32 * KPL];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x, row = rows[t];
+    const int cb = blockIdx.y * 32 * KPL;
+    double acc[KPL];
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) acc[j] = 0.0;
+    const int rb = Aptr[row], re = Aptr[row + 1];
+    for (int e0 = rb + 32 * wl; e0 < re; e0 += 32 * MR_WARPS) {
+        const int e = e0 + lane;
+        const int myc = e < re ? Aidx[e] : 0;
+        const double myv = e < re ? Aval[e] : 0.0;
+        const int cnt = min(32, re - e0);
+#pragma unroll 8
+        for (int q = 0; q < cnt; ++q) {
+            const int c = __shfl_sync(0xffffffffu, myc, q);
+            const double v = __shfl_sync(0xffffffffu, myv, q);
+            const double* xr = X + (int64_t)c * KP + cb + lane * KPL;
+#pragma unroll
+            for (int j = 0; j < KPL; ++j) acc[j] = fma(v, xr[j], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < KPL; ++j) part[wl][lane * KPL + j] = acc[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 32 * KPL; i += 32 * MR_WARPS) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < MR_WARPS; ++w) s += part[w][i];
+        Rc[(int64_t)t * KP + cb + i] = F[(int64_t)row * KP + cb + i] - s;
+    }
+}
+
+// x_B += A_BB^{-1} r_B, a warp per (row of the colour, column chunk); the star's residual rows are
+// consecutive in R_c starting at the star's base
+template <int KPL>
+__global__ void __launch_bounds__(256) multi_apply_kernel(int nrows_c, const int32_t* __restrict__ rows,
+                                                          const int32_t* __restrict__ rstar,
+                                                          const int32_t* __restrict__ rq,
+                                                          const int32_t* __restrict__ rbase,
+                                                          const int32_t* __restrict__ sptr,
+                                                          const int64_t* __restrict__ ioff,
+                                                          const double* __restrict__ inv, int KP,
+                                                          const double* __restrict__ Rc, double* __restrict__ X) {
+    const int t = blockIdx.x * MR_WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (t >= nrows_c) return;
+    const int cb = blockIdx.y * 32 * KPL;
+    const int j = rstar[t], q = rq[t], base = rbase[t];
+    const int b = sptr[j + 1] - sptr[j];
+    const double* iv = inv + ioff[j] + (int64_t)q * b;
+    double d[KPL];
+#pragma unroll
+    for (int u = 0; u < KPL; ++u) d[u] = 0.0;
+    for (int k = 0; k < b; ++k) {
+        const double a = iv[k];
+        const double* rr = Rc + (int64_t)(base + k) * KP + cb + lane * KPL;
+#pragma unroll
+        for (int u = 0; u < KPL; ++u) d[u] = fma(a, rr[u], d[u]);
+    }
+    double* xr = X + (int64_t)rows[t] * KP + cb + lane * KPL;
+#pragma unroll
+    for (int u = 0; u < KPL; ++u) xr[u] += d[u];
+}
+
 __global__ void star_inverse_rm_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
                                        const double* __restrict__ Aval, int nstars, const int32_t* __restrict__ star_ptr,
                                        const int32_t* __restrict__ star_idx, const int64_t* __restrict__ ioff,
@@ -228,6 +302,27 @@ void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double*
     const int nst = se - sb;
     if (nst <= 0) return;
     const int kpl = lane_width(KP);
+    if (L.splitk) {
+        const int r0 = L.colour_row_begin[colour], nr = L.colour_row_begin[colour + 1] - r0;
+        if (nr <= 0) return;
+        const unsigned chunks = (unsigned)(KP / (32 * kpl));
+        dim3 g1((unsigned)nr, chunks), g2((unsigned)((nr + MR_WARPS - 1) / MR_WARPS), chunks);
+#define AMGH_SK(K)                                                                                                 \
+    multi_resid_splitk_kernel<K><<<g1, 32 * MR_WARPS, 0, s>>>(L.A->ptr.p, L.A->idx.p, L.A->val.p, L.crow.p + r0, KP, F, \
+                                                             X, L.Rc.p);                                              \
+    multi_apply_kernel<K><<<g2, 32 * MR_WARPS, 0, s>>>(nr, L.crow.p + r0, L.cstar.p + r0, L.cq.p + r0, L.cbase.p + r0, \
+                                                      L.star_ptr.p, L.inv_off.p, L.inv.p, KP, L.Rc.p, X);
+        switch (kpl) {
+            case 1: AMGH_SK(1) break;
+            case 2: AMGH_SK(2) break;
+            case 4: AMGH_SK(4) break;
+            default: AMGH_SK(8) break;
+        }
+#undef AMGH_SK
+        AMGH_LAUNCHED();
+        AMGH_LAUNCHED();
+        return;
+    }
     const size_t shm = (size_t)L.bmax * 32 * kpl * 8;   // <= 32 x 256 doubles = 64 KB
     dim3 grid((unsigned)nst, (unsigned)(KP / (32 * kpl)));
     const int32_t* stars = L.star_list.p + sb;

@@ -213,7 +213,14 @@ __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, const
     return true;
 }
 
-template <class V, class T, int L>
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// CLUSTER: the grid is one thread-block cluster and the colour steps are ordered by the hardware
+// cluster barrier instead of the bounded grid barrier.  A CTA whose bounded copy wait gives up
+// stops computing and copying but keeps arriving at every cluster barrier, so the others finish.
+template <class V, class T, int L, bool CLUSTER>
 __global__ void __launch_bounds__(CTA_THREADS) schwarz_staged_kernel(SmootherLView<V> S, StageLayout<V> lay,
                                                                      const int32_t* __restrict__ sweep, int nsteps,
                                                                      const int32_t* __restrict__ cbeg, const T* f,
@@ -246,14 +253,14 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_staged_kernel(SmootherLVi
         const int b = st & 1;
         unsigned char* sb = dyn + b * sbytes;
         const int c = sweep[st], cta = cbeg[c] + (int)blockIdx.x;
-        if (st + 1 < nsteps) {
+        if (st + 1 < nsteps && !(CLUSTER && stop)) {
             const int cn = sweep[st + 1], ctan = cbeg[cn] + (int)blockIdx.x;
             if (ctan < cbeg[cn + 1]) {
                 if (tid == 0) stage_issue<V>(S, lay, ctan, dyn + (b ^ 1) * sbytes, &mbar[b ^ 1]);
                 pending |= 2u >> b;
             }
         }
-        if (cta < cbeg[c + 1]) {
+        if (cta < cbeg[c + 1] && !(CLUSTER && stop)) {
             // per-slot metadata and slice offsets do not depend on x
             const int64_t gslot = (int64_t)cta * SLOTS + slot;
             const int row = S.slot_row[gslot];
@@ -269,7 +276,9 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_staged_kernel(SmootherLVi
                 pending &= ~(1u << b);
             }
             __syncthreads();
-            if (stop) break;
+            if (stop) {
+                if (!CLUSTER) break;
+            } else {
             const int32_t* scol = reinterpret_cast<const int32_t*>(sb) + (st0 - s0) + lane;
             const V* sval = reinterpret_cast<const V*>(sb + lay.col_bytes()) + (st0 - s0) + lane;
             const V* sinv = reinterpret_cast<const V*>(sb + lay.col_bytes() + lay.val_bytes());
@@ -285,8 +294,16 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_staged_kernel(SmootherLVi
                 for (int k = 0; k < bs; ++k) d = fma(widen<T>(sinv[k * SLOTS + slot]), smem_r[base + k], d);
                 x[row] += d;
             }
+            }
         }
-        if (st + 1 < nsteps && !grid_sync(bar, gen)) break;
+        if (st + 1 < nsteps) {
+            if (CLUSTER) {
+                __syncthreads();
+                cluster_sync_all();
+            } else if (!grid_sync(bar, gen)) {
+                break;
+            }
+        }
     }
     // leave no bulk copy in flight into this CTA's shared memory
     for (int q = 0; q < 2; ++q)
@@ -529,16 +546,62 @@ void launch_staged_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s)
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
+    if (S.cluster) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)S.persist;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_staged_kernel<V, T, L>, view(S), lay, (const int32_t*)S.sweep_d.p,
-                                 (int)S.sweep_d.n, (const int32_t*)S.colour_cta_begin_d.p, f, x, S.barrier()));
+    if (S.cluster)
+        AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_staged_kernel<V, T, L, true>, view(S), lay,
+                                     (const int32_t*)S.sweep_d.p, (int)S.sweep_d.n,
+                                     (const int32_t*)S.colour_cta_begin_d.p, f, x, S.barrier()));
+    else
+        AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_staged_kernel<V, T, L, false>, view(S), lay,
+                                     (const int32_t*)S.sweep_d.p, (int)S.sweep_d.n,
+                                     (const int32_t*)S.colour_cta_begin_d.p, f, x, S.barrier()));
+}
+
+// whether one cluster of `size` CTAs of the staged kernel can be resident with this shared memory
+template <class V, class T, int L>
+bool staged_cluster_ok_impl(int size, size_t smem) {
+    int dev = 0, maxsm = 0;
+    AMGH_CUDA(cudaGetDevice(&dev));
+    AMGH_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (size < 1 || size > 16 || smem + 4096 > (size_t)maxsm) return false;
+    auto kern = schwarz_staged_kernel<V, T, L, true>;
+    AMGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - 4096));
+    if (size > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)size);
+    cfg.blockDim = dim3(CTA_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters >= 1;
 }
 
 template <class V, class T, int L>
 int staged_cap_impl(size_t smem) {
+    auto kern = schwarz_staged_kernel<V, T, L, false>;
     int dev = 0, nsm = 0, per_sm = 0, maxsm = 0;
     AMGH_CUDA(cudaGetDevice(&dev));
     AMGH_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -546,10 +609,8 @@ int staged_cap_impl(size_t smem) {
     if (smem + 4096 > (size_t)maxsm) return 0;   // static shared memory needs the rest
     // the opt-in limit is per kernel: raise it to the device's maximum once, so that levels of
     // different staging sizes can share one instantiation
-    AMGH_CUDA(cudaFuncSetAttribute(schwarz_staged_kernel<V, T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   maxsm - 4096));
-    AMGH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_staged_kernel<V, T, L>, CTA_THREADS,
-                                                            smem));
+    AMGH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - 4096));
+    AMGH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CTA_THREADS, smem));
     return nsm * per_sm;
 }
 
@@ -698,6 +759,19 @@ int stream_cap_nbuf(const SmootherL<V>& S) {
 }
 
 template <class V, class T>
+bool schwarz_cluster_ok(const SmootherL<V>& S, int size) {
+    const size_t smem = 2 * (size_t)stage_layout(S).stage_bytes();
+    switch (S.L) {
+        case 1: return staged_cluster_ok_impl<V, T, 1>(size, smem);
+        case 2: return staged_cluster_ok_impl<V, T, 2>(size, smem);
+        case 4: return staged_cluster_ok_impl<V, T, 4>(size, smem);
+        case 8: return staged_cluster_ok_impl<V, T, 8>(size, smem);
+        case 16: return staged_cluster_ok_impl<V, T, 16>(size, smem);
+        default: return staged_cluster_ok_impl<V, T, 32>(size, smem);
+    }
+}
+
+template <class V, class T>
 int schwarz_stream_cap(const SmootherL<V>& S, int nbuf) {
     if (S.bmax > STREAM_BMAX || S.wmax < 1) return 0;
     return nbuf == 1 ? stream_cap_nbuf<V, T, 1>(S) : stream_cap_nbuf<V, T, 2>(S);
@@ -775,7 +849,8 @@ void launch_star_kappa(const DevCSR& A, int nstars, const int32_t* star_ptr, con
     template void launch_schwarz_persistent<V, T>(const SmootherL<V>&, const T*, T*, cudaStream_t);        \
     template int schwarz_persistent_cap<V, T>(int);                                                      \
     template int schwarz_staged_cap<V, T>(const SmootherL<V>&);                                         \
-    template int schwarz_stream_cap<V, T>(const SmootherL<V>&, int);
+    template int schwarz_stream_cap<V, T>(const SmootherL<V>&, int);                                    \
+    template bool schwarz_cluster_ok<V, T>(const SmootherL<V>&, int);
 INST_SCHWARZ(double, double)
 INST_SCHWARZ(float, float)
 INST_SCHWARZ(__nv_bfloat16, float)

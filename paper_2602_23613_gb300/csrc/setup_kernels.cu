@@ -2,6 +2,8 @@
 // product (Eq. tl), star-block and coarsest inverses, l1 row norms, SELL layouts.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace amgh {
@@ -115,6 +117,89 @@ __global__ void patch_solve_kernel(const int32_t* __restrict__ Aptr, const int32
     }
 }
 
+// Small patches (at most WARP_PATCH DoFs): a warp per coarse edge, four per CTA, the same
+// L D L^T factorisation and solves with warp-level synchronisation only; each lane owns the rows
+// i = lane, lane + 32 of the trailing update.
+constexpr int WARP_PATCH = 48;
+
+constexpr int PATCH_WARPS = 4;   // 4 x 10.4 KB of static shared memory per CTA
+
+__global__ void __launch_bounds__(32 * PATCH_WARPS) patch_solve_warp_kernel(
+    const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx, const double* __restrict__ Aval, int c0,
+    int nc, const int32_t* __restrict__ edges4, const int32_t* __restrict__ patch_ptr,
+    const int32_t* __restrict__ patch_idx, const int64_t* __restrict__ pos_P, const int64_t* __restrict__ pos_PT,
+    double* __restrict__ Pval, double* __restrict__ PTval, int* err_flag) {
+    constexpr int TRI = WARP_PATCH * (WARP_PATCH + 1) / 2;
+    __shared__ double Ls[PATCH_WARPS][TRI];
+    __shared__ double ys[PATCH_WARPS][WARP_PATCH], dis[PATCH_WARPS][WARP_PATCH];
+    __shared__ int ps[PATCH_WARPS][WARP_PATCH];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = c0 + blockIdx.x * PATCH_WARPS + w;
+    if (c >= nc) return;
+    const int p0 = patch_ptr[c];
+    const int m = patch_ptr[c + 1] - p0;
+    if (m == 0) return;
+    double* L = Ls[w];
+    double* y = ys[w];
+    double* dinv = dis[w];
+    int* pidx = ps[w];
+    for (int a = lane; a < m; a += 32) pidx[a] = patch_idx[p0 + a];
+    for (int e = lane; e < tri(m); e += 32) L[e] = 0.0;
+    __syncwarp();
+    const int d1 = edges4[4 * c], s1 = edges4[4 * c + 1], d2 = edges4[4 * c + 2], s2 = edges4[4 * c + 3];
+    for (int a = lane; a < m; a += 32) {
+        const int g = pidx[a];
+        const int rb = Aptr[g], re = Aptr[g + 1];
+        for (int q = rb; q < re; ++q) {
+            const int b = bsearch_i32(pidx, 0, a + 1, Aidx[q]);
+            if (b >= 0) L[tri(a) + b] = Aval[q];
+        }
+        const int q1 = bsearch_i32(Aidx, rb, re, d1);
+        const int q2 = bsearch_i32(Aidx, rb, re, d2);
+        double rhs = 0.0;
+        if (q1 >= 0) rhs -= Aval[q1] * (double)s1;
+        if (q2 >= 0) rhs -= Aval[q2] * (double)s2;
+        y[a] = rhs;
+    }
+    bool bad = false;
+    for (int k = 0; k < m; ++k) {
+        __syncwarp();
+        const double piv = L[tri(k) + k];
+        if (!(piv > 0.0)) {
+            bad = true;
+            break;
+        }
+        const double inv = 1.0 / piv;
+        if (lane == 0) dinv[k] = inv;
+        for (int i = k + 1 + lane; i < m; i += 32) {
+            const double lik = L[tri(i) + k] * inv;
+            double* Li = L + tri(i);
+            for (int j = k + 1; j <= i; ++j) Li[j] -= lik * L[tri(j) + k];
+        }
+    }
+    if (bad) {
+        if (lane == 0) atomicExch(err_flag, 1);
+        return;
+    }
+    for (int k = 0; k < m; ++k) {
+        __syncwarp();
+        const double zk = y[k] * dinv[k];
+        for (int i = k + 1 + lane; i < m; i += 32) y[i] -= L[tri(i) + k] * zk;
+    }
+    __syncwarp();
+    for (int k = lane; k < m; k += 32) y[k] *= dinv[k];
+    for (int k = m - 1; k >= 0; --k) {
+        __syncwarp();
+        const double xk = y[k];
+        for (int i = lane; i < k; i += 32) y[i] -= L[tri(k) + i] * dinv[i] * xk;
+    }
+    __syncwarp();
+    for (int a = lane; a < m; a += 32) {
+        Pval[pos_P[p0 + a]] = y[a];
+        PTval[pos_PT[p0 + a]] = y[a];
+    }
+}
+
 // exterior entries of column c of P (and row c of P^T): s1 at DoF1, s2 at DoF2 (R^T of Alg. 3)
 __global__ void ext_scatter_kernel(int nc, const int32_t* __restrict__ edges4, const int64_t* __restrict__ ext_P,
                                    const int64_t* __restrict__ ext_PT, double* __restrict__ Pval,
@@ -151,6 +236,57 @@ __global__ void ap_kernel(int n, const int32_t* __restrict__ Aptr, const int32_t
         }
         Oval[o] = s;
     }
+}
+
+// Row-accumulating numeric product O = A P on O's known pattern: a warp per output row keeps the
+// row's columns and running sums in shared memory; for every term A(I, q) in ascending q, the
+// lanes take the entries of row q of P (distinct columns, so no two lanes touch one sum) and add
+// A(I, q) P(q, J) into the sum of J, found by binary search among the row's columns.  Every sum
+// therefore adds its terms in ascending q, as the entry-wise kernel above does.
+constexpr int ROWACC_MAX = 8192;
+
+__global__ void ap_rowacc_kernel(int n, const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
+                                 const double* __restrict__ Aval, const int32_t* __restrict__ Pptr,
+                                 const int32_t* __restrict__ Pidx, const double* __restrict__ Pval,
+                                 const int32_t* __restrict__ Optr, const int32_t* __restrict__ Oidx,
+                                 double* __restrict__ Oval, int stride) {
+    extern __shared__ double rsm[];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int row = blockIdx.x * nw + wl;
+    if (row >= n) return;   // warp-level synchronisation only
+    double* acc = rsm + (size_t)wl * stride;
+    int* oc = reinterpret_cast<int*>(rsm + (size_t)nw * stride) + (size_t)wl * stride;
+    const int ob = Optr[row], m = Optr[row + 1] - ob;
+    for (int i = lane; i < m; i += 32) {
+        oc[i] = Oidx[ob + i];
+        acc[i] = 0.0;
+    }
+    const int qb = Aptr[row], qe = Aptr[row + 1];
+    for (int q0 = qb; q0 < qe; q0 += 32) {
+        const int q = q0 + lane;
+        const bool ok = q < qe;
+        const int j = ok ? Aidx[q] : 0;
+        const double a = ok ? Aval[q] : 0.0;
+        const int pb = ok ? Pptr[j] : 0, pe = ok ? Pptr[j + 1] : 0;
+        const int cnt = min(32, qe - q0);
+        for (int t = 0; t < cnt; ++t) {
+            const double at = __shfl_sync(0xffffffffu, a, t);
+            const int b = __shfl_sync(0xffffffffu, pb, t), e = __shfl_sync(0xffffffffu, pe, t);
+            __syncwarp();
+            for (int u = b + lane; u < e; u += 32) {
+                const int J = Pidx[u];
+                int lo = 0, hi = m;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (oc[mid] < J) lo = mid + 1;
+                    else hi = mid;
+                }
+                acc[lo] = fma(at, Pval[u], acc[lo]);
+            }
+        }
+    }
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) Oval[ob + i] = acc[i];
 }
 
 __global__ void l1inv_kernel_d(int n, const int32_t* __restrict__ ptr, const double* __restrict__ val,
@@ -244,6 +380,17 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
                         const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
                         double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s) {
     if (nc == 0 || max_patch == 0) return;
+    if (max_patch <= WARP_PATCH) {
+        const int per = PATCH_WARPS, chunk = 65535 * per;
+        for (int c0 = 0; c0 < nc; c0 += chunk) {
+            const int cnt = std::min(chunk, nc - c0);
+            patch_solve_warp_kernel<<<(cnt + per - 1) / per, 32 * PATCH_WARPS, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, c0, nc, edges4,
+                                                                          patch_ptr, patch_idx, pos_P, pos_PT, Pval,
+                                                                          PTval, err_flag);
+            AMGH_LAUNCHED();
+        }
+        return;
+    }
     const size_t tri_n = (size_t)max_patch * (max_patch + 1) / 2;
     const size_t shm = tri_n * 8 + 2 * (size_t)max_patch * 8 + (size_t)max_patch * 4;
     static_assert(sizeof(int) == 4, "int");
@@ -349,6 +496,7 @@ bool spgemm_symbolic(const DevCSR& X, const DevCSR& Y, DevCSR& Z, int* flag, cud
         ptr[r + 1] = (int32_t)tot;
     }
     Z.nnz = tot;
+    Z.max_row = n > 0 ? *std::max_element(hl.begin(), hl.end()) : 0;
     Z.ptr.upload(ptr, s);
     Z.idx.alloc(std::max<int64_t>(1, tot));
     Z.val.alloc(std::max<int64_t>(1, tot));
@@ -363,6 +511,18 @@ bool spgemm_symbolic(const DevCSR& X, const DevCSR& Y, DevCSR& Z, int* flag, cud
 void launch_ap_numeric(const DevCSR& A, const DevCSR& P, DevCSR& AP, cudaStream_t s) {
     const int n = AP.nrows;
     if (n == 0) return;
+    if (AP.max_row > 0 && AP.max_row <= ROWACC_MAX) {
+        // warps per CTA so that every warp's output row (columns and sums) fits in shared memory
+        const int stride = (AP.max_row + 1) & ~1;
+        const size_t per_warp = (size_t)stride * 12;
+        const int nw = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(96 * 1024) / per_warp));
+        const size_t shm = per_warp * nw;
+        AMGH_CUDA(cudaFuncSetAttribute(ap_rowacc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        ap_rowacc_kernel<<<(n + nw - 1) / nw, 32 * nw, shm, s>>>(n, A.ptr.p, A.idx.p, A.val.p, P.ptr.p, P.idx.p,
+                                                                   P.val.p, AP.ptr.p, AP.idx.p, AP.val.p, stride);
+        AMGH_LAUNCHED();
+        return;
+    }
     const int threads = 256, warps_per_block = threads / 32;
     ap_kernel<<<(n + warps_per_block - 1) / warps_per_block, threads, 0, s>>>(
         n, A.ptr.p, A.idx.p, A.val.p, P.ptr.p, P.idx.p, P.val.p, AP.ptr.p, AP.idx.p, AP.val.p);

@@ -36,6 +36,10 @@ int schwarz_staged_cap(const SmootherL<V>& S);
 // run for this smoother
 template <class V, class T>
 int schwarz_stream_cap(const SmootherL<V>& S, int nbuf);
+// whether the staged sweep can run as one thread-block cluster of `size` CTAs (S.persist = size,
+// S.staged and S.cluster then select it): colour steps ordered by the hardware cluster barrier
+template <class V, class T>
+bool schwarz_cluster_ok(const SmootherL<V>& S, int size);
 // whether a cooperative launch can be captured into a graph and replayed on the current device
 bool cooperative_capture_works();
 
