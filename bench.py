@@ -24,9 +24,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to 1e-8 rel residual; V-cycle HBM GB/s vs 8 TB/s; FP64 vs mixed/learned"
 WORKLOAD = "hex64_checker"
-WORKLOAD_DESC = ("unit-cube 64^3 hex mesh, lowest-order Nedelec (762,048 edge DoFs), alpha on an 8^3 "
-                 "checkerboard of blocks {1, 1e4}, beta = 1e-2, f ~ U(-1,1) seed 1, x0 = 0, tol 1e-8")
-SAMPLE = "hex16_checker"   # bounded CPU sample of the same workload family (10,800 DoFs)
 
 
 def parse():
@@ -37,6 +34,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--dense-tail", type=int, default=None,
+                    help="rows at or below which the V-cycle tail is one dense operator (library default if unset)")
     ap.add_argument("--profile-setup", action="store_true",
                     help="set up once, then once more between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -109,7 +108,7 @@ def traffic_for(kernel, workload, mode):
     """dram bytes per launch from the committed ncu summary, if the kernel source and its launch
     mode are the ones that were captured."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "schwarz_kernels.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2602_23613_gb300", "csrc", "schwarz_chunk.cuh"), "rb").read()
     sha = hashlib.sha256(src).hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -125,13 +124,15 @@ def traffic_for(kernel, workload, mode):
 # ----------------------------------------------------------------------------------------------
 # CPU oracle leg (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(gpu_iters=None):
-    """Oracle setup + PCG on the 16^3 member of the workload family, scaled to the 64^3 workload
+def oracle_sample(gpu_iters=None, workload=WORKLOAD):
+    """Oracle setup + PCG on the 16^3 member of the workload family, scaled to the full workload
     by the DoF ratio (both are O(n) per iteration) and by the iteration ratio."""
     import workloads as W
     from oracle import amg as O
-    s = W.make_config(SAMPLE)
-    full_n = 3 * 64 * 63 * 63
+    _, sample = W.describe(workload)
+    s = W.make_config(sample)
+    nfull = W.CONFIGS[workload]["n"]
+    full_n = 3 * nfull * (nfull - 1) ** 2
     t0 = time.perf_counter()
     H = O.setup(s["A"], s["G"], coarse_size=100)
     _, it, _ = O.pcg(H, s["f"], tol=1e-8, maxit=1000)
@@ -141,7 +142,7 @@ def oracle_sample(gpu_iters=None):
         scale *= gpu_iters / max(it, 1)
     return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": "%s (%d DoFs): oracle setup + PCG to 1e-8 took %.2f s in %d iterations; scaled by "
-                      "DoFs %d/%d%s" % (SAMPLE, s["ndof"], t, it, full_n, s["ndof"],
+                      "DoFs %d/%d%s" % (sample, s["ndof"], t, it, full_n, s["ndof"],
                                         " and iterations %d/%d" % (gpu_iters, it) if gpu_iters else ""),
             "sample_seconds": t, "sample_iters": it}
 
@@ -149,12 +150,13 @@ def oracle_sample(gpu_iters=None):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    import workloads as W
     for _ in range(args.warmup):
-        oracle_sample()
+        oracle_sample(workload=args.workload)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_sample())
+        vals.append(oracle_sample(workload=args.workload))
     wall = time.perf_counter() - t0
     v = statistics.mean(x["value"] for x in vals)
     cb = dict(vals[-1])
@@ -162,7 +164,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "desc": WORKLOAD_DESC, "sample": SAMPLE},
+            "data": "synthetic", "config": {"workload": args.workload, "desc": W.describe(args.workload)[0],
+                                            "sample": W.describe(args.workload)[1]},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -194,20 +197,21 @@ def run_gpu(args, rank, world, local_rank):
     Ad, Gd = dcsr(A), dcsr(G)
     fd = torch.tensor(f, device=dev)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
+    extra = {} if args.dense_tail is None else {"dense_tail": args.dense_tail}
 
     if args.profile_setup:
-        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
         amgh.amgh_destroy(h)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print("profiled one setup of %s (%d DoFs)" % (args.workload, n), flush=True)
         return 0
 
     if args.profile_vcycles > 0:
-        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
         amgh.amgh_vcycle(h, fd, xd)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
@@ -219,7 +223,7 @@ def run_gpu(args, rank, world, local_rank):
         return 0
 
     def step(profile):
-        h = amgh.amgh_setup(Ad, Gd, precision=prec)
+        h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
         if profile:
             amgh.amgh_profile(h, 1, "schwarz", 0)
         xd.zero_()
@@ -275,7 +279,7 @@ def run_gpu(args, rank, world, local_rank):
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        h = amgh.amgh_setup(A, G, precision=prec)
+        h = amgh.amgh_setup(A, G, precision=prec, **extra)
         xh[:] = 0.0
         amgh.amgh_pcg_solve(h, fh, xh, 1e-8, 2000)
         amgh.amgh_destroy(h)
@@ -287,18 +291,19 @@ def run_gpu(args, rank, world, local_rank):
 
     if rank != 0:
         return 0
-    cpu = oracle_sample(gpu_iters=last["iters"])
+    cpu = oracle_sample(gpu_iters=last["iters"], workload=args.workload)
     info = last["info"]
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOAD_DESC, "n_dofs": n, "nnz": int(A.nnz),
+        "config": {"workload": args.workload, "desc": W.describe(args.workload)[0], "n_dofs": n, "nnz": int(A.nnz),
                    "precision": args.precision, "tol": 1e-8,
                    "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
                    "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
                    "level_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["precision"]],
-                   "smoother_lanes": info["lanes"], "smoother_fused": info["fused"]},
+                   "smoother_lanes": info["lanes"], "smoother_fused": info["fused"],
+                   "dense_tail_level": info["dense_tail"]},
         "pcg_iters": last["iters"], "relres": last["relres"], "converged": last["ok"],
         "solve_ms": 1000 * statistics.mean(r["solve_s"] for r in res),
         "setup_host_ms": info["setup_host_ms"], "setup_device_ms": info["setup_device_ms"],

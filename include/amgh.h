@@ -92,7 +92,7 @@ typedef struct {
                              finest) with at most this many DoFs is linear in its right-hand
                              side; it is computed once at setup, column block by column block,
                              and applied as one dense FP64 (or FP32) operator.  0 = recurse to
-                             the coarsest level every time.  Default 2048, at most 8192.       */
+                             the coarsest level every time.  Default 8192, the largest allowed. */
     amgh_mlp mlp;         /* network for AMGH_INTERP_LEARNED (see amgh_mlp_*), else NULL        */
     double rho_ref;       /* reference convergence factor of the exact local solves for the
                              learned fallback test; <= 0: measure it with an exact setup       */
@@ -291,6 +291,14 @@ amgh_status amgh_mlp_predict(amgh_mlp m, const float* X, int64_t n, float* Y);  
 amgh_status amgh_mlp_features(amgh_handle h, float* X, float* T, float* M, int64_t* n);
 const char* amgh_mlp_last_error(amgh_mlp m);
 void amgh_mlp_destroy(amgh_mlp m);
+
+/* Self-test of the device-side bounded waits (the grid barriers of the cooperative smoother
+ * sweeps): launches a two-CTA cooperative grid whose barrier expects one arrival more than the
+ * grid has, so it can never complete.  Every wait must give up after its bound (about a second),
+ * raise the error flag and return; the context stays usable.  Returns AMGH_ERR_TIMEOUT when that
+ * happened (the expected outcome), with the elapsed wall time in *seconds; any other status is a
+ * failure of the mechanism.  The paper has no counterpart. */
+amgh_status amgh_selftest_wait_timeout(double* seconds);
 
 const char* amgh_last_error(amgh_handle h);
 void amgh_destroy(amgh_handle h);

@@ -50,7 +50,8 @@ EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "am
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
            "amgh_launch_count", "amgh_last_error", "amgh_destroy",
            "amgh_mlp_create", "amgh_mlp_add_samples", "amgh_mlp_num_samples", "amgh_mlp_train", "amgh_mlp_params",
-           "amgh_mlp_loss_grad", "amgh_mlp_predict", "amgh_mlp_features", "amgh_mlp_last_error", "amgh_mlp_destroy"]
+           "amgh_mlp_loss_grad", "amgh_mlp_predict", "amgh_mlp_features", "amgh_mlp_last_error", "amgh_mlp_destroy",
+           "amgh_selftest_wait_timeout"]
 _NOT_STATUS = ("amgh_default_params", "amgh_launch_count", "amgh_last_error", "amgh_destroy", "amgh_mlp_num_samples",
                "amgh_mlp_last_error", "amgh_mlp_destroy")
 
@@ -107,6 +108,7 @@ def load():
     L.amgh_mlp_last_error.restype = ctypes.c_char_p
     L.amgh_mlp_destroy.argtypes = [P]
     L.amgh_mlp_destroy.restype = None
+    L.amgh_selftest_wait_timeout.argtypes = [ctypes.POINTER(D)]
     for name in EXPORTS:
         if name not in _NOT_STATUS:
             getattr(L, name).restype = I
@@ -347,6 +349,13 @@ def amgh_kernel_stats(h):
 
 def amgh_launch_count(h):
     return int(load().amgh_launch_count(h.ptr))
+
+
+def amgh_selftest_wait_timeout():
+    """Run the bounded-wait self-test; returns (status, seconds).  AMGH_ERR_TIMEOUT is the pass."""
+    sec = ctypes.c_double(0.0)
+    st = load().amgh_selftest_wait_timeout(ctypes.byref(sec))
+    return st, sec.value
 
 
 def amgh_last_error(h=None):

@@ -2109,7 +2109,7 @@ void amgh_default_params(amgh_params* p) {
     p->theta = 0.25;
     p->stall_ratio = 0.9;
     p->stream = nullptr;
-    p->dense_tail = 2048;
+    p->dense_tail = 8192;
     p->mlp = nullptr;
     p->rho_ref = 0.0;
 }
@@ -2634,6 +2634,29 @@ amgh_status amgh_mlp_features(amgh_handle h, float* X, float* T, float* M, int64
         AMGH_CUDA(cudaStreamSynchronize(s));
         return AMGH_OK;
     });
+}
+
+amgh_status amgh_selftest_wait_timeout(double* seconds) {
+    try {
+        cudaStream_t s = nullptr;
+        AMGH_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        DevArray<int> err;
+        err.alloc(1);
+        const double t0 = now_ms();
+        const bool fired = run_wait_timeout_probe(err.p, s);
+        const double t1 = now_ms();
+        cudaStreamDestroy(s);
+        if (seconds) *seconds = (t1 - t0) / 1000.0;
+        if (!fired) {
+            g_setup_error = "the bounded wait did not report giving up";
+            return AMGH_ERR_INVALID_ARG;
+        }
+        g_setup_error = "a device-side wait gave up (expected by this self-test)";
+        return AMGH_ERR_TIMEOUT;
+    } catch (const CudaError& e) {
+        g_setup_error = std::string("CUDA error ") + cudaGetErrorString(e.code) + " in " + e.where;
+        return AMGH_ERR_CUDA;
+    }
 }
 
 const char* amgh_mlp_last_error(amgh_mlp m) { return m ? m->err.c_str() : g_setup_error.c_str(); }

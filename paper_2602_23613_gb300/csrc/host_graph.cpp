@@ -574,19 +574,36 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     // ---- Eq. sparseP patches: components of graph(A_II) if small enough, else rings ----------
     std::vector<char> ext(n, 0);
     for (const auto& e : out.edges) ext[e.d1] = ext[e.d2] = 1;
+    // connected components of graph(A_II) by a concurrent union-find: a root is only ever linked
+    // below a smaller root (compare-and-swap), so every component ends with its smallest member as
+    // root whatever the order of the unions; finds halve paths with relaxed stores, which keep
+    // every node's parent an ancestor
     std::vector<int32_t> parent(n);
     std::iota(parent.begin(), parent.end(), 0);
-    auto find = [&](int32_t x) {
-        while (parent[x] != x) { parent[x] = parent[parent[x]]; x = parent[x]; }
-        return x;
+    int32_t* par = parent.data();
+    auto find = [par](int32_t x) {
+        for (;;) {
+            const int32_t p = __atomic_load_n(&par[x], __ATOMIC_RELAXED);
+            if (p == x) return x;
+            const int32_t gp = __atomic_load_n(&par[p], __ATOMIC_RELAXED);
+            if (gp != p) __atomic_store_n(&par[x], gp, __ATOMIC_RELAXED);
+            x = gp;
+        }
     };
+#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
     for (int r = 0; r < n; ++r) {
         if (ext[r]) continue;
         for (int32_t t = A.ptr[r]; t < A.ptr[r + 1]; ++t) {
-            int32_t c = A.idx[t];
-            if (c > r && !ext[c]) {
-                int32_t x = find(r), y = find(c);
-                if (x != y) parent[std::max(x, y)] = std::min(x, y);
+            const int32_t c = A.idx[t];
+            if (c <= r || ext[c]) continue;
+            int32_t x = r, y = c;
+            for (;;) {
+                x = find(x);
+                y = find(y);
+                if (x == y) break;
+                if (x < y) std::swap(x, y);   // link the larger root below the smaller one
+                int32_t expect = x;
+                if (__atomic_compare_exchange_n(&par[x], &expect, y, false, __ATOMIC_ACQ_REL, __ATOMIC_RELAXED)) break;
             }
         }
     }
@@ -814,40 +831,6 @@ std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
     }
     L.ncolours = ncol;
     clk.mark("stars + colouring");
-    // warp slots
-    L.colour_warp_begin.assign(ncol + 1, 0);
-    L.slot_row.clear(); L.slot_star.clear(); L.slot_base.clear(); L.slot_bsize.clear(); L.slot_pos.clear();
-    int nwarps = 0;
-    for (int c = 0; c < ncol; ++c) {
-        L.colour_warp_begin[c] = nwarps;
-        int lane = 32;   // force a new warp for the first star of the colour
-        for (int j = 0; j < ns; ++j) {
-            if (L.colour[j] != c) continue;
-            int b = GT.ptr[j + 1] - GT.ptr[j];
-            if (b == 0) continue;
-            if (lane + b > 32) {
-                // close the current warp (pad) and open a new one
-                nwarps++;
-                size_t base = (size_t)(nwarps - 1) * 32;
-                L.slot_row.resize(base + 32, -1);
-                L.slot_star.resize(base + 32, -1);
-                L.slot_base.resize(base + 32, 0);
-                L.slot_bsize.resize(base + 32, 0);
-                L.slot_pos.resize(base + 32, 0);
-                lane = 0;
-            }
-            size_t base = (size_t)(nwarps - 1) * 32;
-            for (int q = 0; q < b; ++q) {
-                L.slot_row[base + lane + q] = GT.idx[GT.ptr[j] + q];
-                L.slot_star[base + lane + q] = j;
-                L.slot_base[base + lane + q] = (int8_t)lane;
-                L.slot_bsize[base + lane + q] = (int8_t)b;
-                L.slot_pos[base + lane + q] = (int8_t)q;
-            }
-            lane += b;
-        }
-    }
-    L.colour_warp_begin[ncol] = nwarps;
     return "";
 }
 

@@ -63,13 +63,6 @@ struct StarLayout {
     int nstars = 0, ncolours = 0, max_block = 0;
     std::vector<int32_t> star_ptr, star_idx;   // star j = rows e with G(e, j) != 0, ascending
     std::vector<int32_t> colour;               // per star
-    // warp slots: stars of colour c packed, without splitting, into groups of 32 lanes
-    std::vector<int32_t> colour_warp_begin;    // ncolours + 1, in warps
-    std::vector<int32_t> slot_row;             // 32 per warp: DoF row or -1
-    std::vector<int32_t> slot_star;            // 32 per warp: star id or -1
-    std::vector<int8_t> slot_base;             // lane of the star's first row
-    std::vector<int8_t> slot_bsize;            // rows of the star
-    std::vector<int8_t> slot_pos;              // position of the row in the star
 };
 
 std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& out);

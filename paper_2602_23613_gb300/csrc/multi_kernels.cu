@@ -305,6 +305,10 @@ void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double*
     if (L.splitk) {
         const int r0 = L.colour_row_begin[colour], nr = L.colour_row_begin[colour + 1] - r0;
         if (nr <= 0) return;
+        // narrower column chunks when the colour has few rows, so that a step fills the GPU
+        int kpl_s = kpl;
+        while (kpl_s > 1 && (int64_t)nr * (KP / (32 * kpl_s)) < 4 * 152) kpl_s >>= 1;
+        const int kpl = kpl_s;
         const unsigned chunks = (unsigned)(KP / (32 * kpl));
         dim3 g1((unsigned)nr, chunks), g2((unsigned)((nr + MR_WARPS - 1) / MR_WARPS), chunks);
 #define AMGH_SK(K)                                                                                                 \

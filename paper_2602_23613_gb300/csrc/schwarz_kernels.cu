@@ -6,61 +6,13 @@
 
 #include <type_traits>
 
+#include "schwarz_chunk.cuh"
 #include "star_invert.cuh"
 #include "vcycle_kernels.h"
 
 namespace amgh {
 
 namespace {
-
-template <class T, class V> __device__ __forceinline__ T widen(V v) { return (T)v; }
-template <> __device__ __forceinline__ float widen<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ double widen<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
-
-template <class V> __device__ __forceinline__ V narrow(double x);
-template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
-template <> __device__ __forceinline__ float narrow<float>(double x) { return (float)x; }
-template <> __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(double x) { return __float2bfloat16_rn((float)x); }
-
-// One chunk (CTA) of one colour: every row slot (L lanes) forms f_i - (A x)_i for its row, the
-// star's residuals meet in shared memory, and each row applies its row of A_BB^{-1}:
-// x_B += A_BB^{-1} r_B.  Stars of one colour share no row and no coupling, so chunks of a colour
-// are independent.  All threads of the CTA call this (it holds two barriers).
-template <class V, class T, int L>
-__device__ __forceinline__ void schwarz_chunk(const SmootherLView<V>& S, int cta, const T* f, T* x, T* smem_r) {
-    constexpr int SLOTS = CTA_THREADS / L;
-    const int tid = threadIdx.x, lane = tid & 31, slot = tid / L, sub = tid % L;
-    const int64_t gslot = (int64_t)cta * SLOTS + slot;
-    const int row = S.slot_row[gslot];
-    const int slice = cta * WARPS_PER_CTA + (tid >> 5);
-    const int64_t st = S.rows.slice_ptr[slice];
-    const int w = (int)((S.rows.slice_ptr[slice + 1] - st) >> 5);
-    const int32_t* c = S.rows.col + st + lane;
-    const V* v = S.rows.val + st + lane;
-    T s = T(0);
-#pragma unroll 8
-    for (int t = 0; t < w; ++t) s = fma(widen<T>(v[32 * t]), x[c[32 * t]], s);
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (sub == 0) smem_r[slot] = row >= 0 ? f[row] - s : T(0);
-    __syncthreads();
-    if (sub == 0 && row >= 0) {
-        const int base = S.slot_base[gslot], bs = S.slot_bsize[gslot];
-        const V* iv = S.inv + (int64_t)cta * S.bmax * SLOTS + slot;
-        T d = T(0);
-        for (int k = 0; k < bs; ++k) d = fma(widen<T>(iv[(int64_t)k * SLOTS]), smem_r[base + k], d);
-        x[row] += d;
-    }
-    __syncthreads();
-}
-
-// at most 40 registers per thread: six CTAs per SM, so a colour of the finest level (about 780
-// chunks) fits in one wave
-template <class V, class T, int L>
-__global__ void __launch_bounds__(CTA_THREADS, 6) schwarz_cta_kernel(SmootherLView<V> S, int cta_begin, const T* f, T* x) {
-    __shared__ T smem_r[CTA_THREADS];
-    schwarz_chunk<V, T, L>(S, cta_begin + blockIdx.x, f, x, smem_r);
-}
 
 // Whole symmetric sweep of a small level: colours in sweep order, chunks of a colour in turn, one
 // CTA; the barriers inside schwarz_chunk order every colour after the previous one (x is read
@@ -81,7 +33,7 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_fused_kernel(SmootherLVie
 // Waits are bounded: a CTA that polls SPIN_LIMIT times raises the abort word and the error flag
 // and gives up, and every waiting CTA that sees the abort word gives up at once, so a grid whose
 // CTAs were not all resident ends with an error instead of hanging.
-constexpr long long SPIN_LIMIT = 1ll << 21;   // about a second of polling
+constexpr long long SPIN_LIMIT = 1ll << 20;   // about a second of polling
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     unsigned v;
@@ -89,13 +41,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& gen) {
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b, unsigned& gen, unsigned arrivals) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int good = 1;
         __threadfence();
-        if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
+        if (atomicAdd(b.count, 1u) == arrivals - 1) {
             atomicExch(b.count, 0u);
             __threadfence();
             atomicExch(b.gen, gen + 1);
@@ -134,8 +86,16 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_persistent_kernel(Smoothe
         const int c = sweep[st];
         for (int cta = cbeg[c] + (int)blockIdx.x; cta < cbeg[c + 1]; cta += (int)gridDim.x)
             schwarz_chunk<V, T, L>(S, cta, f, x, smem_r);
-        if (st + 1 < nsteps && !grid_sync(bar, gen)) return;
+        if (st + 1 < nsteps && !grid_sync(bar, gen, gridDim.x)) return;
     }
+}
+
+// Self-test of the bounded waits: a grid barrier that expects one arrival more than the grid
+// has can never complete, so every CTA's wait must give up, raise *b.err and return.
+__global__ void wait_timeout_probe_kernel(GridBarrier b) {
+    unsigned gen = 0;
+    if (threadIdx.x == 0) gen = ld_acquire_gpu(b.gen);
+    grid_sync(b, gen, gridDim.x + 1);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -300,7 +260,7 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_staged_kernel(SmootherLVi
             if (CLUSTER) {
                 __syncthreads();
                 cluster_sync_all();
-            } else if (!grid_sync(bar, gen)) {
+            } else if (!grid_sync(bar, gen, gridDim.x)) {
                 break;
             }
         }
@@ -464,6 +424,28 @@ __global__ void star_inverseL_kernel(const int32_t* __restrict__ Aptr, const int
     if (lane < b)
         for (int k = 0; k < b; ++k)
             inv[((int64_t)cta * bmax + k) * slots + base + lane] = narrow<V>(sm[wl][1][lane * 33 + k]);
+}
+
+// small stars (at most 8 rows, e.g. the finest level's node stars): eight warps per CTA with
+// 8 x 9 blocks, the same Gauss-Jordan as above
+template <class V>
+__global__ void __launch_bounds__(256) star_inverse_small_kernel(
+    const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx, const double* __restrict__ Aval, int nstars,
+    const int32_t* __restrict__ star_ptr, const int32_t* __restrict__ star_idx, const int32_t* __restrict__ star_cta,
+    const int32_t* __restrict__ star_base, int slots, int bmax, V* __restrict__ inv, int* err_flag) {
+    __shared__ double sm[8][2][8 * 9];
+    __shared__ double fac[8][8];
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + wl;
+    if (j >= nstars) return;
+    const int b0 = star_ptr[j], b = star_ptr[j + 1] - b0;
+    if (b == 0) return;
+    const bool ok = star_invert_s<9>(Aptr, Aidx, Aval, star_idx, b0, b, sm[wl][0], sm[wl][1], fac[wl]);
+    if (!ok && lane == 0) atomicExch(err_flag, 1);
+    const int cta = star_cta[j], base = star_base[j];
+    if (lane < b)
+        for (int k = 0; k < b; ++k)
+            inv[((int64_t)cta * bmax + k) * slots + base + lane] = narrow<V>(sm[wl][1][lane * 9 + k]);
 }
 
 __global__ void star_kappa_kernel(const int32_t* __restrict__ Aptr, const int32_t* __restrict__ Aidx,
@@ -683,6 +665,29 @@ void launch_schwarz_persistent(const SmootherL<V>& S, const T* f, T* x, cudaStre
     AMGH_LAUNCHED();
 }
 
+bool run_wait_timeout_probe(int* err, cudaStream_t s) {
+    DevArray<unsigned> words;
+    words.alloc(4);
+    words.zero(s);
+    AMGH_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    GridBarrier b{words.p, words.p + 1, words.p + 2, err};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AMGH_CUDA(cudaLaunchKernelEx(&cfg, wait_timeout_probe_kernel, b));
+    AMGH_LAUNCHED();
+    int flag = 0;
+    AMGH_CUDA(cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    return flag != 0;
+}
+
 bool cooperative_capture_works() {
     int dev = 0, coop = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -830,6 +835,13 @@ void launch_star_inverseL(const DevCSR& A, int nstars, const int32_t* star_ptr, 
                           const int32_t* star_cta, const int32_t* star_base, SmootherL<V>& S, int* err_flag,
                           cudaStream_t s) {
     if (nstars == 0) return;
+    if (S.bmax <= 8) {
+        star_inverse_small_kernel<V><<<(nstars + 7) / 8, 256, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, nstars, star_ptr,
+                                                                     star_idx, star_cta, star_base, S.slots, S.bmax,
+                                                                     S.inv.p, err_flag);
+        AMGH_LAUNCHED();
+        return;
+    }
     star_inverseL_kernel<V><<<(nstars + 1) / 2, 64, 0, s>>>(A.ptr.p, A.idx.p, A.val.p, nstars, star_ptr, star_idx,
                                                             star_cta, star_base, S.slots, S.bmax, S.inv.p, err_flag);
     AMGH_LAUNCHED();

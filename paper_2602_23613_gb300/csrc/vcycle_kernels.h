@@ -40,6 +40,9 @@ int schwarz_stream_cap(const SmootherL<V>& S, int nbuf);
 // S.staged and S.cluster then select it): colour steps ordered by the hardware cluster barrier
 template <class V, class T>
 bool schwarz_cluster_ok(const SmootherL<V>& S, int size);
+// self-test: a grid barrier that can never complete (one arrival short) must give up after its
+// bounded wait and raise *err; returns whether it did (err: device int)
+bool run_wait_timeout_probe(int* err, cudaStream_t s);
 // whether a cooperative launch can be captured into a graph and replayed on the current device
 bool cooperative_capture_works();
 

@@ -17,7 +17,26 @@ CONFIGS = {
     "hex128_spheres": dict(n=128, alpha="spheres", beta=1.0, rhs_seed=2),
     # 96^3 checkerboard (12^3-element blocks), for 64 right-hand sides with seeds 0..63
     "hex96_checker": dict(n=96, alpha="checker", beta=1e-2, rhs_seed=0),
+    # 16^3 member of the inclusion family (bounded CPU samples)
+    "hex16_spheres": dict(n=16, alpha="spheres", beta=1.0, rhs_seed=2),
 }
+
+# one-line descriptions and the 16^3 member of each family (bounded CPU samples)
+DESCRIPTIONS = {
+    "checker": ("alpha on an 8^3 checkerboard of blocks {1, 1e4}", "hex16_checker"),
+    "spheres": ("log10 alpha ~ U(-3,3) per element with 64 spherical inclusions of alpha = 1e6", "hex16_spheres"),
+    "one": ("alpha = 1", "hex8_unit"),
+}
+
+
+def describe(name):
+    """(description, name of the family's bounded CPU sample) of a named workload."""
+    c = CONFIGS[name]
+    n = c["n"]
+    what, sample = DESCRIPTIONS[c["alpha"]]
+    ndof = 3 * n * (n - 1) ** 2
+    return ("unit-cube %d^3 hex mesh, lowest-order Nedelec (%s edge DoFs), %s, beta = %g, f ~ U(-1,1) seed %d, "
+            "x0 = 0, tol 1e-8" % (n, format(ndof, ","), what, c["beta"], c["rhs_seed"]), sample)
 
 
 def make_alpha(n, kind, seed=None):
