@@ -107,6 +107,7 @@ struct LevelChoice {
     bool cluster = false;  // ... and runs as one thread-block cluster (hardware barrier)
     int stream = 0;        // per-colour streaming launches of at most this many CTAs, 0: not used
     int stream_bufs = 2;   // their stage buffers per CTA
+    bool pdl = false;      // per-colour launches with programmatic dependent launch
     double kappa = 0.0;
 };
 
@@ -746,7 +747,7 @@ static std::string smoother_mode_name(const LevelChoice& m) {
     if (m.fused) return "fused";
     if (m.persist > 0) return m.cluster ? "cluster" : m.staged ? "staged" : "persistent";
     if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
-    return "colour";
+    return m.pdl ? "pdl" : "colour";
 }
 
 // launch mode of a built smoother (the layout is the same for every mode)
@@ -758,6 +759,7 @@ static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
     sm.cluster = sm.staged && m.cluster;
     sm.stream_grid = (m.fused || sm.persist > 0) ? 0 : m.stream;
     sm.stream_bufs = m.stream_bufs;
+    sm.pdl = !m.fused && sm.persist == 0 && sm.stream_grid == 0 && m.pdl;
 }
 
 template <class V>
@@ -1037,7 +1039,13 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
             m0.persist = 0;
             m0.staged = false;
             m0.stream = 0;
+            m0.pdl = false;
             modes.push_back(m0);
+            {
+                LevelChoice m = m0;
+                m.pdl = true;
+                modes.push_back(m);
+            }
             for (int nb : {2, 1}) {
                 const int scap = schwarz_stream_cap<V, T>(cand, nb);
                 for (int g : {scap, 2 * h->nsm, h->nsm}) {
@@ -2377,7 +2385,8 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
             const LevelChoice& cl = e->choice[l];
-            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4 : 0;
+            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
+                           : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
         }
         return AMGH_OK;

@@ -53,6 +53,7 @@ struct SmootherL {
     bool staged = false;                      // persistent sweep with chunks staged by bulk copies
     bool cluster = false;                     // ... launched as one thread-block cluster
     int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
+    bool pdl = false;                         // per-colour launches with programmatic dependent launch
     int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches
     int wmax = 0;                             // longest slice (in 32-wide steps), for the staging buffers
     DevArray<unsigned> bar;                   // count, generation, abort (persistent sweep)

@@ -14,6 +14,65 @@ namespace amgh {
 
 namespace {
 
+// Colour step with programmatic dependent launch: the kernel lets its successor launch at once,
+// loads everything that does not depend on the previous colour step (slot metadata, the first
+// PDL_PREFETCH entries of its row slices, its row of the block inverse), and only then waits for
+// the previous kernel's results (griddepcontrol.wait) before gathering x.  The next colour's
+// launch and its matrix loads thus overlap this one.  The arithmetic and its order are those of
+// schwarz_chunk.  The successor may only launch once every CTA of this grid has started, so the
+// head of a chain of such launches always has all its CTAs resident.
+constexpr int PDL_PREFETCH = 16;
+constexpr int PDL_BMAX = 8;
+
+template <class V, class T, int L>
+__global__ void __launch_bounds__(CTA_THREADS) schwarz_pdl_kernel(SmootherLView<V> S, int cta_begin, const T* f,
+                                                                  T* x) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int SLOTS = CTA_THREADS / L;
+    __shared__ T smem_r[CTA_THREADS];
+    const int cta = cta_begin + (int)blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, slot = tid / L, sub = tid % L;
+    const int64_t gslot = (int64_t)cta * SLOTS + slot;
+    const int row = S.slot_row[gslot];
+    const int slice = cta * WARPS_PER_CTA + (tid >> 5);
+    const int64_t st = S.rows.slice_ptr[slice];
+    const int w = (int)((S.rows.slice_ptr[slice + 1] - st) >> 5);
+    const int32_t* c = S.rows.col + st + lane;
+    const V* v = S.rows.val + st + lane;
+    int cc[PDL_PREFETCH];
+    V vv[PDL_PREFETCH];
+#pragma unroll
+    for (int q = 0; q < PDL_PREFETCH; ++q)
+        if (q < w) {
+            cc[q] = c[32 * q];
+            vv[q] = v[32 * q];
+        }
+    const int base = S.slot_base[gslot], bs = S.slot_bsize[gslot];
+    const V* iv = S.inv + (int64_t)cta * S.bmax * SLOTS + slot;
+    T ivr[PDL_BMAX];
+#pragma unroll
+    for (int k = 0; k < PDL_BMAX; ++k) ivr[k] = (sub == 0 && row >= 0 && k < bs) ? widen<T>(iv[(int64_t)k * SLOTS]) : T(0);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < PDL_PREFETCH; ++q)
+        if (q < w) s = fma(widen<T>(vv[q]), x[cc[q]], s);
+#pragma unroll 8
+    for (int t = PDL_PREFETCH; t < w; ++t) s = fma(widen<T>(v[32 * t]), x[c[32 * t]], s);
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (sub == 0) smem_r[slot] = row >= 0 ? f[row] - s : T(0);
+    __syncthreads();
+    if (sub == 0 && row >= 0) {
+        T d = T(0);
+#pragma unroll
+        for (int k = 0; k < PDL_BMAX; ++k)
+            if (k < bs) d = fma(ivr[k], smem_r[base + k], d);
+        for (int k = PDL_BMAX; k < bs; ++k) d = fma(widen<T>(iv[(int64_t)k * SLOTS]), smem_r[base + k], d);
+        x[row] += d;
+    }
+}
+
 // Whole symmetric sweep of a small level: colours in sweep order, chunks of a colour in turn, one
 // CTA; the barriers inside schwarz_chunk order every colour after the previous one (x is read
 // with ordinary coherent loads).
@@ -482,6 +541,19 @@ __global__ void star_kappa_kernel(const int32_t* __restrict__ Aptr, const int32_
 
 template <class V, class T, int L>
 void launch_colour_impl(const SmootherL<V>& S, int cb, int ce, const T* f, T* x, cudaStream_t s) {
+    if (S.pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(ce - cb));
+        cfg.blockDim = dim3(CTA_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_pdl_kernel<V, T, L>, view(S), cb, f, x));
+        return;
+    }
     schwarz_cta_kernel<V, T, L><<<ce - cb, CTA_THREADS, 0, s>>>(view(S), cb, f, x);
 }
 
