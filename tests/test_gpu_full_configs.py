@@ -1,0 +1,83 @@
+"""The batched workload at its full size, checked through properties that hold at any size (the
+oracle cannot run these sizes): 64 right-hand sides on the 96^3 checkerboard (2,599,200 DoFs) as
+one multi-RHS solve, and 32 independent systems with mesh sizes n ~ U{16..96}, each with its own
+jump field alpha in {1, 10^k}, k ~ U{1..6}, solved in one graph launch.
+
+Checked: every column / system reaches the 1e-8 relative residual of its recurrence; the true
+residual f - A x, formed with plain PyTorch sparse products in FP64, is small; sampled columns
+and systems take the iterations of the single-system solver (within one) and their solutions
+agree with it in the A-norm."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amgh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2602_23613_gb300 import build, amgh as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def torch_csr(A):
+    import torch
+    return torch.sparse_csr_tensor(torch.tensor(A.indptr, dtype=torch.int64), torch.tensor(A.indices, dtype=torch.int64),
+                                   torch.tensor(A.data), size=A.shape, device="cuda")
+
+
+def test_64_right_hand_sides_on_96_checkerboard(amgh):
+    import torch
+    p = W.make_config("hex96_checker")
+    n, k = p["ndof"], 64
+    h = amgh.amgh_setup(p["A"], p["G"])
+    F = torch.stack([torch.tensor(W.fields.rhs(n, s), device="cuda") for s in range(k)])
+    X = torch.zeros_like(F)
+    its, rels, ok = amgh.amgh_pcg_solve_multi(h, F, X, 1e-8, 500)
+    print("96^3 x 64: iterations min %d max %d" % (min(its), max(its)))
+    assert ok and max(rels) <= 1e-8
+    A = torch_csr(p["A"])
+    for c in (0, 31, 63):
+        r = F[c] - torch.mv(A, X[c])
+        tr = float(torch.linalg.norm(r) / torch.linalg.norm(F[c]))
+        x1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        it1, _, ok1 = amgh.amgh_pcg_solve(h, F[c].contiguous(), x1, 1e-8, 500)
+        d = X[c] - x1
+        en = float(torch.sqrt(torch.dot(d, torch.mv(A, d)) / torch.dot(x1, torch.mv(A, x1))))
+        print("column %d: %d iterations (single %d), true residual %.2e, A-norm difference %.2e"
+              % (c, its[c], it1, tr, en))
+        assert ok1 and abs(it1 - its[c]) <= 1
+        assert tr < 1e-5            # the FP64 floor of this problem lies near kappa(A) eps
+        assert en < 1e-6
+
+
+def test_32_uneven_systems_in_one_launch(amgh):
+    import torch
+    probs = []
+    for s in range(32):
+        nn = 16 + int(W.uniform01("sys_n", s, 1)[0] * 81)          # 16..96 hexes per side
+        kk = 1 + int(W.uniform01("sys_k", s, 1)[0] * 6)            # alpha in {1, 10^k}, k in 1..6
+        p = W.hex_problem(nn, W.fields.random_jump(nn, kk, 100 + s), 1e-2)
+        p["f"] = W.fields.rhs(p["ndof"], s)
+        probs.append(p)
+    hs = [amgh.amgh_setup(p["A"], p["G"], precision=amgh.AMGH_F32) for p in probs]
+    fs = [torch.tensor(p["f"], device="cuda") for p in probs]
+    xs = [torch.zeros_like(f) for f in fs]
+    its, rels, ok = amgh.amgh_batch_pcg_solve(hs, fs, xs, 1e-8, 1000)
+    print("32 systems, %d DoFs in all: iterations %s" % (sum(p["ndof"] for p in probs), its))
+    assert ok and max(rels) <= 1e-8
+    for i in (0, 7, 19, 31):
+        p = probs[i]
+        A = torch_csr(p["A"])
+        r = fs[i] - torch.mv(A, xs[i])
+        tr = float(torch.linalg.norm(r) / torch.linalg.norm(fs[i]))
+        x1 = torch.zeros_like(fs[i])
+        it1, _, ok1 = amgh.amgh_pcg_solve(hs[i], fs[i], x1, 1e-8, 1000)
+        assert ok1 and it1 == its[i] and torch.equal(x1, xs[i]), i
+        assert tr < 1e-4, (i, tr)

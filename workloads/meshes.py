@@ -114,10 +114,11 @@ def hex_node_index(n):
     return nid
 
 
-def _assemble(ndof, elem_dofs, Kloc, Mloc, alpha, beta):
+def _assemble(ndof, elem_dofs, Kloc, Mloc, alpha, beta, parts=True):
     """Sum alpha_e K_e + beta_e M_e over elements into sorted CSR; -1 dofs are eliminated.
 
-    Kloc/Mloc: (nl, nl) shared or (ne, nl, nl) per element."""
+    Kloc/Mloc: (nl, nl) shared or (ne, nl, nl) per element.  With parts=False the curl-curl and
+    mass parts are not assembled separately (returned as None)."""
     ne, nl = elem_dofs.shape
     rows = np.repeat(elem_dofs, nl, axis=1).ravel()
     cols = np.tile(elem_dofs, (1, nl)).ravel()
@@ -129,10 +130,12 @@ def _assemble(ndof, elem_dofs, Kloc, Mloc, alpha, beta):
         mv = (beta[:, None] * Mloc.reshape(ne, -1)).ravel()
     keep = (rows >= 0) & (cols >= 0)
     rows, cols = rows[keep], cols[keep]
-    As = sp.coo_matrix((kv[keep], (rows, cols)), shape=(ndof, ndof)).tocsr()
-    Am = sp.coo_matrix((mv[keep], (rows, cols)), shape=(ndof, ndof)).tocsr()
-    As.sum_duplicates()
-    Am.sum_duplicates()
+    As = Am = None
+    if parts:
+        As = sp.coo_matrix((kv[keep], (rows, cols)), shape=(ndof, ndof)).tocsr()
+        Am = sp.coo_matrix((mv[keep], (rows, cols)), shape=(ndof, ndof)).tocsr()
+        As.sum_duplicates()
+        Am.sum_duplicates()
     # same pattern for A, A^s, A^m: assemble the sum directly
     A = sp.coo_matrix((kv[keep] + mv[keep], (rows, cols)), shape=(ndof, ndof)).tocsr()
     A.sum_duplicates()
@@ -170,7 +173,7 @@ def hex_problem(n, alpha, beta, with_parts=False):
     for l, (d, (a, b, c)) in enumerate(HEX_LOCAL_EDGES):
         elem_dofs[:, l] = eid(d, ei + a, ej + b, ek + c)
     ndof = 3 * n * (n - 1) ** 2
-    A, As, Am = _assemble(ndof, elem_dofs, K, M, alpha, beta)
+    A, As, Am = _assemble(ndof, elem_dofs, K, M, alpha, beta, parts=with_parts)
     # gradient
     nid = hex_node_index(n)
     tail = np.empty(ndof, dtype=np.int64)
