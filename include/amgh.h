@@ -208,10 +208,13 @@ typedef struct {
                              barriers, 3 the same with chunks staged in shared memory, 4 one
                              streaming launch per colour step (chunks staged by bulk copies),
                              5 staged chunks in one thread-block cluster (hardware barrier),
-                             6 one launch per colour step with programmatic dependent launch.
+                             6 one launch per colour step with programmatic dependent launch,
+                             7 one cluster of 512-thread CTAs prefetching each step's matrix
+                             entries into registers before the hardware cluster barrier.
                              The autotuner picks the fastest; AMGH_TUNE=0 disables tuning and
                              AMGH_SMOOTHER_MODE=colour|pdl|stream1|stream2|fused|persistent|
-                             staged|cluster restricts it to one mode where the level has it.  */
+                             staged|cluster|cluster2 restricts it to one mode where the level
+                             has it.                                                          */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
                                (coarsest level: of its matrix); estimated only when a reduced
                                precision is requested, else 0 (coarsest level: always)          */

@@ -108,6 +108,7 @@ struct LevelChoice {
     int stream = 0;        // per-colour streaming launches of at most this many CTAs, 0: not used
     int stream_bufs = 2;   // their stage buffers per CTA
     bool pdl = false;      // per-colour launches with programmatic dependent launch
+    int cluster2 = 0;      // register-prefetching sweep in one cluster of this many 512-thread CTAs
     double kappa = 0.0;
 };
 
@@ -744,6 +745,7 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
 
 // name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
 static std::string smoother_mode_name(const LevelChoice& m) {
+    if (m.cluster2 > 0) return "cluster2";
     if (m.fused) return "fused";
     if (m.persist > 0) return m.cluster ? "cluster" : m.staged ? "staged" : "persistent";
     if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
@@ -754,8 +756,9 @@ static std::string smoother_mode_name(const LevelChoice& m) {
 template <class V>
 static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
     sm.fused = m.fused;
-    sm.persist = m.fused ? 0 : m.persist;
-    sm.staged = sm.persist > 0 && m.staged;
+    sm.cluster2 = m.fused ? 0 : m.cluster2;
+    sm.persist = m.fused ? 0 : (sm.cluster2 > 0 ? sm.cluster2 : m.persist);
+    sm.staged = sm.persist > 0 && sm.cluster2 == 0 && m.staged;
     sm.cluster = sm.staged && m.cluster;
     sm.stream_grid = (m.fused || sm.persist > 0) ? 0 : m.stream;
     sm.stream_bufs = m.stream_bufs;
@@ -1083,6 +1086,11 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                     modes.push_back(m);
                 }
             }
+            if (cand.ncolours >= 4 && maxc <= 16 && schwarz_cluster2_ok<V, T>(cand, (maxc + 1) / 2)) {
+                LevelChoice m = m0;
+                m.cluster2 = (maxc + 1) / 2;
+                modes.push_back(m);
+            }
             if (cand.ncolours >= 4 && maxc <= 8 && schwarz_cluster_ok<V, T>(cand, maxc)) {
                 LevelChoice m = m0;
                 m.persist = maxc;
@@ -1147,6 +1155,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     // a mode whose shared-memory staging no longer fits (another device) falls back to per-colour
     // launches; the capacity queries also raise the kernels' shared-memory limits
     d.sm.persist = ch.persist;
+    if (ch.cluster2 > 0 && !schwarz_cluster2_ok<V, T>(d.sm, ch.cluster2)) ch.cluster2 = 0;
     if (ch.cluster && !schwarz_cluster_ok<V, T>(d.sm, ch.persist)) {
         ch.cluster = false;
         ch.staged = false;
@@ -2385,7 +2394,8 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
             const LevelChoice& cl = e->choice[l];
-            info->fused[l] = cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
+            info->fused[l] = cl.cluster2 > 0 ? 7
+                           : cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
                            : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
         }

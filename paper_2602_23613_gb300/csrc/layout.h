@@ -52,6 +52,7 @@ struct SmootherL {
     int persist = 0;                          // > 0: whole sweep in one cooperative launch of this many CTAs
     bool staged = false;                      // persistent sweep with chunks staged by bulk copies
     bool cluster = false;                     // ... launched as one thread-block cluster
+    int cluster2 = 0;                         // > 0: register-prefetching sweep in one cluster of this many CTAs
     int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
     bool pdl = false;                         // per-colour launches with programmatic dependent launch
     int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches

@@ -47,6 +47,5 @@ void launch_coldot(const double* a, const double* b, int64_t n, int KP, double* 
 void launch_mcg_update(int64_t n, int KP, double* X, double* R, double* Rold, const double* P, const double* Q,
                        const double* alpha, cudaStream_t s);
 void launch_mp_update(int64_t n, int KP, double* P, const double* Z, const double* beta, cudaStream_t s);
-void launch_axpy_multi(int64_t n, int KP, double* X, const double* Z, cudaStream_t s);
 
 }  // namespace amgh

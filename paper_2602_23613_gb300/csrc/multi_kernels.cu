@@ -278,10 +278,6 @@ __global__ void mp_update_kernel(int64_t total, int KP, double* __restrict__ P, 
         P[t] = fma(beta[t % KP], P[t], Z[t]);
 }
 
-__global__ void axpy_multi_kernel(int64_t total, double* __restrict__ X, const double* __restrict__ Z) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
-        X[t] += Z[t];
-}
 
 }  // namespace
 
@@ -391,9 +387,5 @@ void launch_mp_update(int64_t n, int KP, double* P, const double* Z, const doubl
     AMGH_LAUNCHED();
 }
 
-void launch_axpy_multi(int64_t n, int KP, double* X, const double* Z, cudaStream_t s) {
-    axpy_multi_kernel<<<608, 256, 0, s>>>(n * KP, X, Z);
-    AMGH_LAUNCHED();
-}
 
 }  // namespace amgh

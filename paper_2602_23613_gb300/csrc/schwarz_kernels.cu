@@ -73,6 +73,112 @@ __global__ void __launch_bounds__(CTA_THREADS) schwarz_pdl_kernel(SmootherLView<
     }
 }
 
+// Whole sweep in one thread-block cluster of 512-thread CTAs, each running two chunk groups of
+// 256 threads (CTA r, group g owns chunk cbeg[c] + 2 r + g of colour c, so the cluster covers
+// colours of up to 2 x cluster-size chunks).  Before each hardware cluster barrier every thread
+// loads, for its chunk of the next colour step, its slot metadata, the first CL_PREFETCH entries
+// of its row slice and its row of the block inverse, into registers; after the barrier only the
+// x gathers, the lane reduction and the block solve remain.  The groups synchronise with named
+// barriers.  No thread waits on anything but the cluster barrier, which every thread reaches the
+// same number of times.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+constexpr int CL_PREFETCH = 16;
+constexpr int CL_BMAX = 16;
+
+template <class V, class T, int L>
+struct ClusterStep {
+    int row = -1, base = 0, bs = 0, w = 0;
+    const int32_t* c = nullptr;
+    const V* v = nullptr;
+    int cc[CL_PREFETCH];
+    V vv[CL_PREFETCH];
+    T ivr[CL_BMAX];
+};
+
+template <class V, class T, int L>
+__device__ __forceinline__ void cluster_prefetch(const SmootherLView<V>& S, int cta, bool have, int gtid,
+                                                 ClusterStep<V, T, L>& P) {
+    constexpr int SLOTS = CTA_THREADS / L;
+    const int lane = gtid & 31, slot = gtid / L, sub = gtid % L;
+    P.row = -1;
+    P.w = 0;
+    P.bs = 0;
+    if (!have) return;
+    const int64_t gslot = (int64_t)cta * SLOTS + slot;
+    P.row = S.slot_row[gslot];
+    P.base = S.slot_base[gslot];
+    P.bs = S.slot_bsize[gslot];
+    const int slice = cta * WARPS_PER_CTA + (gtid >> 5);
+    const int64_t st = S.rows.slice_ptr[slice];
+    P.w = (int)((S.rows.slice_ptr[slice + 1] - st) >> 5);
+    P.c = S.rows.col + st + lane;
+    P.v = S.rows.val + st + lane;
+#pragma unroll
+    for (int q = 0; q < CL_PREFETCH; ++q)
+        if (q < P.w) {
+            P.cc[q] = P.c[32 * q];
+            P.vv[q] = P.v[32 * q];
+        }
+    const V* iv = S.inv + (int64_t)cta * S.bmax * SLOTS + slot;
+#pragma unroll
+    for (int k = 0; k < CL_BMAX; ++k)
+        P.ivr[k] = (sub == 0 && P.row >= 0 && k < P.bs) ? widen<T>(iv[(int64_t)k * SLOTS]) : T(0);
+}
+
+__device__ __forceinline__ void group_sync(int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(CTA_THREADS) : "memory");
+}
+
+template <class V, class T, int L>
+__global__ void __launch_bounds__(2 * CTA_THREADS, 1) schwarz_cluster2_kernel(SmootherLView<V> S,
+                                                                             const int32_t* __restrict__ sweep,
+                                                                             int nsteps,
+                                                                             const int32_t* __restrict__ cbeg,
+                                                                             const T* f, T* x) {
+    constexpr int SLOTS = CTA_THREADS / L;
+    __shared__ T smem_r[2][CTA_THREADS];
+    const int g = threadIdx.x / CTA_THREADS, gtid = threadIdx.x % CTA_THREADS;
+    const int lane = gtid & 31, slot = gtid / L, sub = gtid % L;
+    const int q = 2 * (int)blockIdx.x + g;
+    ClusterStep<V, T, L> P;
+    {
+        const int c0 = sweep[0], cta0 = cbeg[c0] + q;
+        cluster_prefetch<V, T, L>(S, cta0, cta0 < cbeg[c0 + 1], gtid, P);
+    }
+    for (int st = 0; st < nsteps; ++st) {
+        const int c = sweep[st], cta = cbeg[c] + q;
+        if (cta < cbeg[c + 1]) {
+            T s = T(0);
+#pragma unroll
+            for (int t = 0; t < CL_PREFETCH; ++t)
+                if (t < P.w) s = fma(widen<T>(P.vv[t]), x[P.cc[t]], s);
+#pragma unroll 8
+            for (int t = CL_PREFETCH; t < P.w; ++t) s = fma(widen<T>(P.v[32 * t]), x[P.c[32 * t]], s);
+#pragma unroll
+            for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (sub == 0) smem_r[g][slot] = P.row >= 0 ? f[P.row] - s : T(0);
+            group_sync(g);
+            if (sub == 0 && P.row >= 0) {
+                T d = T(0);
+#pragma unroll
+                for (int k = 0; k < CL_BMAX; ++k)
+                    if (k < P.bs) d = fma(P.ivr[k], smem_r[g][P.base + k], d);
+                x[P.row] += d;
+            }
+            group_sync(g);
+        }
+        if (st + 1 < nsteps) {
+            const int cn = sweep[st + 1], ctan = cbeg[cn] + q;
+            cluster_prefetch<V, T, L>(S, ctan, ctan < cbeg[cn + 1], gtid, P);
+            __syncthreads();
+            cluster_sync_all();
+        }
+    }
+}
+
 // Whole symmetric sweep of a small level: colours in sweep order, chunks of a colour in turn, one
 // CTA; the barriers inside schwarz_chunk order every colour after the previous one (x is read
 // with ordinary coherent loads).
@@ -232,9 +338,6 @@ __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity, const
     return true;
 }
 
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // CLUSTER: the grid is one thread-block cluster and the colour steps are ordered by the hardware
 // cluster barrier instead of the bounded grid barrier.  A CTA whose bounded copy wait gives up
@@ -701,6 +804,45 @@ int stream_cap_impl(size_t smem) {
 }
 
 template <class V, class T, int L>
+void launch_cluster2_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)S.cluster2);
+    cfg.blockDim = dim3(2 * CTA_THREADS);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)S.cluster2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_cluster2_kernel<V, T, L>, view(S), (const int32_t*)S.sweep_d.p,
+                                 (int)S.sweep_d.n, (const int32_t*)S.colour_cta_begin_d.p, f, x));
+}
+
+template <class V, class T, int L>
+bool cluster2_ok_impl(int size) {
+    if (size < 1 || size > 8) return false;
+    auto kern = schwarz_cluster2_kernel<V, T, L>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)size);
+    cfg.blockDim = dim3(2 * CTA_THREADS);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)size;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nclusters >= 1;
+}
+
+template <class V, class T, int L>
 int persistent_cap_impl() {
     int dev = 0, nsm = 0, per_sm = 0;
     AMGH_CUDA(cudaGetDevice(&dev));
@@ -714,6 +856,18 @@ int persistent_cap_impl() {
 
 template <class V, class T>
 void launch_schwarz_persistent(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
+    if (S.cluster2 > 0) {
+        switch (S.L) {
+            case 1: launch_cluster2_impl<V, T, 1>(S, f, x, s); break;
+            case 2: launch_cluster2_impl<V, T, 2>(S, f, x, s); break;
+            case 4: launch_cluster2_impl<V, T, 4>(S, f, x, s); break;
+            case 8: launch_cluster2_impl<V, T, 8>(S, f, x, s); break;
+            case 16: launch_cluster2_impl<V, T, 16>(S, f, x, s); break;
+            default: launch_cluster2_impl<V, T, 32>(S, f, x, s); break;
+        }
+        AMGH_LAUNCHED();
+        return;
+    }
     if (S.staged) {
         switch (S.L) {
             case 1: launch_staged_impl<V, T, 1>(S, f, x, s); break;
@@ -836,6 +990,19 @@ int stream_cap_nbuf(const SmootherL<V>& S) {
 }
 
 template <class V, class T>
+bool schwarz_cluster2_ok(const SmootherL<V>& S, int size) {
+    if (S.bmax > CL_BMAX) return false;
+    switch (S.L) {
+        case 1: return cluster2_ok_impl<V, T, 1>(size);
+        case 2: return cluster2_ok_impl<V, T, 2>(size);
+        case 4: return cluster2_ok_impl<V, T, 4>(size);
+        case 8: return cluster2_ok_impl<V, T, 8>(size);
+        case 16: return cluster2_ok_impl<V, T, 16>(size);
+        default: return cluster2_ok_impl<V, T, 32>(size);
+    }
+}
+
+template <class V, class T>
 bool schwarz_cluster_ok(const SmootherL<V>& S, int size) {
     const size_t smem = 2 * (size_t)stage_layout(S).stage_bytes();
     switch (S.L) {
@@ -934,7 +1101,8 @@ void launch_star_kappa(const DevCSR& A, int nstars, const int32_t* star_ptr, con
     template int schwarz_persistent_cap<V, T>(int);                                                      \
     template int schwarz_staged_cap<V, T>(const SmootherL<V>&);                                         \
     template int schwarz_stream_cap<V, T>(const SmootherL<V>&, int);                                    \
-    template bool schwarz_cluster_ok<V, T>(const SmootherL<V>&, int);
+    template bool schwarz_cluster_ok<V, T>(const SmootherL<V>&, int);                                   \
+    template bool schwarz_cluster2_ok<V, T>(const SmootherL<V>&, int);
 INST_SCHWARZ(double, double)
 INST_SCHWARZ(float, float)
 INST_SCHWARZ(__nv_bfloat16, float)

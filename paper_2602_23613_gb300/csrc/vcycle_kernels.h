@@ -43,6 +43,10 @@ bool schwarz_cluster_ok(const SmootherL<V>& S, int size);
 // self-test: a grid barrier that can never complete (one arrival short) must give up after its
 // bounded wait and raise *err; returns whether it did (err: device int)
 bool run_wait_timeout_probe(int* err, cudaStream_t s);
+// whether the register-prefetching sweep can run as one cluster of `size` 512-thread CTAs (two
+// chunk groups each: colours of at most 2 x size chunks; S.cluster2 = size selects it)
+template <class V, class T>
+bool schwarz_cluster2_ok(const SmootherL<V>& S, int size);
 // whether a cooperative launch can be captured into a graph and replayed on the current device
 bool cooperative_capture_works();
 

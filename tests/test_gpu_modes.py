@@ -18,8 +18,9 @@ from test_gpu_parity import level_tols, rel, vcycle_tol
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster"]
-CODE = {"colour": 0, "fused": 1, "persistent": 2, "staged": 3, "stream1": 4, "stream2": 4, "cluster": 5, "pdl": 6}
+MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster", "cluster2"]
+CODE = {"colour": 0, "fused": 1, "persistent": 2, "staged": 3, "stream1": 4, "stream2": 4, "cluster": 5, "pdl": 6,
+        "cluster2": 7}
 
 
 @pytest.fixture(scope="module")
@@ -56,7 +57,7 @@ def test_forced_mode_matches_oracle(amgh, problem, mode):
     info = amgh.amgh_info(h)
     used = [info["fused"][l] for l in range(info["levels"] - 1)]
     print("forced %s: level modes %s" % (mode, used))
-    assert CODE[mode] in used or mode in ("fused", "cluster", "persistent", "staged")
+    assert CODE[mode] in used or mode in ("fused", "cluster", "cluster2", "persistent", "staged")
     for l in range(info["levels"] - 1):
         L = H[l]
         n = L["A"].shape[0]
