@@ -1036,12 +1036,17 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
             for (int c = 0; c < cand.ncolours; ++c)
                 maxc = std::max(maxc, cand.colour_cta_begin[c + 1] - cand.colour_cta_begin[c]);
             std::vector<LevelChoice> modes;
+            // every launch-mode field starts cleared: the best choice so far must not leak into
+            // another lane count's candidates
             LevelChoice m0 = ch;
             m0.L_sm = Lc;
             m0.fused = false;
             m0.persist = 0;
             m0.staged = false;
+            m0.cluster = false;
+            m0.cluster2 = 0;
             m0.stream = 0;
+            m0.stream_bufs = 2;
             m0.pdl = false;
             modes.push_back(m0);
             {

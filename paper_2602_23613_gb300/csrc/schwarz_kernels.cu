@@ -695,6 +695,10 @@ StageLayout<V> stage_layout(const SmootherL<V>& S) {
 
 template <class V, class T, int L>
 void launch_staged_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
+    // one chunk per CTA and colour step: refuse a grid smaller than a colour
+    for (int c = 0; c < S.ncolours; ++c)
+        if (S.colour_cta_begin[c + 1] - S.colour_cta_begin[c] > S.persist)
+            throw CudaError{cudaErrorInvalidConfiguration, "staged sweep grid smaller than a colour"};
     const StageLayout<V> lay = stage_layout(S);
     const size_t smem = 2 * (size_t)lay.stage_bytes();   // opt-in limit set by schwarz_staged_cap
     cudaLaunchConfig_t cfg = {};
@@ -805,6 +809,11 @@ int stream_cap_impl(size_t smem) {
 
 template <class V, class T, int L>
 void launch_cluster2_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
+    // each of the cluster's 2 x size chunk groups owns one chunk per colour step: refuse a cluster
+    // that would leave chunks of some colour unprocessed
+    for (int c = 0; c < S.ncolours; ++c)
+        if (S.colour_cta_begin[c + 1] - S.colour_cta_begin[c] > 2 * S.cluster2)
+            throw CudaError{cudaErrorInvalidConfiguration, "cluster sweep smaller than a colour"};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)S.cluster2);
     cfg.blockDim = dim3(2 * CTA_THREADS);
