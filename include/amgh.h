@@ -92,7 +92,7 @@ typedef struct {
                              finest) with at most this many DoFs is linear in its right-hand
                              side; it is computed once at setup, column block by column block,
                              and applied as one dense FP64 (or FP32) operator.  0 = recurse to
-                             the coarsest level every time.  Default 8192, the largest allowed. */
+                             the coarsest level every time.  Default 8192, at most 16384.       */
     amgh_mlp mlp;         /* network for AMGH_INTERP_LEARNED (see amgh_mlp_*), else NULL        */
     double rho_ref;       /* reference convergence factor of the exact local solves for the
                              learned fallback test; <= 0: measure it with an exact setup       */

@@ -1308,7 +1308,7 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
 static void check_params(const amgh_params& prm) {
     if (prm.max_levels < 1 || prm.max_levels > 32 || prm.coarse_size < 1 || prm.ring < 1 || prm.p_max < 1 ||
         prm.p_max > 256 || prm.precision < 0 || prm.precision > 2 || !(prm.theta >= 0.0 && prm.theta <= 1.0) ||
-        !(prm.stall_ratio > 0.0) || prm.dense_tail < 0 || prm.dense_tail > 8192)
+        !(prm.stall_ratio > 0.0) || prm.dense_tail < 0 || prm.dense_tail > 16384)
         throw StatusError{AMGH_ERR_INVALID_ARG, "parameter out of range"};
     if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED)
         throw StatusError{AMGH_ERR_INVALID_ARG, "unknown interpolation mode"};
@@ -1416,14 +1416,11 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 cur.cz = Coarsening();
             }
         }
-        if (!coarsest) {
-            std::string msg = build_stars(cur.A, cur.G, cur.stars);
-            if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
-        }
         h->host_ms += now_ms() - t0;
         ph.mark(s, "host graph steps", l);
         if (coarsest) break;
         t0 = now_ms();
+        double t_stars = 0.0;
         Coarsening& cz = cur.cz;
         const int nc = (int)cz.edges.size();
         h->P64.emplace_back();
@@ -1461,11 +1458,20 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 launch_ext_scatter(nc, de4.p, dex.p, dext.p, P.val.p, PT.val.p, s);
                 AMGH_CUDA(cudaStreamSynchronize(s));
             }
-            double ti = 0.0;
+            // the finest P's fill time, on the stream, without a host synchronisation
+            struct FillEvents {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                ~FillEvents() {
+                    if (e0) cudaEventDestroy(e0);
+                    if (e1) cudaEventDestroy(e1);
+                }
+            } fe;
             if (l == 0) {
-                AMGH_CUDA(cudaStreamSynchronize(s));
-                ti = now_ms();
+                AMGH_CUDA(cudaEventCreate(&fe.e0));
+                AMGH_CUDA(cudaEventCreate(&fe.e1));
+                AMGH_CUDA(cudaEventRecord(fe.e0, s));
             }
+            bool solved = false;
             auto* net = static_cast<amgh_mlp_ctx*>(prm.mlp);
             if (l == 0 && prm.interp == AMGH_INTERP_LEARNED && net && maxp <= MLP_SLOTS) {
                 // the network predicts the interior values of every column of P on its patch
@@ -1482,11 +1488,23 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             } else {
                 launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
                                    h->errflag.p, s);
-                check_flag(h, "a local harmonic-extension solve");
+                solved = true;
             }
+            if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
+            // the smoother's node stars and colouring are host work: built while the solves run
+            {
+                const double ts = now_ms();
+                std::string msg = build_stars(cur.A, cur.G, cur.stars);
+                if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+                t_stars = now_ms() - ts;
+                h->host_ms += t_stars;
+            }
+            if (solved) check_flag(h, "a local harmonic-extension solve");
             if (l == 0) {
-                AMGH_CUDA(cudaStreamSynchronize(s));
-                h->interp_ms = now_ms() - ti;
+                float ms = 0.f;
+                AMGH_CUDA(cudaEventSynchronize(fe.e1));
+                AMGH_CUDA(cudaEventElapsedTime(&ms, fe.e0, fe.e1));
+                h->interp_ms = ms;
             }
         }
         ph.mark(s, "P upload + patch solves", l);
@@ -1521,7 +1539,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         AMGH_CUDA(cudaMemcpyAsync(An.idx.data(), Ac.idx.p, sizeof(int32_t) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaStreamSynchronize(s));
-        h->dev_ms += now_ms() - t0;
+        h->dev_ms += std::max(0.0, now_ms() - t0 - t_stars);
         ph.mark(s, "Galerkin + download", l);
         A = std::move(An);
         G = cz.Gc;
@@ -1560,14 +1578,13 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             e->tail = t;
             const int nt = h->hl[t].A.nrows;
             if (std::holds_alternative<LevelX<double, double>>(e->L[t])) {
-                e->tail_d.alloc((size_t)nt * nt);
-                AMGH_CUDA(cudaMemcpyAsync(e->tail_d.p, h->dense_tail_B.p, sizeof(double) * nt * nt,
-                                          cudaMemcpyDeviceToDevice, s));
+                e->tail_d = std::move(h->dense_tail_B);   // FP64 level: the engine keeps the operator
             } else {
                 e->tail_f.alloc((size_t)nt * nt);
                 launch_convert<float>(h->dense_tail_B.p, e->tail_f.p, (int64_t)nt * nt, s);
             }
             AMGH_CUDA(cudaStreamSynchronize(s));
+            h->dense_tail_B = DevArray<double>();
             ph.mark(s, "dense tail");
         }
     }
