@@ -99,7 +99,7 @@ typedef struct {
 } amgh_params;
 
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 2048. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,
@@ -210,11 +210,15 @@ typedef struct {
                              5 staged chunks in one thread-block cluster (hardware barrier),
                              6 one launch per colour step with programmatic dependent launch,
                              7 one cluster of 512-thread CTAs prefetching each step's matrix
-                             entries into registers before the hardware cluster barrier.
+                             entries into registers before the hardware cluster barrier,
+                             8 one cluster of 8 or 16 CTAs, each holding the level's x in
+                             shared memory (updated rows written to every copy through
+                             distributed shared memory), for levels whose x fits in a CTA.
                              The autotuner picks the fastest; AMGH_TUNE=0 disables tuning and
                              AMGH_SMOOTHER_MODE=colour|pdl|stream1|stream2|fused|persistent|
-                             staged|cluster|cluster2 restricts it to one mode where the level
-                             has it.                                                          */
+                             staged|cluster|cluster2|resident restricts it to one mode where
+                             the level has it (resident-<C>x<G>-L<lanes>, e.g. resident-16x2-L8:
+                             one shape of mode 8 with C CTAs of G 256-thread chunk groups).   */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
                                (coarsest level: of its matrix); estimated only when a reduced
                                precision is requested, else 0 (coarsest level: always)          */

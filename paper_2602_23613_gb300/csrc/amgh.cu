@@ -109,6 +109,8 @@ struct LevelChoice {
     int stream_bufs = 2;   // their stage buffers per CTA
     bool pdl = false;      // per-colour launches with programmatic dependent launch
     int cluster2 = 0;      // register-prefetching sweep in one cluster of this many 512-thread CTAs
+    int resident = 0;      // sweep with x in shared memory in one cluster of this many CTAs
+    int resident_g = 1;    // ... of this many 256-thread chunk groups each
     double kappa = 0.0;
 };
 
@@ -745,20 +747,29 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
 
 // name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
 static std::string smoother_mode_name(const LevelChoice& m) {
-    if (m.cluster2 > 0) return "cluster2";
     if (m.fused) return "fused";
+    if (m.resident > 0) return "resident";
+    if (m.cluster2 > 0) return "cluster2";
     if (m.persist > 0) return m.cluster ? "cluster" : m.staged ? "staged" : "persistent";
     if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
     return m.pdl ? "pdl" : "colour";
+}
+
+// the same with the resident sweep's shape: resident-<cluster CTAs>x<chunk groups>-L<lanes>
+static std::string smoother_mode_detail(const LevelChoice& m) {
+    if (m.fused || m.resident <= 0) return smoother_mode_name(m);
+    return "resident-" + std::to_string(m.resident) + "x" + std::to_string(m.resident_g) + "-L" + std::to_string(m.L_sm);
 }
 
 // launch mode of a built smoother (the layout is the same for every mode)
 template <class V>
 static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
     sm.fused = m.fused;
-    sm.cluster2 = m.fused ? 0 : m.cluster2;
-    sm.persist = m.fused ? 0 : (sm.cluster2 > 0 ? sm.cluster2 : m.persist);
-    sm.staged = sm.persist > 0 && sm.cluster2 == 0 && m.staged;
+    sm.resident = m.fused ? 0 : m.resident;
+    sm.resident_g = m.resident_g;
+    sm.cluster2 = (m.fused || sm.resident > 0) ? 0 : m.cluster2;
+    sm.persist = m.fused ? 0 : sm.resident > 0 ? sm.resident : sm.cluster2 > 0 ? sm.cluster2 : m.persist;
+    sm.staged = sm.persist > 0 && sm.cluster2 == 0 && sm.resident == 0 && m.staged;
     sm.cluster = sm.staged && m.cluster;
     sm.stream_grid = (m.fused || sm.persist > 0) ? 0 : m.stream;
     sm.stream_bufs = m.stream_bufs;
@@ -777,6 +788,7 @@ static void build_smoother(amgh_ctx* h, int l, int L, bool fused, int persist, b
     sm.nctas = pk.nctas;
     sm.bmax = std::max(1, st.max_block);
     sm.ncolours = st.ncolours;
+    sm.n = (int)hl.A.nrows;
     sm.fused = fused;
     sm.persist = fused ? 0 : persist;
     sm.bar.alloc(4);
@@ -1045,6 +1057,8 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
             m0.staged = false;
             m0.cluster = false;
             m0.cluster2 = 0;
+            m0.resident = 0;
+            m0.resident_g = 1;
             m0.stream = 0;
             m0.stream_bufs = 2;
             m0.pdl = false;
@@ -1096,6 +1110,17 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                 m.cluster2 = (maxc + 1) / 2;
                 modes.push_back(m);
             }
+            // x resident in the shared memory of one cluster: levels whose iterate fits in a CTA
+            if (cand.ncolours >= 4) {
+                for (int size : {16, 8})
+                    for (int groups : {1, 2})
+                        if (schwarz_resident_ok<V, T>(cand, size, groups)) {
+                            LevelChoice m = m0;
+                            m.resident = size;
+                            m.resident_g = groups;
+                            modes.push_back(m);
+                        }
+            }
             if (cand.ncolours >= 4 && maxc <= 8 && schwarz_cluster_ok<V, T>(cand, maxc)) {
                 LevelChoice m = m0;
                 m.persist = maxc;
@@ -1105,7 +1130,9 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
             }
             const char* force = std::getenv("AMGH_SMOOTHER_MODE");
             for (const LevelChoice& m : modes) {
-                if (force && *force && std::string(force) != smoother_mode_name(m)) continue;
+                if (force && *force && std::string(force) != smoother_mode_name(m) &&
+                    std::string(force) != smoother_mode_detail(m))
+                    continue;
                 set_smoother_mode(cand, m);
                 float ms = 0.f;
                 try {
@@ -1135,6 +1162,9 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                     cand.bar.zero(s);
                     continue;
                 }
+                if (ph.on)
+                    std::fprintf(stderr, "[amgh] L%d tune lanes %2d %-22s %9.4f ms (%d steps)\n", l, Lc,
+                                 smoother_mode_detail(m).c_str(), ms, 2 * cand.ncolours - 1);
                 if (ms < best) {
                     best = ms;
                     const double kap = ch.kappa;
@@ -1161,6 +1191,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     // launches; the capacity queries also raise the kernels' shared-memory limits
     d.sm.persist = ch.persist;
     if (ch.cluster2 > 0 && !schwarz_cluster2_ok<V, T>(d.sm, ch.cluster2)) ch.cluster2 = 0;
+    if (ch.resident > 0 && !schwarz_resident_ok<V, T>(d.sm, ch.resident, ch.resident_g)) ch.resident = 0;
     if (ch.cluster && !schwarz_cluster_ok<V, T>(d.sm, ch.persist)) {
         ch.cluster = false;
         ch.staged = false;
@@ -2416,8 +2447,8 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
             const LevelChoice& cl = e->choice[l];
-            info->fused[l] = cl.cluster2 > 0 ? 7
-                           : cl.fused ? 1 : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
+            info->fused[l] = cl.fused ? 1 : cl.resident > 0 ? 8 : cl.cluster2 > 0 ? 7
+                           : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
                            : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
         }

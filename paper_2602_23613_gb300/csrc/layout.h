@@ -53,6 +53,9 @@ struct SmootherL {
     bool staged = false;                      // persistent sweep with chunks staged by bulk copies
     bool cluster = false;                     // ... launched as one thread-block cluster
     int cluster2 = 0;                         // > 0: register-prefetching sweep in one cluster of this many CTAs
+    int resident = 0;                         // > 0: sweep with x in shared memory, one cluster of this many CTAs
+    int resident_g = 1;                       // ... each running this many 256-thread chunk groups
+    int n = 0;                                // rows of the level (the resident sweep's copy of x)
     int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
     bool pdl = false;                         // per-colour launches with programmatic dependent launch
     int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches

@@ -865,6 +865,10 @@ int persistent_cap_impl() {
 
 template <class V, class T>
 void launch_schwarz_persistent(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
+    if (S.resident > 0) {
+        launch_schwarz_resident<V, T>(S, f, x, s);
+        return;
+    }
     if (S.cluster2 > 0) {
         switch (S.L) {
             case 1: launch_cluster2_impl<V, T, 1>(S, f, x, s); break;

@@ -47,6 +47,14 @@ bool run_wait_timeout_probe(int* err, cudaStream_t s);
 // chunk groups each: colours of at most 2 x size chunks; S.cluster2 = size selects it)
 template <class V, class T>
 bool schwarz_cluster2_ok(const SmootherL<V>& S, int size);
+// whether the resident sweep can run as one cluster of `size` CTAs of `groups` x 256 threads:
+// every CTA holds x (S.n values of T) in shared memory; L = 4, 8, 16 or 32.  Raises the kernel's
+// shared-memory and cluster-size limits.  S.resident = size, S.resident_g = groups select it.
+template <class V, class T>
+bool schwarz_resident_ok(const SmootherL<V>& S, int size, int groups);
+// whole symmetric sweep with x resident in the shared memory of one thread-block cluster
+template <class V, class T>
+void launch_schwarz_resident(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s);
 // whether a cooperative launch can be captured into a graph and replayed on the current device
 bool cooperative_capture_works();
 

@@ -18,9 +18,9 @@ from test_gpu_parity import level_tols, rel, vcycle_tol
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster", "cluster2"]
+MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster", "cluster2", "resident"]
 CODE = {"colour": 0, "fused": 1, "persistent": 2, "staged": 3, "stream1": 4, "stream2": 4, "cluster": 5, "pdl": 6,
-        "cluster2": 7}
+        "cluster2": 7, "resident": 8}
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +57,7 @@ def test_forced_mode_matches_oracle(amgh, problem, mode):
     info = amgh.amgh_info(h)
     used = [info["fused"][l] for l in range(info["levels"] - 1)]
     print("forced %s: level modes %s" % (mode, used))
-    assert CODE[mode] in used or mode in ("fused", "cluster", "cluster2", "persistent", "staged")
+    assert CODE[mode] in used or mode in ("fused", "cluster", "cluster2", "persistent", "staged", "resident")
     for l in range(info["levels"] - 1):
         L = H[l]
         n = L["A"].shape[0]
@@ -73,3 +73,44 @@ def test_forced_mode_matches_oracle(amgh, problem, mode):
     z = torch.zeros_like(r)
     amgh.amgh_vcycle(h, r, z)
     assert rel(z.cpu().numpy(), O.vcycle(H, r.cpu().numpy())) < vcycle_tol(tols), mode
+
+
+RESIDENT = ["resident-%dx%d-L%d" % (c, g, l) for c in (16, 8) for g in (1, 2) for l in (4, 8, 16, 32)]
+
+
+@pytest.mark.parametrize("shape", RESIDENT)
+def test_resident_shape_matches_oracle(amgh, problem, shape):
+    """Every shape of the resident sweep (cluster size, chunk groups per CTA, lanes per row): with
+    4 lanes and two groups the rows of levels 1-2 (up to 108 entries) run past the 16 prefetched
+    entries per lane, and the finest level's colours have more chunks than the cluster has groups."""
+    import torch
+    p, H, tols = problem
+    old = os.environ.get("AMGH_SMOOTHER_MODE")
+    os.environ["AMGH_SMOOTHER_MODE"] = shape
+    try:
+        h = amgh.amgh_setup(p["A"], p["G"], dense_tail=0)
+    finally:
+        if old is None:
+            del os.environ["AMGH_SMOOTHER_MODE"]
+        else:
+            os.environ["AMGH_SMOOTHER_MODE"] = old
+    info = amgh.amgh_info(h)
+    used = [info["fused"][l] for l in range(info["levels"] - 1)]
+    lanes = [info["lanes"][l] for l in range(info["levels"] - 1)]
+    print("forced %s: level modes %s, lanes %s" % (shape, used, lanes))
+    assert 8 in used
+    for l in range(info["levels"] - 1):
+        L = H[l]
+        n = L["A"].shape[0]
+        f = W.uniform("probe", 40 + l, n)
+        x = W.uniform("probe", 60 + l, n)
+        fd, xd = torch.tensor(f, device="cuda"), torch.tensor(x, device="cuda")
+        y = torch.zeros_like(fd)
+        amgh.amgh_level_apply(h, l, 2, fd, xd, y)
+        assert rel(y.cpu().numpy(), O.smooth_pre(L, f, x.copy())) < tols[l]["smooth"], (shape, l, "pre-step")
+        amgh.amgh_level_apply(h, l, 3, fd, xd, y)
+        assert rel(y.cpu().numpy(), O.smooth_post(L, f, x.copy())) < tols[l]["smooth"], (shape, l, "post-step")
+    r = torch.tensor(W.uniform("probe", 7, p["ndof"]), device="cuda")
+    z = torch.zeros_like(r)
+    amgh.amgh_vcycle(h, r, z)
+    assert rel(z.cpu().numpy(), O.vcycle(H, r.cpu().numpy())) < vcycle_tol(tols), shape
