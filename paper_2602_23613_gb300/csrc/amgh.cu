@@ -1133,6 +1133,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                 if (force && *force && std::string(force) != smoother_mode_name(m) &&
                     std::string(force) != smoother_mode_detail(m))
                     continue;
+                if (m.resident > 0) schwarz_resident_prepare<V>(cand, m.resident, m.resident_g, s);
                 set_smoother_mode(cand, m);
                 float ms = 0.f;
                 try {
@@ -1192,6 +1193,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     d.sm.persist = ch.persist;
     if (ch.cluster2 > 0 && !schwarz_cluster2_ok<V, T>(d.sm, ch.cluster2)) ch.cluster2 = 0;
     if (ch.resident > 0 && !schwarz_resident_ok<V, T>(d.sm, ch.resident, ch.resident_g)) ch.resident = 0;
+    if (ch.resident > 0) schwarz_resident_prepare<V>(d.sm, ch.resident, ch.resident_g, s);
     if (ch.cluster && !schwarz_cluster_ok<V, T>(d.sm, ch.persist)) {
         ch.cluster = false;
         ch.staged = false;

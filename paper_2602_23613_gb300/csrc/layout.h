@@ -56,6 +56,9 @@ struct SmootherL {
     int resident = 0;                         // > 0: sweep with x in shared memory, one cluster of this many CTAs
     int resident_g = 1;                       // ... each running this many 256-thread chunk groups
     int n = 0;                                // rows of the level (the resident sweep's copy of x)
+    int rs_size = 0, rs_groups = 0;           // shape the resident item lists were built for
+    DevArray<int32_t> rs_items;               // per chunk group: (colour step, chunk) pairs in order
+    DevArray<int32_t> rs_ptr;                 // chunk group q's items: [rs_ptr[q], rs_ptr[q + 1])
     int stream_grid = 0;                      // > 0: per-colour streaming launches of at most this many CTAs
     bool pdl = false;                         // per-colour launches with programmatic dependent launch
     int stream_bufs = 2;                      // stage buffers per CTA of the streaming launches

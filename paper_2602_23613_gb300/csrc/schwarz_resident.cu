@@ -5,12 +5,21 @@
 // barrier that ends the step.  The matrix entries, slot metadata, right-hand side and block
 // inverse rows of a CTA's next chunk do not depend on x; they are loaded into registers before
 // that barrier, so after it only shared-memory gathers, the lane reduction and the block solve
-// remain.  The arithmetic and its order are those of the per-colour chunk step.
+// remain.
 //
-// Work split: the cluster's CTAs each run G chunk groups of 256 threads; group q of the Q = C G
-// groups handles chunks cbeg[c] + q, + Q, ... of colour c, so any colour size is covered.  The
-// kernel has no spin waits: every thread reaches the same sequence of cluster barriers.
+// Work split: the cluster's CTAs each run G chunk groups of 256 threads; the j-th chunk of a
+// colour step goes to group j mod Q of the Q = C G groups (group q = g C + rank, so a step's
+// first C chunks land on C different SMs), so any colour size is covered.  Each group walks its
+// own host-built list of (step, chunk) items through a software pipeline: the id of the item
+// three ahead, the slot metadata of the item two ahead, and the matrix entries, block-inverse
+// row and right-hand side of the next item are loaded while the current one computes.  The
+// residual of a lane's entries is summed in two interleaved partial sums (even and odd entries)
+// to keep two FP64 FMA chains in flight.  The kernel has no spin waits: every thread reaches the
+// same sequence of cluster barriers.
 #include <cuda_bf16.h>
+
+#include <climits>
+#include <vector>
 
 #include "schwarz_chunk.cuh"
 #include "vcycle_kernels.h"
@@ -20,7 +29,7 @@ namespace amgh {
 namespace {
 
 constexpr int RS_PREFETCH = 32;   // row-slice entries per lane held in registers (over G groups)
-constexpr int RS_BMAX = 16;       // block-inverse entries per row held in registers
+constexpr int RS_BMAX = 16;       // block-inverse entries per row held in registers (over G groups)
 
 __device__ __forceinline__ void rs_cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -59,108 +68,152 @@ __device__ __forceinline__ void rs_store_remote(float* local, unsigned rank, flo
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(ra), "f"(v) : "memory");
 }
 
-// one chunk's x-independent data, per thread
-template <class V, class T, int PF>
-struct ResidentItem {
-    int k = -1;   // chunk held, -1: none
-    int row = -1, base = 0, bs = 0, w = 0;
-    T fr = T(0);
-    const int32_t* c = nullptr;
-    const V* v = nullptr;
-    const V* iv = nullptr;
-    int cc[PF];
-    V vv[PF];
-    T ivr[RS_BMAX];
+// Where the x-independent data of one item (a chunk of a colour step) lives, per thread: its
+// slot's row, star base and size, and its warp's slice.  The loads are issued one item before
+// they are used and only read at that point, so no round trip waits in between.
+struct RsMeta {
+    int step = INT_MAX;   // colour step of the item; INT_MAX: none
+    int k = 0, row = -1, base = 0, bs = 0;
+    int64_t s0 = 0, s1 = 0;   // slice bounds (entries)
 };
 
-template <class V, class T, int L, int PF>
-__device__ __forceinline__ void resident_load(const SmootherLView<V>& S, int k, int gtid, const T* __restrict__ f,
-                                              ResidentItem<V, T, PF>& P) {
+template <class V, int L>
+__device__ __forceinline__ void rs_meta(const SmootherLView<V>& S, int2 id, int gtid, RsMeta& m) {
     constexpr int SLOTS = CTA_THREADS / L;
-    const int lane = gtid & 31, slot = gtid / L, sub = gtid % L;
-    P.k = k;
-    const int64_t gslot = (int64_t)k * SLOTS + slot;
-    P.row = S.slot_row[gslot];
-    P.base = S.slot_base[gslot];
-    P.bs = S.slot_bsize[gslot];
-    P.fr = (sub == 0 && P.row >= 0) ? f[P.row] : T(0);
-    const int slice = k * WARPS_PER_CTA + (gtid >> 5);
-    const int64_t st = S.rows.slice_ptr[slice];
-    P.w = (int)((S.rows.slice_ptr[slice + 1] - st) >> 5);
-    P.c = S.rows.col + st + lane;
-    P.v = S.rows.val + st + lane;
-#pragma unroll
-    for (int t = 0; t < PF; ++t)
-        if (t < P.w) {
-            P.cc[t] = P.c[32 * t];
-            P.vv[t] = P.v[32 * t];
-        }
-    P.iv = S.inv + (int64_t)k * S.bmax * SLOTS + slot;
-#pragma unroll
-    for (int j = 0; j < RS_BMAX; ++j)
-        P.ivr[j] = (sub == 0 && P.row >= 0 && j < P.bs) ? widen<T>(P.iv[(int64_t)j * SLOTS]) : T(0);
+    m.step = id.x;
+    m.k = id.y;
+    m.row = -1;
+    m.bs = 0;
+    m.s0 = m.s1 = 0;
+    if (id.x == INT_MAX) return;
+    const int64_t gslot = (int64_t)id.y * SLOTS + gtid / L;
+    m.row = S.slot_row[gslot];
+    m.base = S.slot_base[gslot];
+    m.bs = S.slot_bsize[gslot];
+    const int slice = id.y * WARPS_PER_CTA + (gtid >> 5);
+    m.s0 = S.rows.slice_ptr[slice];
+    m.s1 = S.rows.slice_ptr[slice + 1];
+}
+
+__device__ __forceinline__ int2 rs_id(const int2* __restrict__ items, int i, int i1) {
+    return i < i1 ? items[i] : make_int2(INT_MAX, 0);
 }
 
 template <class V, class T, int L, int G>
 __global__ void __launch_bounds__(G* CTA_THREADS, 1)
-    schwarz_resident_kernel(SmootherLView<V> S, int n, const int32_t* __restrict__ sweep, int nsteps,
-                            const int32_t* __restrict__ cbeg, const T* __restrict__ f, T* __restrict__ x) {
+    schwarz_resident_kernel(SmootherLView<V> S, int n, const int2* __restrict__ items, const int32_t* __restrict__ iptr,
+                            int nsteps, const T* __restrict__ f, T* __restrict__ x) {
     constexpr int SLOTS = CTA_THREADS / L;
     constexpr int PF = RS_PREFETCH / G;
+    constexpr int BM = RS_BMAX / G;
     extern __shared__ __align__(16) unsigned char rs_dyn[];
     T* xs = reinterpret_cast<T*>(rs_dyn);
     __shared__ T smem_r[G][CTA_THREADS];
     const unsigned rank = rs_cluster_rank(), C = rs_cluster_size();
     const int g = threadIdx.x / CTA_THREADS, gtid = threadIdx.x % CTA_THREADS;
     const int lane = gtid & 31, slot = gtid / L, sub = gtid % L;
-    const int q = (int)rank * G + g, Q = (int)C * G;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = x[i];
-    ResidentItem<V, T, PF> P;
+    // group-major: the first C chunks of a colour step go to C different CTAs
+    const int q = g * (int)C + (int)rank;
+    const int i1 = iptr[q + 1];
+    int i = iptr[q];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = x[j];
+
+    // pipeline: entries of item i (registers), metadata of items i and i+1, id of item i+2
+    RsMeta mc, mn;
+    rs_meta<V, L>(S, rs_id(items, i, i1), gtid, mc);
+    rs_meta<V, L>(S, rs_id(items, i + 1, i1), gtid, mn);
+    int2 id2 = rs_id(items, i + 2, i1);
+    int cc[PF];
+    V vv[PF];
+    T ivr[BM];
+    T fr = T(0);
     {
-        const int c0 = sweep[0], k0 = cbeg[c0] + q;
-        if (k0 < cbeg[c0 + 1]) resident_load<V, T, L, PF>(S, k0, gtid, f, P);
+        const int w = (int)((mc.s1 - mc.s0) >> 5);
+        const int32_t* cp = S.rows.col + mc.s0 + lane;
+        const V* vp = S.rows.val + mc.s0 + lane;
+#pragma unroll
+        for (int t = 0; t < PF; ++t)
+            if (t < w) {
+                cc[t] = cp[32 * t];
+                vv[t] = vp[32 * t];
+            }
+        const V* iv = S.inv + (int64_t)mc.k * S.bmax * SLOTS + slot;
+        const bool own = sub == 0 && mc.row >= 0;
+#pragma unroll
+        for (int j = 0; j < BM; ++j) ivr[j] = (own && j < mc.bs) ? widen<T>(iv[(int64_t)j * SLOTS]) : T(0);
+        fr = own ? f[mc.row] : T(0);
     }
     // every copy of x is loaded before any CTA writes into another's copy
     rs_cluster_sync();
     for (int st = 0; st < nsteps; ++st) {
-        const int c = sweep[st], end = cbeg[c + 1];
-        for (int k = cbeg[c] + q; k < end; k += Q) {
-            if (P.k != k) resident_load<V, T, L, PF>(S, k, gtid, f, P);
-            T s = T(0);
+        while (mc.step == st) {
+            // metadata two items ahead, id three items ahead
+            RsMeta m2;
+            rs_meta<V, L>(S, id2, gtid, m2);
+            const int2 id3 = rs_id(items, i + 3, i1);
+            const int w = (int)((mc.s1 - mc.s0) >> 5);
+            const int wn = (int)((mn.s1 - mn.s0) >> 5);
+            const int32_t* cpn = S.rows.col + mn.s0 + lane;
+            const V* vpn = S.rows.val + mn.s0 + lane;
+            // residual of the current item; each register is refilled with the next item's
+            // entry as soon as it has been used
+            T s0 = T(0), s1 = T(0);
 #pragma unroll
-            for (int t = 0; t < PF; ++t)
-                if (t < P.w) s = fma(widen<T>(P.vv[t]), xs[P.cc[t]], s);
-#pragma unroll 4
-            for (int t = PF; t < P.w; ++t) s = fma(widen<T>(P.v[32 * t]), xs[P.c[32 * t]], s);
+            for (int t = 0; t < PF; ++t) {
+                if (t < w) {
+                    if (t & 1) s1 = fma(widen<T>(vv[t]), xs[cc[t]], s1);
+                    else s0 = fma(widen<T>(vv[t]), xs[cc[t]], s0);
+                }
+                if (t < wn) {
+                    cc[t] = cpn[32 * t];
+                    vv[t] = vpn[32 * t];
+                }
+            }
+            {
+                const int32_t* cp = S.rows.col + mc.s0 + lane;
+                const V* vp = S.rows.val + mc.s0 + lane;
+                for (int t = PF; t < w; ++t) {
+                    if (t & 1) s1 = fma(widen<T>(vp[32 * t]), xs[cp[32 * t]], s1);
+                    else s0 = fma(widen<T>(vp[32 * t]), xs[cp[32 * t]], s0);
+                }
+            }
+            T s = s0 + s1;
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (sub == 0) smem_r[g][slot] = P.row >= 0 ? P.fr - s : T(0);
+            if (sub == 0) smem_r[g][slot] = mc.row >= 0 ? fr - s : T(0);
             rs_group_sync<G>(g);
             T xn = T(0);
-            if (sub == 0 && P.row >= 0) {
+            if (sub == 0 && mc.row >= 0) {
                 T d = T(0);
 #pragma unroll
-                for (int j = 0; j < RS_BMAX; ++j)
-                    if (j < P.bs) d = fma(P.ivr[j], smem_r[g][P.base + j], d);
-                for (int j = RS_BMAX; j < P.bs; ++j) d = fma(widen<T>(P.iv[(int64_t)j * SLOTS]), smem_r[g][P.base + j], d);
-                xn = xs[P.row] + d;
+                for (int j = 0; j < BM; ++j)
+                    if (j < mc.bs) d = fma(ivr[j], smem_r[g][mc.base + j], d);
+                const V* iv = S.inv + (int64_t)mc.k * S.bmax * SLOTS + slot;
+                for (int j = BM; j < mc.bs; ++j) d = fma(widen<T>(iv[(int64_t)j * SLOTS]), smem_r[g][mc.base + j], d);
+                xn = xs[mc.row] + d;
             }
             // the row's L lanes share its new value and write it into the cluster's copies
             xn = __shfl_sync(0xffffffffu, xn, lane - sub);
-            if (P.row >= 0)
-                for (unsigned r = (unsigned)sub; r < C; r += L) rs_store_remote(&xs[P.row], r, xn);
+            if (mc.row >= 0)
+                for (unsigned r = (unsigned)sub; r < C; r += L) rs_store_remote(&xs[mc.row], r, xn);
+            // block-inverse row and right-hand side of the next item
+            {
+                const V* iv = S.inv + (int64_t)mn.k * S.bmax * SLOTS + slot;
+                const bool own = sub == 0 && mn.row >= 0;
+#pragma unroll
+                for (int j = 0; j < BM; ++j) ivr[j] = (own && j < mn.bs) ? widen<T>(iv[(int64_t)j * SLOTS]) : T(0);
+                fr = own ? f[mn.row] : T(0);
+            }
             rs_group_sync<G>(g);
-            // the next chunk of this colour step, if any, is loaded now
-            if (k + Q < end) resident_load<V, T, L, PF>(S, k + Q, gtid, f, P);
-        }
-        if (st + 1 < nsteps) {
-            const int cn = sweep[st + 1], kn = cbeg[cn] + q;
-            if (kn < cbeg[cn + 1] && P.k != kn) resident_load<V, T, L, PF>(S, kn, gtid, f, P);
+            mc = mn;
+            mn = m2;
+            id2 = id3;
+            ++i;
         }
         rs_cluster_sync();
     }
     // after the last barrier every copy is final and no remote store is in flight
-    for (int i = (int)rank * blockDim.x + threadIdx.x; i < n; i += (int)C * blockDim.x) x[i] = xs[i];
+    for (int j = (int)rank * blockDim.x + threadIdx.x; j < n; j += (int)C * blockDim.x) x[j] = xs[j];
 }
 
 template <class V, class T, int L, int G>
@@ -183,9 +236,11 @@ void launch_resident_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t 
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = resident_config<V, T, L, G>(S.resident, S.n, attr);
     cfg.stream = s;
+    if (S.rs_size != S.resident || S.rs_groups != G)
+        throw CudaError{cudaErrorInvalidConfiguration, "resident sweep launched without its item lists"};
     AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_resident_kernel<V, T, L, G>, view(S), S.n,
-                                 (const int32_t*)S.sweep_d.p, (int)S.sweep_d.n,
-                                 (const int32_t*)S.colour_cta_begin_d.p, f, x));
+                                 reinterpret_cast<const int2*>(S.rs_items.p), (const int32_t*)S.rs_ptr.p,
+                                 (int)S.sweep_d.n, f, x));
 }
 
 // raises the kernel's shared-memory and cluster-size limits, then asks whether one cluster fits
@@ -253,6 +308,33 @@ bool schwarz_resident_ok(const SmootherL<V>& S, int size, int groups) {
     return groups == 2 ? resident_ok_g<V, T, 2>(S, size) : groups == 1 ? resident_ok_g<V, T, 1>(S, size) : false;
 }
 
+template <class V>
+void schwarz_resident_prepare(SmootherL<V>& S, int size, int groups, cudaStream_t s) {
+    if (S.rs_size == size && S.rs_groups == groups) return;
+    const int Q = size * groups, C = S.ncolours;
+    std::vector<std::vector<int32_t>> per(Q);
+    int st = 0;
+    auto add = [&](int c) {
+        for (int k = S.colour_cta_begin[c], j = 0; k < S.colour_cta_begin[c + 1]; ++k, ++j) {
+            per[j % Q].push_back(st);
+            per[j % Q].push_back(k);
+        }
+        ++st;
+    };
+    for (int c = 0; c < C; ++c) add(c);
+    for (int c = C - 2; c >= 0; --c) add(c);
+    std::vector<int32_t> items, ptr(Q + 1, 0);
+    for (int q = 0; q < Q; ++q) {
+        items.insert(items.end(), per[q].begin(), per[q].end());
+        ptr[q + 1] = (int32_t)(items.size() / 2);
+    }
+    if (items.empty()) items.assign(2, 0);   // a valid (unused) address
+    S.rs_items.upload(items, s);
+    S.rs_ptr.upload(ptr, s);
+    S.rs_size = size;
+    S.rs_groups = groups;
+}
+
 template <class V, class T>
 void launch_schwarz_resident(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
     if (S.resident_g == 2) launch_resident_g<V, T, 2>(S, f, x, s);
@@ -262,6 +344,7 @@ void launch_schwarz_resident(const SmootherL<V>& S, const T* f, T* x, cudaStream
 
 #define INST_RESIDENT(V, T)                                                                      \
     template bool schwarz_resident_ok<V, T>(const SmootherL<V>&, int, int);                     \
+    template void schwarz_resident_prepare<V>(SmootherL<V>&, int, int, cudaStream_t);           \
     template void launch_schwarz_resident<V, T>(const SmootherL<V>&, const T*, T*, cudaStream_t);
 INST_RESIDENT(double, double)
 INST_RESIDENT(float, float)

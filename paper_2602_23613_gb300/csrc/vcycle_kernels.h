@@ -52,6 +52,9 @@ bool schwarz_cluster2_ok(const SmootherL<V>& S, int size);
 // shared-memory and cluster-size limits.  S.resident = size, S.resident_g = groups select it.
 template <class V, class T>
 bool schwarz_resident_ok(const SmootherL<V>& S, int size, int groups);
+// host-built item lists of the resident sweep for that shape (kept until the shape changes)
+template <class V>
+void schwarz_resident_prepare(SmootherL<V>& S, int size, int groups, cudaStream_t s);
 // whole symmetric sweep with x resident in the shared memory of one thread-block cluster
 template <class V, class T>
 void launch_schwarz_resident(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s);
