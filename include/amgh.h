@@ -213,12 +213,15 @@ typedef struct {
                              entries into registers before the hardware cluster barrier,
                              8 one cluster of 8 or 16 CTAs, each holding the level's x in
                              shared memory (updated rows written to every copy through
-                             distributed shared memory), for levels whose x fits in a CTA.
+                             distributed shared memory), for levels whose x fits in a CTA,
+                             9 the same pipelined item walk as one cooperative grid with x in
+                             global memory and a counter barrier between colour steps.
                              The autotuner picks the fastest; AMGH_TUNE=0 disables tuning and
                              AMGH_SMOOTHER_MODE=colour|pdl|stream1|stream2|fused|persistent|
-                             staged|cluster|cluster2|resident restricts it to one mode where
-                             the level has it (resident-<C>x<G>-L<lanes>, e.g. resident-16x2-L8:
-                             one shape of mode 8 with C CTAs of G 256-thread chunk groups).   */
+                             staged|cluster|cluster2|resident|pipeline restricts it to one
+                             mode where the level has it (resident-<C>x<G>-L<lanes>, e.g.
+                             resident-16x2-L8: one shape of mode 8 with C CTAs of G 256-thread
+                             chunk groups; pipeline-<C>x<G>-L<lanes> likewise for mode 9).     */
     double block_kappa[32]; /* largest 1-norm condition estimate of the level's smoother blocks
                                (coarsest level: of its matrix); estimated only when a reduced
                                precision is requested, else 0 (coarsest level: always)          */

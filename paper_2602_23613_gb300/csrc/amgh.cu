@@ -111,6 +111,7 @@ struct LevelChoice {
     int cluster2 = 0;      // register-prefetching sweep in one cluster of this many 512-thread CTAs
     int resident = 0;      // sweep with x in shared memory in one cluster of this many CTAs
     int resident_g = 1;    // ... of this many 256-thread chunk groups each
+    bool resident_grid = false;   // ... as a cooperative grid of `resident` CTAs with x in global memory
     double kappa = 0.0;
 };
 
@@ -748,17 +749,18 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
 // name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
 static std::string smoother_mode_name(const LevelChoice& m) {
     if (m.fused) return "fused";
-    if (m.resident > 0) return "resident";
+    if (m.resident > 0) return m.resident_grid ? "pipeline" : "resident";
     if (m.cluster2 > 0) return "cluster2";
     if (m.persist > 0) return m.cluster ? "cluster" : m.staged ? "staged" : "persistent";
     if (m.stream > 0) return m.stream_bufs == 1 ? "stream1" : "stream2";
     return m.pdl ? "pdl" : "colour";
 }
 
-// the same with the resident sweep's shape: resident-<cluster CTAs>x<chunk groups>-L<lanes>
+// the same with the shape of a resident or pipelined sweep: <name>-<CTAs>x<chunk groups>-L<lanes>
 static std::string smoother_mode_detail(const LevelChoice& m) {
     if (m.fused || m.resident <= 0) return smoother_mode_name(m);
-    return "resident-" + std::to_string(m.resident) + "x" + std::to_string(m.resident_g) + "-L" + std::to_string(m.L_sm);
+    return smoother_mode_name(m) + "-" + std::to_string(m.resident) + "x" + std::to_string(m.resident_g) + "-L" +
+           std::to_string(m.L_sm);
 }
 
 // launch mode of a built smoother (the layout is the same for every mode)
@@ -767,6 +769,7 @@ static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
     sm.fused = m.fused;
     sm.resident = m.fused ? 0 : m.resident;
     sm.resident_g = m.resident_g;
+    sm.resident_grid = m.resident_grid;
     sm.cluster2 = (m.fused || sm.resident > 0) ? 0 : m.cluster2;
     sm.persist = m.fused ? 0 : sm.resident > 0 ? sm.resident : sm.cluster2 > 0 ? sm.cluster2 : m.persist;
     sm.staged = sm.persist > 0 && sm.cluster2 == 0 && sm.resident == 0 && m.staged;
@@ -1059,6 +1062,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
             m0.cluster2 = 0;
             m0.resident = 0;
             m0.resident_g = 1;
+            m0.resident_grid = false;
             m0.stream = 0;
             m0.stream_bufs = 2;
             m0.pdl = false;
@@ -1120,6 +1124,24 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
                             m.resident_g = groups;
                             modes.push_back(m);
                         }
+            }
+            // the same item walk over a cooperative grid (x in global memory, counter barrier)
+            if (cand.ncolours >= 4 && cooperative_ok(h)) {
+                for (int groups : {1, 2}) {
+                    const int cap = schwarz_pipeline_cap<V, T>(cand, groups);
+                    std::vector<int> grids;
+                    for (int gsz : {(maxc + groups - 1) / groups, h->nsm, h->nsm / 2, h->nsm / 4}) {
+                        gsz = std::min(gsz, cap);
+                        if (gsz >= 1 && std::find(grids.begin(), grids.end(), gsz) == grids.end()) grids.push_back(gsz);
+                    }
+                    for (int gsz : grids) {
+                        LevelChoice m = m0;
+                        m.resident = gsz;
+                        m.resident_g = groups;
+                        m.resident_grid = true;
+                        modes.push_back(m);
+                    }
+                }
             }
             if (cand.ncolours >= 4 && maxc <= 8 && schwarz_cluster_ok<V, T>(cand, maxc)) {
                 LevelChoice m = m0;
@@ -1192,7 +1214,10 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     // launches; the capacity queries also raise the kernels' shared-memory limits
     d.sm.persist = ch.persist;
     if (ch.cluster2 > 0 && !schwarz_cluster2_ok<V, T>(d.sm, ch.cluster2)) ch.cluster2 = 0;
-    if (ch.resident > 0 && !schwarz_resident_ok<V, T>(d.sm, ch.resident, ch.resident_g)) ch.resident = 0;
+    if (ch.resident > 0 && (ch.resident_grid ? (!cooperative_ok(h) ||
+                                                schwarz_pipeline_cap<V, T>(d.sm, ch.resident_g) < ch.resident)
+                                             : !schwarz_resident_ok<V, T>(d.sm, ch.resident, ch.resident_g)))
+        ch.resident = 0;
     if (ch.resident > 0) schwarz_resident_prepare<V>(d.sm, ch.resident, ch.resident_g, s);
     if (ch.cluster && !schwarz_cluster_ok<V, T>(d.sm, ch.persist)) {
         ch.cluster = false;
@@ -1316,9 +1341,11 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
     HostCSR h;
     h.nrows = (int)M->nrows;
     h.ncols = (int)M->ncols;
+    const double t0 = now_ms();
     h.ptr.resize(h.nrows + 1);
     h.idx.resize(M->nnz);
     h.val.resize(M->nnz);
+    const double t1 = now_ms();
     if (!M->on_device) {
         std::memcpy(h.ptr.data(), M->row_ptr, sizeof(int32_t) * (h.nrows + 1));
         if (M->nnz) {
@@ -1334,6 +1361,9 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
         }
         AMGH_CUDA(cudaStreamSynchronize(s));
     }
+    if (std::getenv("AMGH_VERBOSE"))
+        std::fprintf(stderr, "[amgh]   input %lld x %lld, %lld nonzeros: allocate %.1f ms, copy %.1f ms\n",
+                     (long long)M->nrows, (long long)M->ncols, (long long)M->nnz, t1 - t0, now_ms() - t1);
     if (h.ptr[h.nrows] != M->nnz) throw StatusError{AMGH_ERR_INVALID_ARG, "row_ptr[nrows] != nnz"};
     return h;
 }
@@ -2449,7 +2479,7 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
             info->precision[l] = e->choice[l].prec;
             info->lanes[l] = e->choice[l].L_sm;
             const LevelChoice& cl = e->choice[l];
-            info->fused[l] = cl.fused ? 1 : cl.resident > 0 ? 8 : cl.cluster2 > 0 ? 7
+            info->fused[l] = cl.fused ? 1 : cl.resident > 0 ? (cl.resident_grid ? 9 : 8) : cl.cluster2 > 0 ? 7
                            : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
                            : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;

@@ -55,6 +55,7 @@ struct SmootherL {
     int cluster2 = 0;                         // > 0: register-prefetching sweep in one cluster of this many CTAs
     int resident = 0;                         // > 0: sweep with x in shared memory, one cluster of this many CTAs
     int resident_g = 1;                       // ... each running this many 256-thread chunk groups
+    bool resident_grid = false;               // ... as a cooperative grid of `resident` CTAs, x in global memory
     int n = 0;                                // rows of the level (the resident sweep's copy of x)
     int rs_size = 0, rs_groups = 0;           // shape the resident item lists were built for
     DevArray<int32_t> rs_items;               // per chunk group: (colour step, chunk) pairs in order

@@ -99,24 +99,63 @@ __device__ __forceinline__ int2 rs_id(const int2* __restrict__ items, int i, int
     return i < i1 ? items[i] : make_int2(INT_MAX, 0);
 }
 
-template <class V, class T, int L, int G>
+// Grid-wide barrier of the pipelined sweep: each CTA adds one to a counter (zeroed before the
+// launch) with release semantics and thread 0 polls it with acquire loads until all CTAs of
+// barrier `round` have arrived.  The wait is bounded: after SPIN_LIMIT polls it raises the abort
+// word and the error flag; a CTA that sees the abort word gives up too.  False when it gave up.
+constexpr long long RS_SPIN_LIMIT = 1ll << 20;
+
+__device__ __forceinline__ unsigned rs_ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool rs_grid_sync(const GridBarrier& b, unsigned round) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(b.count) : "memory");
+        const unsigned target = round * gridDim.x;
+        long long it = 0;
+        while (rs_ld_acquire(b.count) < target) {
+            if (rs_ld_acquire(b.abort) != 0u || ++it > RS_SPIN_LIMIT) {
+                atomicExch(b.abort, 1u);
+                atomicExch(b.err, 1);
+                good = 0;
+                break;
+            }
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// GRID = false: the resident sweep (one cluster, x in every CTA's shared memory, hardware cluster
+// barrier).  GRID = true: the same pipelined item walk over a cooperative grid of any size, with x
+// in global memory (gathers from L2) and the counter barrier above, so the FP64 work of a step
+// spreads over as many SMs as the grid has CTAs.
+template <class V, class T, int L, int G, bool GRID>
 __global__ void __launch_bounds__(G* CTA_THREADS, 1)
     schwarz_resident_kernel(SmootherLView<V> S, int n, const int2* __restrict__ items, const int32_t* __restrict__ iptr,
-                            int nsteps, const T* __restrict__ f, T* __restrict__ x) {
+                            int nsteps, const T* __restrict__ f, T* __restrict__ x, GridBarrier bar) {
     constexpr int SLOTS = CTA_THREADS / L;
     constexpr int PF = RS_PREFETCH / G;
     constexpr int BM = RS_BMAX / G;
     extern __shared__ __align__(16) unsigned char rs_dyn[];
-    T* xs = reinterpret_cast<T*>(rs_dyn);
+    T* xs = GRID ? x : reinterpret_cast<T*>(rs_dyn);
     __shared__ T smem_r[G][CTA_THREADS];
-    const unsigned rank = rs_cluster_rank(), C = rs_cluster_size();
+    const unsigned rank = GRID ? blockIdx.x : rs_cluster_rank(), C = GRID ? gridDim.x : rs_cluster_size();
     const int g = threadIdx.x / CTA_THREADS, gtid = threadIdx.x % CTA_THREADS;
     const int lane = gtid & 31, slot = gtid / L, sub = gtid % L;
     // group-major: the first C chunks of a colour step go to C different CTAs
     const int q = g * (int)C + (int)rank;
     const int i1 = iptr[q + 1];
     int i = iptr[q];
-    for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = x[j];
+    if (!GRID)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) xs[j] = x[j];
 
     // pipeline: entries of item i (registers), metadata of items i and i+1, id of item i+2
     RsMeta mc, mn;
@@ -144,7 +183,7 @@ __global__ void __launch_bounds__(G* CTA_THREADS, 1)
         fr = own ? f[mc.row] : T(0);
     }
     // every copy of x is loaded before any CTA writes into another's copy
-    rs_cluster_sync();
+    if (!GRID) rs_cluster_sync();
     for (int st = 0; st < nsteps; ++st) {
         while (mc.step == st) {
             // metadata two items ahead, id three items ahead
@@ -192,10 +231,14 @@ __global__ void __launch_bounds__(G* CTA_THREADS, 1)
                 for (int j = BM; j < mc.bs; ++j) d = fma(widen<T>(iv[(int64_t)j * SLOTS]), smem_r[g][mc.base + j], d);
                 xn = xs[mc.row] + d;
             }
-            // the row's L lanes share its new value and write it into the cluster's copies
-            xn = __shfl_sync(0xffffffffu, xn, lane - sub);
-            if (mc.row >= 0)
-                for (unsigned r = (unsigned)sub; r < C; r += L) rs_store_remote(&xs[mc.row], r, xn);
+            if (GRID) {
+                if (sub == 0 && mc.row >= 0) x[mc.row] = xn;
+            } else {
+                // the row's L lanes share its new value and write it into the cluster's copies
+                xn = __shfl_sync(0xffffffffu, xn, lane - sub);
+                if (mc.row >= 0)
+                    for (unsigned r = (unsigned)sub; r < C; r += L) rs_store_remote(&xs[mc.row], r, xn);
+            }
             // block-inverse row and right-hand side of the next item
             {
                 const V* iv = S.inv + (int64_t)mn.k * S.bmax * SLOTS + slot;
@@ -210,37 +253,49 @@ __global__ void __launch_bounds__(G* CTA_THREADS, 1)
             id2 = id3;
             ++i;
         }
-        rs_cluster_sync();
+        if (GRID) {
+            if (st + 1 < nsteps && !rs_grid_sync(bar, (unsigned)st + 1u)) return;
+        } else {
+            rs_cluster_sync();
+        }
     }
+    if (GRID) return;
     // after the last barrier every copy is final and no remote store is in flight
     for (int j = (int)rank * blockDim.x + threadIdx.x; j < n; j += (int)C * blockDim.x) x[j] = xs[j];
 }
 
-template <class V, class T, int L, int G>
+template <class V, class T, int L, int G, bool GRID>
 cudaLaunchConfig_t resident_config(int size, int n, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)size);
     cfg.blockDim = dim3(G * CTA_THREADS);
-    cfg.dynamicSmemBytes = (size_t)n * sizeof(T);
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)size;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
+    cfg.dynamicSmemBytes = GRID ? 0 : (size_t)n * sizeof(T);
+    if (GRID) {
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+    } else {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)size;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+    }
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cfg;
 }
 
-template <class V, class T, int L, int G>
+template <class V, class T, int L, int G, bool GRID>
 void launch_resident_impl(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
-    cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = resident_config<V, T, L, G>(S.resident, S.n, attr);
-    cfg.stream = s;
     if (S.rs_size != S.resident || S.rs_groups != G)
         throw CudaError{cudaErrorInvalidConfiguration, "resident sweep launched without its item lists"};
-    AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_resident_kernel<V, T, L, G>, view(S), S.n,
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = resident_config<V, T, L, G, GRID>(S.resident, S.n, attr);
+    cfg.stream = s;
+    // the grid barrier counts arrivals from zero in every launch
+    if (GRID) AMGH_CUDA(cudaMemsetAsync(S.bar.p, 0, sizeof(unsigned), s));
+    AMGH_CUDA(cudaLaunchKernelEx(&cfg, schwarz_resident_kernel<V, T, L, G, GRID>, view(S), S.n,
                                  reinterpret_cast<const int2*>(S.rs_items.p), (const int32_t*)S.rs_ptr.p,
-                                 (int)S.sweep_d.n, f, x));
+                                 (int)S.sweep_d.n, f, x, S.barrier()));
 }
 
 // raises the kernel's shared-memory and cluster-size limits, then asks whether one cluster fits
@@ -253,7 +308,7 @@ bool resident_ok_impl(int size, int n) {
         cudaGetLastError();
         return false;
     }
-    auto kern = schwarz_resident_kernel<V, T, L, G>;
+    auto kern = schwarz_resident_kernel<V, T, L, G, false>;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
         cudaGetLastError();
@@ -269,13 +324,27 @@ bool resident_ok_impl(int size, int n) {
         return false;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = resident_config<V, T, L, G>(size, n, attr);
+    cudaLaunchConfig_t cfg = resident_config<V, T, L, G, false>(size, n, attr);
     int nclusters = 0;
     if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return nclusters >= 1;
+}
+
+// co-resident CTAs of the pipelined grid sweep on this device
+template <class V, class T, int L, int G>
+int pipeline_cap_impl() {
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, schwarz_resident_kernel<V, T, L, G, true>,
+                                                      G * CTA_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nsm * per_sm;
 }
 
 template <class V, class T, int G>
@@ -290,12 +359,23 @@ bool resident_ok_g(const SmootherL<V>& S, int size) {
 }
 
 template <class V, class T, int G>
+int pipeline_cap_g(const SmootherL<V>& S) {
+    switch (S.L) {
+        case 4: return pipeline_cap_impl<V, T, 4, G>();
+        case 8: return pipeline_cap_impl<V, T, 8, G>();
+        case 16: return pipeline_cap_impl<V, T, 16, G>();
+        case 32: return pipeline_cap_impl<V, T, 32, G>();
+        default: return 0;
+    }
+}
+
+template <class V, class T, int G, bool GRID>
 void launch_resident_g(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
     switch (S.L) {
-        case 4: launch_resident_impl<V, T, 4, G>(S, f, x, s); break;
-        case 8: launch_resident_impl<V, T, 8, G>(S, f, x, s); break;
-        case 16: launch_resident_impl<V, T, 16, G>(S, f, x, s); break;
-        case 32: launch_resident_impl<V, T, 32, G>(S, f, x, s); break;
+        case 4: launch_resident_impl<V, T, 4, G, GRID>(S, f, x, s); break;
+        case 8: launch_resident_impl<V, T, 8, G, GRID>(S, f, x, s); break;
+        case 16: launch_resident_impl<V, T, 16, G, GRID>(S, f, x, s); break;
+        case 32: launch_resident_impl<V, T, 32, G, GRID>(S, f, x, s); break;
         default: throw CudaError{cudaErrorInvalidConfiguration, "resident sweep needs 4, 8, 16 or 32 lanes per row"};
     }
 }
@@ -336,14 +416,26 @@ void schwarz_resident_prepare(SmootherL<V>& S, int size, int groups, cudaStream_
 }
 
 template <class V, class T>
+int schwarz_pipeline_cap(const SmootherL<V>& S, int groups) {
+    if (S.ncolours < 1 || S.n < 1) return 0;
+    return groups == 2 ? pipeline_cap_g<V, T, 2>(S) : groups == 1 ? pipeline_cap_g<V, T, 1>(S) : 0;
+}
+
+template <class V, class T>
 void launch_schwarz_resident(const SmootherL<V>& S, const T* f, T* x, cudaStream_t s) {
-    if (S.resident_g == 2) launch_resident_g<V, T, 2>(S, f, x, s);
-    else launch_resident_g<V, T, 1>(S, f, x, s);
+    if (S.resident_grid) {
+        if (S.resident_g == 2) launch_resident_g<V, T, 2, true>(S, f, x, s);
+        else launch_resident_g<V, T, 1, true>(S, f, x, s);
+    } else {
+        if (S.resident_g == 2) launch_resident_g<V, T, 2, false>(S, f, x, s);
+        else launch_resident_g<V, T, 1, false>(S, f, x, s);
+    }
     AMGH_LAUNCHED();
 }
 
 #define INST_RESIDENT(V, T)                                                                      \
     template bool schwarz_resident_ok<V, T>(const SmootherL<V>&, int, int);                     \
+    template int schwarz_pipeline_cap<V, T>(const SmootherL<V>&, int);                          \
     template void schwarz_resident_prepare<V>(SmootherL<V>&, int, int, cudaStream_t);           \
     template void launch_schwarz_resident<V, T>(const SmootherL<V>&, const T*, T*, cudaStream_t);
 INST_RESIDENT(double, double)

@@ -52,6 +52,11 @@ bool schwarz_cluster2_ok(const SmootherL<V>& S, int size);
 // shared-memory and cluster-size limits.  S.resident = size, S.resident_g = groups select it.
 template <class V, class T>
 bool schwarz_resident_ok(const SmootherL<V>& S, int size, int groups);
+// co-resident CTAs of the pipelined grid sweep (the resident sweep's item walk over a cooperative
+// grid, x in global memory, counter barrier; S.resident = grid, S.resident_grid select it), 0
+// when L is not 4, 8, 16 or 32
+template <class V, class T>
+int schwarz_pipeline_cap(const SmootherL<V>& S, int groups);
 // host-built item lists of the resident sweep for that shape (kept until the shape changes)
 template <class V>
 void schwarz_resident_prepare(SmootherL<V>& S, int size, int groups, cudaStream_t s);

@@ -18,9 +18,10 @@ from test_gpu_parity import level_tols, rel, vcycle_tol
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster", "cluster2", "resident"]
+MODES = ["colour", "pdl", "stream1", "stream2", "fused", "persistent", "staged", "cluster", "cluster2", "resident",
+         "pipeline"]
 CODE = {"colour": 0, "fused": 1, "persistent": 2, "staged": 3, "stream1": 4, "stream2": 4, "cluster": 5, "pdl": 6,
-        "cluster2": 7, "resident": 8}
+        "cluster2": 7, "resident": 8, "pipeline": 9}
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +58,8 @@ def test_forced_mode_matches_oracle(amgh, problem, mode):
     info = amgh.amgh_info(h)
     used = [info["fused"][l] for l in range(info["levels"] - 1)]
     print("forced %s: level modes %s" % (mode, used))
-    assert CODE[mode] in used or mode in ("fused", "cluster", "cluster2", "persistent", "staged", "resident")
+    assert CODE[mode] in used or mode in ("fused", "cluster", "cluster2", "persistent", "staged", "resident",
+                                          "pipeline")
     for l in range(info["levels"] - 1):
         L = H[l]
         n = L["A"].shape[0]
@@ -76,13 +78,15 @@ def test_forced_mode_matches_oracle(amgh, problem, mode):
 
 
 RESIDENT = ["resident-%dx%d-L%d" % (c, g, l) for c in (16, 8) for g in (1, 2) for l in (4, 8, 16, 32)]
+PIPELINE = ["pipeline-%dx%d-L%d" % (c, g, l) for c in (152, 38) for g in (1, 2) for l in (4, 32)]
 
 
-@pytest.mark.parametrize("shape", RESIDENT)
+@pytest.mark.parametrize("shape", RESIDENT + PIPELINE)
 def test_resident_shape_matches_oracle(amgh, problem, shape):
-    """Every shape of the resident sweep (cluster size, chunk groups per CTA, lanes per row): with
-    4 lanes and two groups the rows of levels 1-2 (up to 108 entries) run past the 16 prefetched
-    entries per lane, and the finest level's colours have more chunks than the cluster has groups."""
+    """Every shape of the resident sweep (cluster size, chunk groups per CTA, lanes per row) and of
+    its grid form (grid size, chunk groups, lanes): with 4 lanes and two groups the rows of levels
+    1-2 (up to 108 entries) run past the 16 prefetched entries per lane, and the finest level's
+    colours have more chunks than the cluster has groups."""
     import torch
     p, H, tols = problem
     old = os.environ.get("AMGH_SMOOTHER_MODE")
@@ -98,7 +102,7 @@ def test_resident_shape_matches_oracle(amgh, problem, shape):
     used = [info["fused"][l] for l in range(info["levels"] - 1)]
     lanes = [info["lanes"][l] for l in range(info["levels"] - 1)]
     print("forced %s: level modes %s, lanes %s" % (shape, used, lanes))
-    assert 8 in used
+    assert CODE[shape.split("-")[0]] in used
     for l in range(info["levels"] - 1):
         L = H[l]
         n = L["A"].shape[0]
