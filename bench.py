@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--profile-vcycles", type=int, default=0,
                     help="set up once, then run this many V-cycles between cudaProfilerStart/Stop and exit "
                          "(for ncu --profile-from-start off); prints no bench line")
+    ap.add_argument("--profile-level", type=int, default=-1,
+                    help="set up once, then run one pre-smoothing step of this level between "
+                         "cudaProfilerStart/Stop and exit (for ncu --profile-from-start off); prints no bench line")
     return ap.parse_args()
 
 
@@ -220,6 +223,26 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         print("profiled %d V-cycles of %s (%d DoFs)" % (args.profile_vcycles, args.workload, n), flush=True)
+        return 0
+
+    if args.profile_level >= 0:
+        h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
+        info = amgh.amgh_info(h)
+        lv = args.profile_level
+        if lv >= info["levels"] - 1:
+            raise SystemExit("level %d has no smoother (%d levels)" % (lv, info["levels"]))
+        nl = info["n"][lv]
+        fl = torch.tensor(W.uniform("probe", 1, nl), device=dev)
+        xl = torch.tensor(W.uniform("probe", 2, nl), device=dev)
+        yl = torch.zeros_like(fl)
+        amgh.amgh_level_apply(h, lv, 2, fl, xl, yl)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        amgh.amgh_level_apply(h, lv, 2, fl, xl, yl)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profiled one pre-smoothing step of level %d of %s (%d rows, %d nonzeros, launch mode %d, %d lanes)"
+              % (lv, args.workload, nl, info["nnz"][lv], info["fused"][lv], info["lanes"][lv]), flush=True)
         return 0
 
     def step(profile):
