@@ -130,6 +130,51 @@ HostCSR transpose_pattern(const HostCSR& M, bool with_values) {
     return T;
 }
 
+// The same transpose in parallel: column counts with relaxed atomic adds, a scatter through atomic
+// cursors, then each output row sorted by source row, which restores the sequential order
+// (entries of one column come from distinct rows).  Small matrices take the sequential path.
+HostCSR transpose_pattern(const HostCSR& M, bool with_values, int nthreads) {
+    if (nthreads <= 1 || M.idx.size() < (size_t)(1 << 18)) return transpose_pattern(M, with_values);
+    HostCSR T;
+    T.nrows = M.ncols;
+    T.ncols = M.nrows;
+    T.ptr.assign(T.nrows + 1, 0);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < M.nrows; ++r)
+        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) __atomic_fetch_add(&T.ptr[M.idx[e] + 1], 1, __ATOMIC_RELAXED);
+    for (int r = 0; r < T.nrows; ++r) T.ptr[r + 1] += T.ptr[r];
+    T.idx.resize(M.idx.size());
+    if (with_values) T.val.resize(M.idx.size());
+    std::vector<int32_t> cur(T.ptr.begin(), T.ptr.end() - 1);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < M.nrows; ++r)
+        for (int32_t e = M.ptr[r]; e < M.ptr[r + 1]; ++e) {
+            const int32_t p = __atomic_fetch_add(&cur[M.idx[e]], 1, __ATOMIC_RELAXED);
+            T.idx[p] = r;
+            if (with_values) T.val[p] = M.val[e];
+        }
+#pragma omp parallel num_threads(nthreads)
+    {
+        std::vector<std::pair<int32_t, double>> row;
+#pragma omp for schedule(dynamic, 4096)
+        for (int c = 0; c < T.nrows; ++c) {
+            const int32_t b = T.ptr[c], e = T.ptr[c + 1];
+            if (!with_values) {
+                std::sort(T.idx.begin() + b, T.idx.begin() + e);
+                continue;
+            }
+            row.clear();
+            for (int32_t q = b; q < e; ++q) row.push_back({T.idx[q], T.val[q]});
+            std::sort(row.begin(), row.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+            for (int32_t q = b; q < e; ++q) {
+                T.idx[q] = row[q - b].first;
+                T.val[q] = row[q - b].second;
+            }
+        }
+    }
+    return T;
+}
+
 static std::string csr_row_error(const HostCSR& M, int r) {
     if (M.ptr[r + 1] < M.ptr[r]) return "row_ptr not monotone";
     if ((int64_t)M.ptr[r + 1] > (int64_t)M.idx.size()) return "row_ptr beyond nnz";
@@ -186,26 +231,31 @@ std::string check_gradient(const HostCSR& G) {
 // Alg. 1: one artificial column per boundary edge-row (a row of G with one entry delta; the
 // new column holds -delta in that row).
 // -------------------------------------------------------------------------------------------
-static HostCSR augment(const HostCSR& G, int& nB) {
+static HostCSR augment(const HostCSR& G, int& nB, int nthreads) {
+    const int n = G.nrows;
     HostCSR Gt;
-    Gt.nrows = G.nrows;
-    Gt.ptr.assign(G.nrows + 1, 0);
-    nB = 0;
-    for (int r = 0; r < G.nrows; ++r) nB += (G.ptr[r + 1] - G.ptr[r] == 1);
+    Gt.nrows = n;
+    // boundary rows before row r: the artificial column of boundary row r is ncols + bpre[r]
+    std::vector<int32_t> bpre(n + 1, 0);
+    for (int r = 0; r < n; ++r) bpre[r + 1] = bpre[r] + (G.ptr[r + 1] - G.ptr[r] == 1);
+    nB = bpre[n];
     Gt.ncols = G.ncols + nB;
-    Gt.idx.reserve(G.nnz() + nB);
-    Gt.val.reserve(G.nnz() + nB);
-    int b = G.ncols;
-    for (int r = 0; r < G.nrows; ++r) {
-        for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e) {
-            Gt.idx.push_back(G.idx[e]);
-            Gt.val.push_back(G.val[e]);
+    Gt.ptr.resize(n + 1);
+    Gt.idx.resize(G.nnz() + nB);
+    Gt.val.resize(G.nnz() + nB);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r <= n; ++r) Gt.ptr[r] = G.ptr[r] + bpre[r];
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int r = 0; r < n; ++r) {
+        int32_t o = Gt.ptr[r];
+        for (int32_t e = G.ptr[r]; e < G.ptr[r + 1]; ++e, ++o) {
+            Gt.idx[o] = G.idx[e];
+            Gt.val[o] = G.val[e];
         }
         if (G.ptr[r + 1] - G.ptr[r] == 1) {
-            Gt.idx.push_back(b++);
-            Gt.val.push_back(-G.val[G.ptr[r]]);
+            Gt.idx[o] = G.ncols + bpre[r];
+            Gt.val[o] = -G.val[G.ptr[r]];
         }
-        Gt.ptr[r + 1] = (int32_t)Gt.idx.size();
     }
     return Gt;
 }
@@ -215,6 +265,47 @@ static HostCSR augment(const HostCSR& G, int& nB) {
 // modes (original columns of G) a Ruge-Stueben strong connection of A_G = G^T A G in either
 // direction, -a_ij >= theta max_{k != i}(-a_ik); any two columns of G~ sharing a row (edge).
 // -------------------------------------------------------------------------------------------
+// Open-addressing map from a non-negative int32 key to a double, for at most `cap` keys per
+// round.  A slot belongs to the current round when its tag equals the round number, so starting a
+// round (next()) clears nothing; a new key's value starts at 0.
+struct TagMap {
+    std::vector<int32_t> key;
+    std::vector<uint32_t> tag;
+    std::vector<double> val;
+    uint32_t round = 0, mask = 0;
+    explicit TagMap(int64_t cap) {
+        size_t sz = 16;
+        while ((int64_t)sz < 2 * cap) sz <<= 1;
+        key.assign(sz, 0);
+        tag.assign(sz, 0);
+        val.assign(sz, 0.0);
+        mask = (uint32_t)sz - 1;
+    }
+    void next() {
+        if (++round == 0) {   // tags wrapped: clear them once
+            std::fill(tag.begin(), tag.end(), 0u);
+            round = 1;
+        }
+    }
+    int slot(int32_t k, bool& fresh) {
+        uint32_t s = ((uint32_t)k * 2654435761u) & mask;
+        for (;;) {
+            if (tag[s] != round) {
+                tag[s] = round;
+                key[s] = k;
+                val[s] = 0.0;
+                fresh = true;
+                return (int)s;
+            }
+            if (key[s] == k) {
+                fresh = false;
+                return (int)s;
+            }
+            s = (s + 1) & mask;
+        }
+    }
+};
+
 // CSR from (row, col) pairs: rows sorted and deduplicated
 static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& parts,
                               int nthreads) {
@@ -253,9 +344,9 @@ static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int
 // -------------------------------------------------------------------------------------------
 static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt, const HostCSR& GtT,
                            double theta, int nthreads, HostCSR& Minc) {
-    const int m = G.ncols, nn = Gt.ncols, ne = A.nrows;
+    const int m = G.ncols, nn = Gt.ncols;
     (void)GtT;
-    HostCSR GT = transpose_pattern(G, true);   // CSC of G: rows of column i with values
+    HostCSR GT = transpose_pattern(G, true, nthreads);   // CSC of G: rows of column i with values
     // incidence pairs: columns sharing a row of G~
     std::vector<std::vector<std::pair<int32_t, int32_t>>> incp(nthreads);
 #pragma omp parallel for schedule(static) num_threads(nthreads)
@@ -279,36 +370,56 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
     {
         const int tid = thread_id(), nt = omp_threads();
         const int i0 = (int)((int64_t)m * tid / nt), i1 = (int)((int64_t)m * (tid + 1) / nt);
-        std::vector<int32_t> wm(ne, -1), am(m, -1), tf, tj;
-        std::vector<double> wv(ne, 0.0), av(m, 0.0);
+        // scratch sized by the largest neighbourhood of this thread's nodes: sparse maps with a
+        // tag per slot, so nothing proportional to the matrix is cleared per thread
+        int64_t wmax = 1;
+        for (int i = i0; i < i1; ++i) {
+            int64_t s = 0;
+            for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) s += A.ptr[GT.idx[t] + 1] - A.ptr[GT.idx[t]];
+            wmax = std::max(wmax, s);
+        }
+        TagMap wmap(wmax), amap(2 * wmax);
+        std::vector<int32_t> tf, tj;
+        std::vector<int32_t> tfs, tjs;   // map slots of tf, tj
         auto& out = sidx[tid];
         for (int i = i0; i < i1; ++i) {
             tf.clear();
             tj.clear();
+            tfs.clear();
+            tjs.clear();
+            wmap.next();
+            amap.next();
             // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
             for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) {
                 const int32_t e = GT.idx[t];
                 const double ge = GT.val[t];
                 for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
                     const int32_t f = A.idx[q];
-                    if (wm[f] != i) { wm[f] = i; wv[f] = 0.0; tf.push_back(f); }
-                    wv[f] += ge * A.val[q];
+                    bool fresh = false;
+                    const int sl = wmap.slot(f, fresh);
+                    if (fresh) { tf.push_back(f); tfs.push_back(sl); }
+                    wmap.val[sl] += ge * A.val[q];
                 }
             }
             // row i of G^T A G
-            for (int32_t f : tf)
+            for (size_t z = 0; z < tf.size(); ++z) {
+                const int32_t f = tf[z];
+                const double wf = wmap.val[tfs[z]];
                 for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
                     const int32_t j = G.idx[u];
-                    if (am[j] != i) { am[j] = i; av[j] = 0.0; tj.push_back(j); }
-                    av[j] += G.val[u] * wv[f];
+                    bool fresh = false;
+                    const int sl = amap.slot(j, fresh);
+                    if (fresh) { tj.push_back(j); tjs.push_back(sl); }
+                    amap.val[sl] += G.val[u] * wf;
                 }
+            }
             double rowmax = -INFINITY;
-            for (int32_t j : tj)
-                if (j != i) rowmax = std::max(rowmax, -av[j]);
+            for (size_t z = 0; z < tj.size(); ++z)
+                if (tj[z] != i) rowmax = std::max(rowmax, -amap.val[tjs[z]]);
             const size_t b = out.size();
             if (rowmax > 0.0)
-                for (int32_t j : tj)
-                    if (j != i && -av[j] >= theta * rowmax) out.push_back(j);
+                for (size_t z = 0; z < tj.size(); ++z)
+                    if (tj[z] != i && -amap.val[tjs[z]] >= theta * rowmax) out.push_back(tj[z]);
             std::sort(out.begin() + b, out.end());
             slen[i] = (int32_t)(out.size() - b);
         }
@@ -316,7 +427,7 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
     for (int i = 0; i < nn; ++i) S.ptr[i + 1] = S.ptr[i] + slen[i];
     for (const auto& v : sidx) S.idx.insert(S.idx.end(), v.begin(), v.end());
     nclk.mark("  strong connections");
-    HostCSR ST = transpose_pattern(S, false);
+    HostCSR ST = transpose_pattern(S, false, nthreads);
     // N = S + S^T + incidence, row by row as sorted unions
     HostCSR N;
     N.nrows = N.ncols = nn;
@@ -522,8 +633,8 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     const int n = A.nrows;
     PhaseClock clk;
     int nB = 0;
-    HostCSR Gt = augment(G, nB);
-    HostCSR GtT = transpose_pattern(Gt, false);
+    HostCSR Gt = augment(G, nB, nthreads);
+    HostCSR GtT = transpose_pattern(Gt, false, nthreads);
     clk.mark("augment");
     HostCSR Minc;
     HostCSR N = nodal_graph(A, G, Gt, GtT, prm.theta, nthreads, Minc);
@@ -717,41 +828,37 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     std::vector<int32_t> fromPT(nzp);   // P position -> P^T position
     std::vector<int32_t> toP(nzp);      // P^T position -> P position
     {
-        // counting sort of the P^T entries by row of P; each thread scatters one contiguous range
-        // of coarse edges, and per-thread offsets keep every row in ascending column order
-        const int nt = std::max(1, nthreads);
-        std::vector<std::vector<int32_t>> cnt(nt);
-#pragma omp parallel num_threads(nt)
+        // counting sort of the P^T entries by row of P: counts with relaxed atomic adds, a scatter
+        // through atomic cursors, then each row of P sorted by column (one entry per column), so
+        // every row ends in ascending column order whatever order the threads scattered in
+        std::vector<int32_t> col(nzp);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+        for (int c = 0; c < nc; ++c)
+            for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q)
+                __atomic_fetch_add(&P.ptr[PT.idx[q] + 1], 1, __ATOMIC_RELAXED);
+        for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
+        std::vector<int32_t> cur(P.ptr.begin(), P.ptr.end() - 1);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+        for (int c = 0; c < nc; ++c)
+            for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
+                const int32_t pp = __atomic_fetch_add(&cur[PT.idx[q]], 1, __ATOMIC_RELAXED);
+                fromPT[pp] = q;
+                col[pp] = c;
+            }
+#pragma omp parallel num_threads(nthreads)
         {
-            const int tid = thread_id(), ntr = omp_threads();
-            const int c0 = (int)((int64_t)nc * tid / ntr), c1 = (int)((int64_t)nc * (tid + 1) / ntr);
-            auto& v = cnt[tid];
-            v.assign(n, 0);
-            for (int32_t q = PT.ptr[c0]; q < PT.ptr[c1]; ++q) v[PT.idx[q]]++;
-#pragma omp barrier
-#pragma omp for schedule(static)
+            std::vector<std::pair<int32_t, int32_t>> row;
+#pragma omp for schedule(dynamic, 4096)
             for (int r = 0; r < n; ++r) {
-                int32_t s = 0;
-                for (int t = 0; t < ntr; ++t) s += cnt[t][r];
-                P.ptr[r + 1] = s;
-            }
-#pragma omp single
-            for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
-#pragma omp for schedule(static)
-            for (int r = 0; r < n; ++r) {
-                int32_t off = P.ptr[r];
-                for (int t = 0; t < ntr; ++t) {
-                    const int32_t k = cnt[t][r];
-                    cnt[t][r] = off;
-                    off += k;
+                const int32_t b = P.ptr[r], e = P.ptr[r + 1];
+                row.clear();
+                for (int32_t pp = b; pp < e; ++pp) row.push_back({col[pp], fromPT[pp]});
+                std::sort(row.begin(), row.end());
+                for (int32_t pp = b; pp < e; ++pp) {
+                    fromPT[pp] = row[pp - b].second;
+                    toP[row[pp - b].second] = pp;
                 }
             }
-            for (int c = c0; c < c1; ++c)
-                for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
-                    const int32_t pp = v[PT.idx[q]]++;
-                    fromPT[pp] = q;
-                    toP[q] = pp;
-                }
         }
     }
     P.idx.resize(nzp);

@@ -17,6 +17,8 @@ struct HostCSR {
 };
 
 HostCSR transpose_pattern(const HostCSR& M, bool with_values);
+// the same on nthreads OpenMP threads (identical result)
+HostCSR transpose_pattern(const HostCSR& M, bool with_values, int nthreads);
 
 struct CoarseEdge {
     int32_t d1, s1, d2, s2;   // fine DoFs and their +-1 signs in the row of R
