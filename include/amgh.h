@@ -175,13 +175,17 @@ amgh_status amgh_pcg_solve_noalloc(amgh_handle h, const double* f, double* x, do
  * column-major (column c at F + c n), host or device (same kind), X holds the initial guesses.
  * The k CG recurrences are independent (their own alpha, beta and stopping test); every matrix
  * product and V-cycle step is done for all unconverged columns at once, reading each matrix
- * entry once per step (sparse matrix times a row-major n x k block).  The V-cycle of this entry
- * is FP64.  iters and relres (may be NULL) receive k entries.  1 <= k <= 4096.  Returns
- * NOT_CONVERGED if any column reached maxit. */
+ * entry once per step (sparse matrix times a row-major n x k block).  Each level of this
+ * entry's V-cycle has the storage the handle's own V-cycle chose for it (amgh_info precision):
+ * FP64, or FP32 values and vectors with FP32 accumulation (BF16 levels run in FP32 here).  With
+ * any FP32 level the recurrences are flexible CG (beta = <z_k+1, r_k+1 - r_k> / <z_k, r_k>);
+ * the outer vectors, products and dots stay FP64.  iters and relres (may be NULL) receive k
+ * entries.  1 <= k <= 4096.  Returns NOT_CONVERGED if any column reached maxit. */
 amgh_status amgh_pcg_solve_multi(amgh_handle h, const double* F, double* X, int k, double tol, int maxit,
                                  int* iters, double* relres);
 
-/* Z = B R for k right-hand sides at once (n x k column-major device arrays). */
+/* Z = B R for k right-hand sides at once (n x k column-major device arrays), with the level
+ * storage described for amgh_pcg_solve_multi. */
 amgh_status amgh_vcycle_multi(amgh_handle h, const double* R, double* Z, int k);
 
 /* Stand-alone V-cycle iteration x <- x + B (f - A x) (Section 5, "AMG" counts), same stopping

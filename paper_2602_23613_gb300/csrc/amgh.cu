@@ -459,9 +459,11 @@ struct MultiEngine {
 
     int first_built = 0;   // levels below it carry no smoother (built for a dense tail only)
 
-    // smoother structures of levels >= first (a dense tail needs only its own sub-cycle)
+    // smoother structures of levels >= first (a dense tail needs only its own sub-cycle).  prec:
+    // storage of each level (AMGH_F64, or reduced: FP32 values and vectors); null = all FP64
     void build(const std::vector<LevelHost>& hl, const std::vector<DevCSR>& A64, const std::vector<DevCSR>& P64,
-               const std::vector<DevCSR>& PT64, const double* cinv64, int* err, cudaStream_t s, int first = 0) {
+               const std::vector<DevCSR>& PT64, const double* cinv64, int* err, cudaStream_t s, int first = 0,
+               const std::vector<int>* prec = nullptr) {
         nlev = (int)hl.size();
         first_built = first;
         width.clear();
@@ -471,6 +473,7 @@ struct MultiEngine {
             MultiLevel& d = L[l];
             d.n = hl[l].A.nrows;
             d.A = &A64[l];
+            d.f32 = prec && l < (int)prec->size() && (*prec)[l] != AMGH_F64;
             if (l + 1 == nlev) break;
             d.P = &P64[l];
             d.PT = &PT64[l];
@@ -525,10 +528,27 @@ struct MultiEngine {
             launch_star_inverse_rowmajor(A64[l], st.nstars, d.star_ptr.p, d.star_idx.p, d.inv_off.p, d.inv.p, err, s);
             d.l1inv.alloc(d.n);
             launch_l1inv<double>(A64[l], d.l1inv.p, s);
+            if (d.f32) {   // FP32 copies of the level's values (rounded once from FP64)
+                auto narrow = [&](const double* src, size_t cnt, DevArray<float>& dst) {
+                    dst.alloc(std::max<size_t>(1, cnt));
+                    if (cnt) launch_convert<float>(src, dst.p, (int64_t)cnt, s);
+                };
+                narrow(A64[l].val.p, (size_t)A64[l].nnz, d.Af);
+                narrow(P64[l].val.p, (size_t)P64[l].nnz, d.Pf);
+                narrow(PT64[l].val.p, (size_t)PT64[l].nnz, d.PTf);
+                narrow(d.inv.p, (size_t)off.back(), d.invf);
+                narrow(d.l1inv.p, (size_t)d.n, d.l1invf);
+            }
         }
         nL = hl.back().A.nrows;
         cinv = cinv64;
         AMGH_CUDA(cudaStreamSynchronize(s));
+    }
+
+    bool any_f32() const {
+        for (const MultiLevel& d : L)
+            if (d.f32) return true;
+        return false;
     }
 
     std::vector<int> width;   // allocated width of each level's vectors (0 = none)
@@ -540,11 +560,20 @@ struct MultiEngine {
         for (size_t l = first; l < L.size(); ++l) {
             if (width[l] == kp) continue;
             MultiLevel& d = L[l];
-            d.F.alloc((size_t)d.n * kp);
-            d.X.alloc((size_t)d.n * kp);
-            d.Y.alloc((size_t)d.n * kp);
-            d.R.alloc((size_t)d.n * kp);
-            if (d.splitk) d.Rc.alloc((size_t)std::max(1, d.max_colour_rows) * kp);
+            const size_t nk = (size_t)d.n * kp, rk = (size_t)std::max(1, d.max_colour_rows) * kp;
+            if (d.f32) {
+                d.Ff.alloc(nk);
+                d.Xf.alloc(nk);
+                d.Yf.alloc(nk);
+                d.Rf.alloc(nk);
+                if (d.splitk) d.Rcf.alloc(rk);
+            } else {
+                d.F.alloc(nk);
+                d.X.alloc(nk);
+                d.Y.alloc(nk);
+                d.R.alloc(nk);
+                if (d.splitk) d.Rc.alloc(rk);
+            }
             width[l] = kp;
         }
         if (partial.n != (size_t)304 * kp) {
@@ -553,28 +582,85 @@ struct MultiEngine {
         }
     }
 
-    // X_t = (V-cycle restricted to levels t..) F_t, for the KP columns of level t's F
+    // one level's arrays in its storage type
+    template <class T>
+    struct View {
+        using type = T;
+        const T *A, *P, *PT, *inv, *l1inv;
+        T *F, *X, *Y, *R, *Rc;
+    };
+    static View<double> view64(MultiLevel& d) {
+        return {d.A ? d.A->val.p : nullptr, d.P ? d.P->val.p : nullptr, d.PT ? d.PT->val.p : nullptr, d.inv.p,
+                d.l1inv.p, d.F.p, d.X.p, d.Y.p, d.R.p, d.Rc.p};
+    }
+    static View<float> view32(MultiLevel& d) {
+        return {d.Af.p, d.Pf.p, d.PTf.p, d.invf.p, d.l1invf.p, d.Ff.p, d.Xf.p, d.Yf.p, d.Rf.p, d.Rcf.p};
+    }
+    template <class Fn>
+    static void typed(MultiLevel& d, Fn&& fn) {
+        if (d.f32) fn(view32(d));
+        else fn(view64(d));
+    }
+
+    // X_t = (V-cycle restricted to levels t..) F_t, for the KP columns of level t's F; every level
+    // works in its own storage type, transfers between levels convert on the fly
     int64_t vcycle_from(int t, cudaStream_t s) {
         int64_t cnt = 0;
         for (int l = t; l + 1 < nlev; ++l) {
             MultiLevel& d = L[l];
-            AMGH_CUDA(cudaMemsetAsync(d.X.p, 0, sizeof(double) * d.n * KP, s));
-            for (int c : colour_sequence(d.ncolours)) { launch_schwarz_multi(d, c, KP, d.F.p, d.X.p, s); cnt++; }
-            launch_spmm(MM_L1, *d.A, KP, d.X.p, d.F.p, d.l1inv.p, d.Y.p, s);
-            launch_spmm(MM_RESID, *d.A, KP, d.Y.p, d.F.p, nullptr, d.R.p, s);
-            launch_spmm(MM_AX, *d.PT, KP, d.R.p, nullptr, nullptr, L[l + 1].F.p, s);
-            cnt += 3;
+            typed(d, [&](auto v) {
+                using T = typename decltype(v)::type;
+                AMGH_CUDA(cudaMemsetAsync(v.X, 0, sizeof(T) * d.n * KP, s));
+                for (int c : colour_sequence(d.ncolours)) {
+                    launch_schwarz_multi_t<T>(d, v.A, v.inv, v.Rc, c, KP, v.F, v.X, s);
+                    cnt++;
+                }
+                launch_spmm_t<T, T, T>(MM_L1, d.n, d.A->ptr.p, d.A->idx.p, v.A, KP, v.X, v.F, v.l1inv, v.Y, s);
+                launch_spmm_t<T, T, T>(MM_RESID, d.n, d.A->ptr.p, d.A->idx.p, v.A, KP, v.Y, v.F, (const T*)nullptr,
+                                       v.R, s);
+                typed(L[l + 1], [&](auto w) {
+                    using U = typename decltype(w)::type;
+                    launch_spmm_t<T, T, U>(MM_AX, d.PT->nrows, d.PT->ptr.p, d.PT->idx.p, v.PT, KP, v.R,
+                                           (const U*)nullptr, (const U*)nullptr, w.F, s);
+                });
+                cnt += 3;
+            });
         }
-        launch_dense_apply_multi(cinv, nL, KP, L[nlev - 1].F.p, L[nlev - 1].X.p, s);
+        typed(L[nlev - 1], [&](auto w) {
+            using U = typename decltype(w)::type;
+            launch_dense_apply_multi_t<U, U>(cinv, nL, KP, w.F, w.X, s);
+        });
         cnt++;
         for (int l = nlev - 2; l >= t; --l) {
             MultiLevel& d = L[l];
-            launch_spmm(MM_ADD, *d.P, KP, L[l + 1].X.p, nullptr, nullptr, d.Y.p, s);
-            launch_spmm(MM_L1, *d.A, KP, d.Y.p, d.F.p, d.l1inv.p, d.X.p, s);
-            cnt += 2;
-            for (int c : colour_sequence(d.ncolours)) { launch_schwarz_multi(d, c, KP, d.F.p, d.X.p, s); cnt++; }
+            typed(d, [&](auto v) {
+                using T = typename decltype(v)::type;
+                typed(L[l + 1], [&](auto w) {
+                    using U = typename decltype(w)::type;
+                    launch_spmm_t<T, U, T>(MM_ADD, d.P->nrows, d.P->ptr.p, d.P->idx.p, v.P, KP, w.X, (const T*)nullptr,
+                                           (const T*)nullptr, v.Y, s);
+                });
+                launch_spmm_t<T, T, T>(MM_L1, d.n, d.A->ptr.p, d.A->idx.p, v.A, KP, v.Y, v.F, v.l1inv, v.X, s);
+                cnt += 2;
+                for (int c : colour_sequence(d.ncolours)) {
+                    launch_schwarz_multi_t<T>(d, v.A, v.inv, v.Rc, c, KP, v.F, v.X, s);
+                    cnt++;
+                }
+            });
         }
         return cnt;
+    }
+
+    // level 0's right-hand side from a row-major FP64 block (n x KP), and its result back
+    void load_rhs(const double* R, cudaStream_t s) {
+        MultiLevel& d = L[0];
+        if (d.f32) launch_convert<float>(R, d.Ff.p, (int64_t)d.n * KP, s);
+        else if (R != d.F.p) AMGH_CUDA(cudaMemcpyAsync(d.F.p, R, sizeof(double) * d.n * KP, cudaMemcpyDeviceToDevice, s));
+    }
+    void store_result(double* Z, cudaStream_t s) {
+        MultiLevel& d = L[0];
+        if (d.f32) launch_widen(d.Xf.p, (int64_t)d.n * KP, Z, s);
+        else if (Z != d.X.p) AMGH_CUDA(cudaMemcpyAsync(Z, d.X.p, sizeof(double) * d.n * KP, cudaMemcpyDeviceToDevice, s));
     }
 
     // dense operator of the V-cycle restricted to levels t.. (row-major n_t x n_t), column blocks
@@ -2054,18 +2140,37 @@ static double measure_rho(amgh_ctx* h) {
     return it > 0 && rel > 0 ? std::pow(rel, 1.0 / it) : 0.0;
 }
 
+// storage of each level in the multi-RHS engine: FP64 for an FP64 request, else the single-system
+// engine's choice from the level's condition estimate (FP32 where it chose FP32 or BF16)
+static std::vector<int> multi_precisions(amgh_ctx* h) {
+    std::vector<int> p(h->hl.size(), AMGH_F64);
+    if (h->prm.precision == AMGH_F64 || !h->eng) return p;
+    const auto* e = static_cast<const Engine*>(h->eng.get());
+    for (size_t l = 0; l < p.size() && l < e->choice.size(); ++l)
+        p[l] = e->choice[l].prec == AMGH_F64 ? AMGH_F64 : AMGH_F32;
+    return p;
+}
+
+// the multi-RHS engine of the whole hierarchy (not the dense-tail one), built on first use
+static MultiEngine& multi_engine(amgh_ctx* h) {
+    if (!h->meng || h->meng->first_built > 0) {
+        const std::vector<int> prec = multi_precisions(h);
+        h->meng.reset(new MultiEngine());
+        h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, h->s, 0, &prec);
+    }
+    return *h->meng;
+}
+
 static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in, int k, double tol, int maxit,
                                   int* iters, double* relres) {
     if (k < 1 || k > 4096 || maxit < 0 || !(tol >= 0.0)) throw StatusError{AMGH_ERR_INVALID_ARG, "bad k, tol or maxit"};
     cudaStream_t s = h->s;
     const int64_t n = h->hl[0].A.nrows;
     const int KP = ((k + 31) / 32) * 32;
-    if (!h->meng || h->meng->first_built > 0) {
-        h->meng.reset(new MultiEngine());
-        h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
-    }
-    MultiEngine& M = *h->meng;
+    MultiEngine& M = multi_engine(h);
     M.ensure_width(KP);
+    // reduced-precision levels make the preconditioner inexact: flexible CG (Notay's FCG(1))
+    const bool flexible = M.any_f32();
     const bool df = is_device_ptr(F_in), dx = is_device_ptr(X_in);
     if (df != dx) throw StatusError{AMGH_ERR_INVALID_ARG, "F and X must both be host or both be device pointers"};
     DevArray<double> Fs, Xs;
@@ -2079,15 +2184,29 @@ static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in,
         F = Fs.p;
         X = Xs.p;
     }
-    DevArray<double> MF, MX, MP, MQ, alpha, beta;
+    DevArray<double> MF, MX, MP, MQ, alpha, beta, MR, MZ, MRold;
     MF.alloc((size_t)n * KP);
     MX.alloc((size_t)n * KP);
     MP.alloc((size_t)n * KP);
     MQ.alloc((size_t)n * KP);
     alpha.alloc(KP);
     beta.alloc(KP);
-    double* R = M.L[0].F.p;   // the V-cycle reads its right-hand side from level 0's F
-    double* Z = M.L[0].X.p;   // and leaves its result in level 0's X
+    // an FP64 level 0 reads its right-hand side from its F and leaves its result in its X; an FP32
+    // one gets them converted
+    double* R = M.L[0].F.p;
+    double* Z = M.L[0].X.p;
+    if (M.L[0].f32) {
+        MR.alloc((size_t)n * KP);
+        MZ.alloc((size_t)n * KP);
+        R = MR.p;
+        Z = MZ.p;
+    }
+    if (flexible) MRold.alloc((size_t)n * KP);
+    auto precondition = [&] {
+        M.load_rhs(R, s);
+        M.vcycle_from(0, s);
+        M.store_result(Z, s);
+    };
     launch_to_rowmajor(F, n, k, KP, MF.p, s);
     launch_to_rowmajor(X, n, k, KP, MX.p, s);
     launch_spmm(MM_RESID, h->A64[0], KP, MX.p, MF.p, nullptr, R, s);
@@ -2106,9 +2225,10 @@ static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in,
         active[c] = rr0[c] > 0.0;
         nact += active[c];
     }
+    std::vector<double> rzo(KP, 0.0);
     int it = 0;
     if (nact) {
-        M.vcycle_from(0, s);
+        precondition();
         coldot(R, Z, rz);
         AMGH_CUDA(cudaMemcpyAsync(MP.p, Z, sizeof(double) * n * KP, cudaMemcpyDeviceToDevice, s));
         for (it = 1; it <= maxit && nact; ++it) {
@@ -2116,7 +2236,7 @@ static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in,
             coldot(MP.p, MQ.p, pq);
             for (int c = 0; c < KP; ++c) al[c] = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
             AMGH_CUDA(cudaMemcpyAsync(alpha.p, al.data(), sizeof(double) * KP, cudaMemcpyHostToDevice, s));
-            launch_mcg_update(n, KP, MX.p, R, nullptr, MP.p, MQ.p, alpha.p, s);
+            launch_mcg_update(n, KP, MX.p, R, flexible ? MRold.p : nullptr, MP.p, MQ.p, alpha.p, s);
             coldot(R, R, rr);
             for (int c = 0; c < k; ++c) {
                 if (!active[c]) continue;
@@ -2127,10 +2247,13 @@ static amgh_status pcg_multi_impl(amgh_ctx* h, const double* F_in, double* X_in,
                 if (rel <= tol) { active[c] = 0; nact--; }
             }
             if (!nact) break;
-            M.vcycle_from(0, s);
+            precondition();
             coldot(R, Z, rzn);
+            // FCG(1): beta = <z_new, r_new - r_old> / <z_old, r_old>
+            if (flexible) coldot(MRold.p, Z, rzo);
             for (int c = 0; c < KP; ++c) {
-                be[c] = active[c] && rz[c] != 0.0 ? rzn[c] / rz[c] : 0.0;
+                const double num = flexible ? rzn[c] - rzo[c] : rzn[c];
+                be[c] = active[c] && rz[c] != 0.0 ? num / rz[c] : 0.0;
                 rz[c] = rzn[c];
             }
             AMGH_CUDA(cudaMemcpyAsync(beta.p, be.data(), sizeof(double) * KP, cudaMemcpyHostToDevice, s));
@@ -2433,15 +2556,21 @@ amgh_status amgh_vcycle_multi(amgh_handle h, const double* Rin, double* Zout, in
         cudaStream_t s = h->s;
         const int64_t n = h->hl[0].A.nrows;
         const int KP = ((k + 31) / 32) * 32;
-        if (!h->meng || h->meng->first_built > 0) {
-            h->meng.reset(new MultiEngine());
-            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s);
-        }
-        MultiEngine& M = *h->meng;
+        MultiEngine& M = multi_engine(h);
         M.ensure_width(KP);
-        launch_to_rowmajor(Rin, n, k, KP, M.L[0].F.p, s);
-        M.vcycle_from(0, s);
-        launch_to_colmajor(M.L[0].X.p, n, k, KP, Zout, s);
+        if (M.L[0].f32) {
+            DevArray<double> tmp;
+            tmp.alloc((size_t)n * KP);
+            launch_to_rowmajor(Rin, n, k, KP, tmp.p, s);
+            M.load_rhs(tmp.p, s);
+            M.vcycle_from(0, s);
+            M.store_result(tmp.p, s);
+            launch_to_colmajor(tmp.p, n, k, KP, Zout, s);
+        } else {
+            launch_to_rowmajor(Rin, n, k, KP, M.L[0].F.p, s);
+            M.vcycle_from(0, s);
+            launch_to_colmajor(M.L[0].X.p, n, k, KP, Zout, s);
+        }
         AMGH_CUDA(cudaStreamSynchronize(s));
         return AMGH_OK;
     });

@@ -265,47 +265,6 @@ static HostCSR augment(const HostCSR& G, int& nB, int nthreads) {
 // modes (original columns of G) a Ruge-Stueben strong connection of A_G = G^T A G in either
 // direction, -a_ij >= theta max_{k != i}(-a_ik); any two columns of G~ sharing a row (edge).
 // -------------------------------------------------------------------------------------------
-// Open-addressing map from a non-negative int32 key to a double, for at most `cap` keys per
-// round.  A slot belongs to the current round when its tag equals the round number, so starting a
-// round (next()) clears nothing; a new key's value starts at 0.
-struct TagMap {
-    std::vector<int32_t> key;
-    std::vector<uint32_t> tag;
-    std::vector<double> val;
-    uint32_t round = 0, mask = 0;
-    explicit TagMap(int64_t cap) {
-        size_t sz = 16;
-        while ((int64_t)sz < 2 * cap) sz <<= 1;
-        key.assign(sz, 0);
-        tag.assign(sz, 0);
-        val.assign(sz, 0.0);
-        mask = (uint32_t)sz - 1;
-    }
-    void next() {
-        if (++round == 0) {   // tags wrapped: clear them once
-            std::fill(tag.begin(), tag.end(), 0u);
-            round = 1;
-        }
-    }
-    int slot(int32_t k, bool& fresh) {
-        uint32_t s = ((uint32_t)k * 2654435761u) & mask;
-        for (;;) {
-            if (tag[s] != round) {
-                tag[s] = round;
-                key[s] = k;
-                val[s] = 0.0;
-                fresh = true;
-                return (int)s;
-            }
-            if (key[s] == k) {
-                fresh = false;
-                return (int)s;
-            }
-            s = (s + 1) & mask;
-        }
-    }
-};
-
 // CSR from (row, col) pairs: rows sorted and deduplicated
 static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int32_t, int32_t>>>& parts,
                               int nthreads) {
@@ -344,7 +303,7 @@ static HostCSR csr_from_pairs(int n, const std::vector<std::vector<std::pair<int
 // -------------------------------------------------------------------------------------------
 static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt, const HostCSR& GtT,
                            double theta, int nthreads, HostCSR& Minc) {
-    const int m = G.ncols, nn = Gt.ncols;
+    const int m = G.ncols, nn = Gt.ncols, ne = A.nrows;
     (void)GtT;
     HostCSR GT = transpose_pattern(G, true, nthreads);   // CSC of G: rows of column i with values
     // incidence pairs: columns sharing a row of G~
@@ -370,56 +329,36 @@ static HostCSR nodal_graph(const HostCSR& A, const HostCSR& G, const HostCSR& Gt
     {
         const int tid = thread_id(), nt = omp_threads();
         const int i0 = (int)((int64_t)m * tid / nt), i1 = (int)((int64_t)m * (tid + 1) / nt);
-        // scratch sized by the largest neighbourhood of this thread's nodes: sparse maps with a
-        // tag per slot, so nothing proportional to the matrix is cleared per thread
-        int64_t wmax = 1;
-        for (int i = i0; i < i1; ++i) {
-            int64_t s = 0;
-            for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) s += A.ptr[GT.idx[t] + 1] - A.ptr[GT.idx[t]];
-            wmax = std::max(wmax, s);
-        }
-        TagMap wmap(wmax), amap(2 * wmax);
-        std::vector<int32_t> tf, tj;
-        std::vector<int32_t> tfs, tjs;   // map slots of tf, tj
+        std::vector<int32_t> wm(ne, -1), am(m, -1), tf, tj;
+        std::vector<double> wv(ne, 0.0), av(m, 0.0);
         auto& out = sidx[tid];
         for (int i = i0; i < i1; ++i) {
             tf.clear();
             tj.clear();
-            tfs.clear();
-            tjs.clear();
-            wmap.next();
-            amap.next();
             // w = A g_i over the edges of node i (A symmetric: column e of A is row e)
             for (int32_t t = GT.ptr[i]; t < GT.ptr[i + 1]; ++t) {
                 const int32_t e = GT.idx[t];
                 const double ge = GT.val[t];
                 for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
                     const int32_t f = A.idx[q];
-                    bool fresh = false;
-                    const int sl = wmap.slot(f, fresh);
-                    if (fresh) { tf.push_back(f); tfs.push_back(sl); }
-                    wmap.val[sl] += ge * A.val[q];
+                    if (wm[f] != i) { wm[f] = i; wv[f] = 0.0; tf.push_back(f); }
+                    wv[f] += ge * A.val[q];
                 }
             }
             // row i of G^T A G
-            for (size_t z = 0; z < tf.size(); ++z) {
-                const int32_t f = tf[z];
-                const double wf = wmap.val[tfs[z]];
+            for (int32_t f : tf)
                 for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
                     const int32_t j = G.idx[u];
-                    bool fresh = false;
-                    const int sl = amap.slot(j, fresh);
-                    if (fresh) { tj.push_back(j); tjs.push_back(sl); }
-                    amap.val[sl] += G.val[u] * wf;
+                    if (am[j] != i) { am[j] = i; av[j] = 0.0; tj.push_back(j); }
+                    av[j] += G.val[u] * wv[f];
                 }
-            }
             double rowmax = -INFINITY;
-            for (size_t z = 0; z < tj.size(); ++z)
-                if (tj[z] != i) rowmax = std::max(rowmax, -amap.val[tjs[z]]);
+            for (int32_t j : tj)
+                if (j != i) rowmax = std::max(rowmax, -av[j]);
             const size_t b = out.size();
             if (rowmax > 0.0)
-                for (size_t z = 0; z < tj.size(); ++z)
-                    if (tj[z] != i && -amap.val[tjs[z]] >= theta * rowmax) out.push_back(tj[z]);
+                for (int32_t j : tj)
+                    if (j != i && -av[j] >= theta * rowmax) out.push_back(j);
             std::sort(out.begin() + b, out.end());
             slen[i] = (int32_t)(out.size() - b);
         }
@@ -828,37 +767,41 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     std::vector<int32_t> fromPT(nzp);   // P position -> P^T position
     std::vector<int32_t> toP(nzp);      // P^T position -> P position
     {
-        // counting sort of the P^T entries by row of P: counts with relaxed atomic adds, a scatter
-        // through atomic cursors, then each row of P sorted by column (one entry per column), so
-        // every row ends in ascending column order whatever order the threads scattered in
-        std::vector<int32_t> col(nzp);
-#pragma omp parallel for schedule(static) num_threads(nthreads)
-        for (int c = 0; c < nc; ++c)
-            for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q)
-                __atomic_fetch_add(&P.ptr[PT.idx[q] + 1], 1, __ATOMIC_RELAXED);
-        for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
-        std::vector<int32_t> cur(P.ptr.begin(), P.ptr.end() - 1);
-#pragma omp parallel for schedule(static) num_threads(nthreads)
-        for (int c = 0; c < nc; ++c)
-            for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
-                const int32_t pp = __atomic_fetch_add(&cur[PT.idx[q]], 1, __ATOMIC_RELAXED);
-                fromPT[pp] = q;
-                col[pp] = c;
-            }
-#pragma omp parallel num_threads(nthreads)
+        // counting sort of the P^T entries by row of P; each thread scatters one contiguous range
+        // of coarse edges, and per-thread offsets keep every row in ascending column order
+        const int nt = std::max(1, nthreads);
+        std::vector<std::vector<int32_t>> cnt(nt);
+#pragma omp parallel num_threads(nt)
         {
-            std::vector<std::pair<int32_t, int32_t>> row;
-#pragma omp for schedule(dynamic, 4096)
+            const int tid = thread_id(), ntr = omp_threads();
+            const int c0 = (int)((int64_t)nc * tid / ntr), c1 = (int)((int64_t)nc * (tid + 1) / ntr);
+            auto& v = cnt[tid];
+            v.assign(n, 0);
+            for (int32_t q = PT.ptr[c0]; q < PT.ptr[c1]; ++q) v[PT.idx[q]]++;
+#pragma omp barrier
+#pragma omp for schedule(static)
             for (int r = 0; r < n; ++r) {
-                const int32_t b = P.ptr[r], e = P.ptr[r + 1];
-                row.clear();
-                for (int32_t pp = b; pp < e; ++pp) row.push_back({col[pp], fromPT[pp]});
-                std::sort(row.begin(), row.end());
-                for (int32_t pp = b; pp < e; ++pp) {
-                    fromPT[pp] = row[pp - b].second;
-                    toP[row[pp - b].second] = pp;
+                int32_t s = 0;
+                for (int t = 0; t < ntr; ++t) s += cnt[t][r];
+                P.ptr[r + 1] = s;
+            }
+#pragma omp single
+            for (int r = 0; r < n; ++r) P.ptr[r + 1] += P.ptr[r];
+#pragma omp for schedule(static)
+            for (int r = 0; r < n; ++r) {
+                int32_t off = P.ptr[r];
+                for (int t = 0; t < ntr; ++t) {
+                    const int32_t k = cnt[t][r];
+                    cnt[t][r] = off;
+                    off += k;
                 }
             }
+            for (int c = c0; c < c1; ++c)
+                for (int32_t q = PT.ptr[c]; q < PT.ptr[c + 1]; ++q) {
+                    const int32_t pp = v[PT.idx[q]]++;
+                    fromPT[pp] = q;
+                    toP[q] = pp;
+                }
         }
     }
     P.idx.resize(nzp);

@@ -7,9 +7,11 @@ namespace amgh {
 
 constexpr int MR_WARPS = 8;   // warps per CTA in the multi-RHS kernels
 
-// per-level data of the multi-RHS engine (FP64; CSR matrices shared with the setup)
+// per-level data of the multi-RHS engine (CSR patterns and FP64 values shared with the setup; an
+// FP32 level adds FP32 copies of the values, inverses and l1 diagonal, and keeps FP32 vectors)
 struct MultiLevel {
     int n = 0, ncolours = 0, bmax = 1;
+    bool f32 = false;
     const DevCSR* A = nullptr;
     const DevCSR* P = nullptr;    // n x n_c
     const DevCSR* PT = nullptr;   // n_c x n
@@ -27,6 +29,8 @@ struct MultiLevel {
     std::vector<int32_t> colour_row_begin;    // host, ncolours + 1 (into crow)
     DevArray<int32_t> crow, cstar, cq, cbase;
     DevArray<double> Rc;                      // max_colour_rows x Kp
+    DevArray<float> Af, Pf, PTf, invf, l1invf;   // FP32 level: value copies (patterns of A, P, P^T)
+    DevArray<float> Ff, Xf, Yf, Rf, Rcf;         // FP32 level: vectors
 };
 
 // kernels (multi_kernels.cu); KP = padded width, x/y row-major with leading dimension KP
@@ -34,6 +38,18 @@ enum MultiMode { MM_AX = 0, MM_RESID = 1, MM_L1 = 2, MM_ADD = 3 };
 void launch_spmm(int mode, const DevCSR& M, int KP, const double* X, const double* F, const double* dinv, double* Y,
                  cudaStream_t s);
 void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double* F, double* X, cudaStream_t s);
+// the same on raw arrays: Y (TY) from M (values V) and X (TX); FP64 accumulation when either vector
+// type is FP64.  Instantiated for (V, TX, TY) in {ddd, fff, ddf, ffd, dfd, fdf}.
+template <class V, class TX, class TY>
+void launch_spmm_t(int mode, int nrows, const int32_t* ptr, const int32_t* idx, const V* val, int KP, const TX* X,
+                   const TY* F, const TY* dinv, TY* Y, cudaStream_t s);
+// one colour step of level L in type T (A's values, inverses, split-K scratch Rc, F and X of type T)
+template <class T>
+void launch_schwarz_multi_t(const MultiLevel& L, const T* Aval, const T* inv, T* Rc, int colour, int KP, const T* F,
+                            T* X, cudaStream_t s);
+template <class TX, class TY>
+void launch_dense_apply_multi_t(const double* Ainv, int n, int KP, const TX* X, TY* Y, cudaStream_t s);
+void launch_widen(const float* in, int64_t n, double* out, cudaStream_t s);
 void launch_star_inverse_rowmajor(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
                                   const int64_t* inv_off, double* inv, int* err_flag, cudaStream_t s);
 // Y = Ainv X for a dense n x n inverse (row-major)

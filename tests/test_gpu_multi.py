@@ -97,3 +97,55 @@ def test_dense_tail_matches_full_recursion(amgh, checker):
     it0, _, _ = amgh.amgh_pcg_solve(h0, f, x0, 1e-8, 300)
     it1, _, _ = amgh.amgh_pcg_solve(h1, f, x1, 1e-8, 300)
     assert abs(it0 - it1) <= 1
+
+
+def test_vcycle_multi_fp32_levels(amgh, checker):
+    """FP32 storage requested: the multi-RHS engine takes each level's storage from the single
+    engine (FP64 where the star blocks' kappa u > 1/4, FP32 below), so its V-cycle is the single
+    engine's FP32 V-cycle up to FP32 rounding, and both stay close to the FP64 oracle."""
+    import torch
+    p, H = checker
+    h = amgh.amgh_setup(p["A"], p["G"], dense_tail=0, precision=amgh.AMGH_F32)
+    info = amgh.amgh_info(h)
+    prec = info["precision"][: info["levels"]]
+    print("level storage", prec)
+    assert amgh.AMGH_F32 in prec
+    k = 4
+    R = np.stack([W.uniform("probe", 400 + c, p["ndof"]) for c in range(k)])
+    Rd = torch.tensor(R, device="cuda")
+    Zd = torch.zeros_like(Rd)
+    amgh.amgh_vcycle_multi(h, Rd, Zd)
+    Z = Zd.cpu().numpy()
+    z1 = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
+    for c in range(k):
+        amgh.amgh_vcycle(h, Rd[c].contiguous(), z1)
+        e_single = rel(Z[c], z1.cpu().numpy())
+        e_oracle = rel(Z[c], O.vcycle(H, R[c]))
+        print("FP32 multi vcycle column %d: vs single FP32 %.3e, vs FP64 oracle %.3e" % (c, e_single, e_oracle))
+        assert e_single < 1e-4 and e_oracle < 1e-3
+
+
+@pytest.mark.parametrize("k", [8, 40])
+def test_pcg_multi_fp32_matches_single(amgh, checker, k):
+    """Flexible block CG with the FP32 multi-RHS V-cycle against flexible single solves with the
+    FP32 single-RHS V-cycle: both reach the 1e-8 FP64 residual in nearly the same iterations."""
+    import torch
+    p, H = checker
+    h = amgh.amgh_setup(p["A"], p["G"], precision=amgh.AMGH_F32)
+    F = np.stack([W.fields.rhs(p["ndof"], 500 + c) for c in range(k)])
+    Fd = torch.tensor(F, device="cuda")
+    Xd = torch.zeros_like(Fd)
+    its, rels, ok = amgh.amgh_pcg_solve_multi(h, Fd, Xd, 1e-8, 300)
+    assert ok and max(rels) <= 1e-8
+    A = p["A"]
+    x1 = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
+    for c in range(0, k, 5):
+        x1.zero_()
+        it1, _, ok1 = amgh.amgh_pcg_solve(h, Fd[c].contiguous(), x1, 1e-8, 300)
+        xm = Xd[c].cpu().numpy()
+        tr = np.linalg.norm(F[c] - A @ xm) / np.linalg.norm(F[c])
+        print("column %d: multi %d iterations, single %d, true residual %.2e" % (c, its[c], it1, tr))
+        assert ok1 and abs(it1 - its[c]) <= 2
+        # the recurrence reaches 1e-8; the true residual stops at the FP64 floor kappa(A) eps of
+        # the 16^3 checkerboard (1.6e-7 with the FP64 V-cycle)
+        assert tr < 1e-6
