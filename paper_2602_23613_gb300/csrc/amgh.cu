@@ -16,6 +16,7 @@
 #include <map>
 #include <tuple>
 #include <mutex>
+#include <thread>
 #include <variant>
 
 #include "engine.cuh"
@@ -1027,6 +1028,13 @@ static bool tuning_enabled() {
 static std::mutex g_tune_mu;
 static std::map<std::string, LevelChoice> g_tune_cache;
 
+static std::string tune_key(const LevelHost& hl, size_t value_bytes) {
+    const char* forced = std::getenv("AMGH_SMOOTHER_MODE");
+    return std::string(forced ? forced : "") + "|" + std::to_string(value_bytes) + "|" + std::to_string(hl.A.nrows) +
+           "|" + std::to_string(hl.A.nnz()) + "|" + std::to_string(hl.stars.ncolours) + "|" +
+           std::to_string(hl.cz.P.nnz());
+}
+
 static std::vector<int> lane_candidates(double avg_len, int n, int need_slots_for) {
     std::vector<int> out;
     for (int L : {1, 2, 4, 8, 16, 32}) {
@@ -1059,10 +1067,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
     const double avg = d.n ? (double)d.nnzA / d.n : 1.0;
     const double avgPT = hl.cz.PT.nrows ? (double)hl.cz.PT.nnz() / hl.cz.PT.nrows : 1.0;
-    const char* forced = std::getenv("AMGH_SMOOTHER_MODE");
-    const std::string key = std::string(forced ? forced : "") + "|" + std::to_string(sizeof(V)) + "|" +
-                            std::to_string(d.n) + "|" + std::to_string(d.nnzA) +
-                            "|" + std::to_string(hl.stars.ncolours) + "|" + std::to_string(hl.cz.P.nnz());
+    const std::string key = tune_key(hl, sizeof(V));
     bool cached = false;
     if (tuning_enabled()) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1710,18 +1715,58 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         auto* e = new Engine();
         h->eng.reset(e);
         e->prof = &h->prof;
-        build_engine(h, e);
-        ph.mark(s, "V-cycle engine");
         // the sub-cycle below the first small level is linear in its right-hand side: apply it as
         // one dense operator, computed column block by column block with the multi-RHS V-cycle
         const int nlev = (int)h->hl.size();
         int t = -1;
         for (int l = 1; l + 1 < nlev && prm.dense_tail > 0; ++l)
             if (h->hl[l].A.nrows <= prm.dense_tail) { t = l; break; }
-        if (t > 0) {
+        auto build_tail = [h, t](cudaStream_t ts) {
             h->meng.reset(new MultiEngine());
-            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, s, t);
-            h->meng->dense_tail(t, h->dense_tail_B, s);
+            h->meng->build(h->hl, h->A64, h->P64, h->PT64, h->cinv64.p, h->errflag.p, ts, t);
+            h->meng->dense_tail(t, h->dense_tail_B, ts);
+            AMGH_CUDA(cudaStreamSynchronize(ts));
+        };
+        // The tail and the engine levels are independent: build the tail on its own stream and
+        // thread meanwhile, unless the engine build times launch modes (the tail's kernels would
+        // disturb those timings), i.e. only for FP64 storage with every level's choice cached
+        bool overlap = t > 0 && prm.precision == AMGH_F64;
+        if (overlap && tuning_enabled()) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            for (int l = 0; l + 1 < nlev && overlap; ++l)
+                overlap = g_tune_cache.count(tune_key(h->hl[l], sizeof(double))) > 0;
+        }
+        if (overlap) {
+            int dev = 0;
+            AMGH_CUDA(cudaGetDevice(&dev));
+            cudaStream_t ts = nullptr;
+            AMGH_CUDA(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+            std::exception_ptr tail_error;
+            std::thread worker([&] {
+                try {
+                    AMGH_CUDA(cudaSetDevice(dev));
+                    build_tail(ts);
+                } catch (...) {
+                    tail_error = std::current_exception();
+                }
+            });
+            std::exception_ptr engine_error;
+            try {
+                build_engine(h, e);
+            } catch (...) {
+                engine_error = std::current_exception();
+            }
+            worker.join();
+            cudaStreamDestroy(ts);
+            if (engine_error) std::rethrow_exception(engine_error);
+            if (tail_error) std::rethrow_exception(tail_error);
+            ph.mark(s, "V-cycle engine + dense tail (concurrent)");
+        } else {
+            build_engine(h, e);
+            ph.mark(s, "V-cycle engine");
+            if (t > 0) build_tail(s);
+        }
+        if (t > 0) {
             check_flag(h, "a smoother block of the dense tail");
             h->dense_tail_level = t;
             e->tail = t;
