@@ -1040,7 +1040,9 @@ static std::vector<int> lane_candidates(double avg_len, int n, int need_slots_fo
     for (int L : {1, 2, 4, 8, 16, 32}) {
         if (need_slots_for > 0 && CTA_THREADS / L < need_slots_for) continue;
         if (L > 1 && L > avg_len / 2.0) continue;
-        if (n > 400000 && L > 2) continue;   // large levels: the FP64 pipe decides, keep L small
+        // large levels with short rows (the finest): the FP64 pipe decides, keep L small; large
+        // levels with long rows (a first coarse level) need lanes to fill the GPU in each step
+        if (n > 400000 && L > 2 && avg_len < 64.0) continue;
         out.push_back(L);
     }
     if (out.empty()) out.push_back(1);
