@@ -100,6 +100,41 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# GB300 dense FP64 rate (nominal): the finest colour step is bound by it as much as by HBM
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def last_colour(res):
+    return res[-1].get("colour0") if res else None
+
+
+def launches_per_sweep(res):
+    """launches of one finest-level sweep: one per colour step in the per-colour modes, else one"""
+    info = res[-1]["info"]
+    return 2 * info["ncolours"][0] - 1 if info["fused"][0] in (0, 4, 6) else 1
+
+
+def finest_sweep_work(A, G, colour, vbytes, tbytes):
+    """(bytes, flops) of one symmetric colour sweep of the finest level, counted per colour step as
+    the library counts its algorithmic bytes: each row of each star of the colour moves its entries
+    (value + column), its star's block-inverse row and three vector values (vbytes: stored value,
+    tbytes: vector value), and does two flops per entry and per inverse entry and two additions."""
+    import numpy as np
+    Gc = G.tocsc()
+    b = np.diff(Gc.indptr)
+    rowlen = np.diff(A.indptr)
+    star_of = np.repeat(np.arange(Gc.shape[1]), b)
+    nz = np.bincount(star_of, weights=rowlen[Gc.indices], minlength=Gc.shape[1])
+    C = int(colour.max()) + 1
+    cn = np.bincount(colour, weights=nz, minlength=C)
+    ci = np.bincount(colour, weights=b.astype(np.float64) ** 2, minlength=C)
+    cr = np.bincount(colour, weights=b.astype(np.float64), minlength=C)
+    seq = list(range(C)) + list(range(C - 2, -1, -1))
+    by = sum(cn[c] * (vbytes + 4) + ci[c] * vbytes + 3 * tbytes * cr[c] for c in seq)
+    fl = sum(2 * cn[c] + 2 * ci[c] + 2 * cr[c] for c in seq)
+    return float(by), float(fl)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -255,8 +290,9 @@ def run_gpu(args, rank, world, local_rank):
         solve_s = time.perf_counter() - t0
         info = amgh.amgh_info(h)
         ks = amgh.amgh_kernel_stats(h) if profile else None
+        colour0 = amgh.amgh_level_structure(h, 0)["colour"] if profile else None
         amgh.amgh_destroy(h)
-        return dict(iters=it, relres=rel, ok=ok, solve_s=solve_s, info=info, ks=ks)
+        return dict(iters=it, relres=rel, ok=ok, solve_s=solve_s, info=info, ks=ks, colour0=colour0)
 
     def barrier():
         if world > 1:
@@ -293,6 +329,17 @@ def run_gpu(args, rank, world, local_rank):
     achieved = ks_bytes / (ks_ms / 1000.0) / 1e9 if ks_ms > 0 else None
     pk = peaks()
     peak = pk["hbm_gbs"] if pk else 6800.0
+    # the same launches' FP64 work: counted like the library counts their bytes (per colour step:
+    # every row of every star of the colour with its entries, its star's block-inverse row and two
+    # additions), summed over one sweep (colours 0..C-1, C-2..0)
+    fp64 = None
+    if achieved and last_colour(res) is not None and res[-1]["info"]["precision"][0] == amgh.AMGH_F64:
+        sw_bytes, sw_flops = finest_sweep_work(A, G, last_colour(res), 8, 8)
+        fl_rate = achieved * 1e9 * (sw_flops / sw_bytes) / 1e12
+        fp64 = {"achieved": fl_rate, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": fl_rate / FP64_NOMINAL_TFLOPS, "peak_source": "nominal",
+                "flops_per_byte": sw_flops / sw_bytes,
+                "sweep_bytes_vs_library": sw_bytes / (ks_bytes / ks_launch * launches_per_sweep(res)) if ks_launch else None}
     modes = {0: "colour", 1: "fused", 2: "persistent", 3: "staged", 4: "stream"}
     traffic = traffic_for("schwarz", args.workload, modes.get(res[-1]["info"]["fused"][0]))
     last = res[-1]
@@ -339,7 +386,8 @@ def run_gpu(args, rank, world, local_rank):
                      "traffic": traffic, "launches": ks_launch,
                      "algorithmic_bytes_per_launch": ks_bytes / ks_launch if ks_launch else None,
                      "ms_per_launch": ks_ms / ks_launch if ks_launch else None,
-                     "timed_on": "CUDA events on the handle's stream, last timed step"},
+                     "timed_on": "CUDA events on the handle's stream, last timed step",
+                     "fp64": fp64},
         "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(gpu_launches), "clocks": clk,
