@@ -37,7 +37,6 @@ struct MultiLevel {
 enum MultiMode { MM_AX = 0, MM_RESID = 1, MM_L1 = 2, MM_ADD = 3 };
 void launch_spmm(int mode, const DevCSR& M, int KP, const double* X, const double* F, const double* dinv, double* Y,
                  cudaStream_t s);
-void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double* F, double* X, cudaStream_t s);
 // the same on raw arrays: Y (TY) from M (values V) and X (TX); FP64 accumulation when either vector
 // type is FP64.  Instantiated for (V, TX, TY) in {ddd, fff, ddf, ffd, dfd, fdf}.
 template <class V, class TX, class TY>
@@ -47,13 +46,14 @@ void launch_spmm_t(int mode, int nrows, const int32_t* ptr, const int32_t* idx, 
 template <class T>
 void launch_schwarz_multi_t(const MultiLevel& L, const T* Aval, const T* inv, T* Rc, int colour, int KP, const T* F,
                             T* X, cudaStream_t s);
+// Y = Ainv X for a dense n x n FP64 inverse (row-major), X and Y of the coarsest level's type
+// (FP64 accumulation); instantiated for (TX, TY) = (double, double), (float, float)
 template <class TX, class TY>
 void launch_dense_apply_multi_t(const double* Ainv, int n, int KP, const TX* X, TY* Y, cudaStream_t s);
+// out = (double) in, n values
 void launch_widen(const float* in, int64_t n, double* out, cudaStream_t s);
 void launch_star_inverse_rowmajor(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
                                   const int64_t* inv_off, double* inv, int* err_flag, cudaStream_t s);
-// Y = Ainv X for a dense n x n inverse (row-major)
-void launch_dense_apply_multi(const double* Ainv, int n, int KP, const double* X, double* Y, cudaStream_t s);
 // column-major (n x k, ld n) <-> row-major padded (n x KP)
 void launch_to_rowmajor(const double* in, int64_t n, int k, int KP, double* out, cudaStream_t s);
 void launch_to_colmajor(const double* in, int64_t n, int k, int KP, double* out, cudaStream_t s);

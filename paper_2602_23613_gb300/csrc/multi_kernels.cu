@@ -363,10 +363,6 @@ void launch_schwarz_multi_t(const MultiLevel& L, const T* Aval, const T* inv, T*
     AMGH_LAUNCHED();
 }
 
-void launch_schwarz_multi(const MultiLevel& L, int colour, int KP, const double* F, double* X, cudaStream_t s) {
-    launch_schwarz_multi_t<double>(L, L.A->val.p, L.inv.p, L.Rc.p, colour, KP, F, X, s);
-}
-
 void launch_star_inverse_rowmajor(const DevCSR& A, int nstars, const int32_t* star_ptr, const int32_t* star_idx,
                                   const int64_t* inv_off, double* inv, int* err_flag, cudaStream_t s) {
     if (nstars == 0) return;
@@ -381,10 +377,6 @@ void launch_dense_apply_multi_t(const double* Ainv, int n, int KP, const TX* X, 
     if (total == 0) return;
     dense_apply_multi_kernel<TX, TY><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Ainv, n, KP, X, Y);
     AMGH_LAUNCHED();
-}
-
-void launch_dense_apply_multi(const double* Ainv, int n, int KP, const double* X, double* Y, cudaStream_t s) {
-    launch_dense_apply_multi_t<double, double>(Ainv, n, KP, X, Y, s);
 }
 
 void launch_widen(const float* in, int64_t n, double* out, cudaStream_t s) {
