@@ -114,3 +114,28 @@ def test_input_validation(amgh):
     st = amgh.load().amgh_setup_host_structure(ctypes.byref(ca), ctypes.byref(cg), None, ctypes.byref(out))
     assert st == amgh.AMGH_ERR_INVALID_ARG
     assert "ascending" in amgh.amgh_last_error()
+
+
+def test_bench_sweep_work_counts(amgh):
+    """The bench's FP64 view counts the finest colour sweep's work from the stars (columns of G),
+    the star colours and A's row lengths; its vectorised count equals a plain loop over the stars
+    of each colour step (0..C-1, C-2..0)."""
+    import bench
+    p = W.make_config("hex8_unit")
+    h = amgh.amgh_setup_host_structure(p["A"], p["G"])
+    colour = amgh.amgh_level_structure(h, 0)["colour"]
+    amgh.amgh_destroy(h)
+    by, fl = bench.finest_sweep_work(p["A"], p["G"], colour, 8, 8)
+    Gc = p["G"].tocsc()
+    rowlen = np.diff(p["A"].indptr)
+    C = int(colour.max()) + 1
+    seq = list(range(C)) + list(range(C - 2, -1, -1))
+    by2 = fl2 = 0
+    for c in seq:
+        for j in np.flatnonzero(colour == c):
+            rows = Gc.indices[Gc.indptr[j]:Gc.indptr[j + 1]]
+            b = len(rows)
+            for e in rows:
+                by2 += rowlen[e] * 12 + b * 8 + 3 * 8
+                fl2 += 2 * rowlen[e] + 2 * b + 2
+    assert by == by2 and fl == fl2
