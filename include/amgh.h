@@ -45,7 +45,7 @@ typedef enum {
     AMGH_ERR_OOM = 5,           /* device or host allocation failed                             */
     AMGH_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                           */
     AMGH_ERR_SETUP_STALL = 7,   /* the finest level produced no coarse edge                     */
-    AMGH_ERR_UNSUPPORTED = 8    /* valid input outside the limits of this build (e.g. block size) */
+    AMGH_ERR_UNSUPPORTED = 8    /* valid input outside the library's limits (e.g. block size)  */
 } amgh_status;
 
 typedef struct amgh_ctx* amgh_handle;
