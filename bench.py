@@ -185,6 +185,18 @@ def oracle_sample(gpu_iters=None, workload=WORKLOAD):
             "sample_seconds": t, "sample_iters": it}
 
 
+def max_over_ranks(value, device):
+    """The largest of every rank's value (the job's time is its slowest replica's); the value
+    itself without a process group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -319,10 +331,7 @@ def run_gpu(args, rank, world, local_rank):
     gpu_launches = lib.amgh_launch_count(None) - l0
     dev_ms = ev0.elapsed_time(ev1)
     t_step = max(dev_ms / 1000.0, wall) / args.steps
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(t_step, dev)
     ks_launch = sum(r["ks"]["launches"] for r in res if r["ks"])
     ks_ms = sum(r["ks"]["total_ms"] for r in res if r["ks"])
     ks_bytes = sum(r["ks"]["algorithmic_bytes"] for r in res if r["ks"])
