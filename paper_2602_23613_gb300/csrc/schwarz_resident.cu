@@ -14,8 +14,13 @@
 // three ahead, the slot metadata of the item two ahead, and the matrix entries, block-inverse
 // row and right-hand side of the next item are loaded while the current one computes.  The
 // residual of a lane's entries is summed in two interleaved partial sums (even and odd entries)
-// to keep two FP64 FMA chains in flight.  The kernel has no spin waits: every thread reaches the
-// same sequence of cluster barriers.
+// to keep two FP64 FMA chains in flight.  In this form the kernel has no spin waits: every thread
+// reaches the same sequence of cluster barriers.
+//
+// The same kernel body also runs as a cooperative grid of any size (GRID = true, launch mode 9):
+// x stays in global memory, updated rows are stored there, and the colour steps are ordered by a
+// counter barrier whose polls are bounded (a poll that gives up raises the abort word and the
+// handle's wait flag, and every CTA returns).
 #include <cuda_bf16.h>
 
 #include <climits>
