@@ -156,15 +156,16 @@ amgh_status amgh_batch_pcg_solve(int nsys, const amgh_handle* hs, const double* 
  * A times it, previous residual, partial sums, scalars) live in one fixed device array that the
  * library defines at file scope (6.3 MB on every GPU that loads the library, kept until the
  * process exits), the loop is driven from the host and the V-cycle kernels are launched one by
- * one, so no memory, graph or staging buffer is created.  It is meant for callers that cannot
- * allocate device memory when they solve: code running while a stream capture in global mode is
- * active (cudaMalloc is refused there), applications whose caching allocator has reserved nearly
- * all device memory, and latency-bound loops that cannot afford the device-wide synchronisation
- * of cudaMalloc/cudaFree.  The paper has no counterpart; it is a deployment variant.
- *  - f and x must be device pointers of the handle's device, which must be current; n <= 262144
- *    rows, larger systems are rejected with INVALID_ARG.
- *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- *    that first call before any stream capture begins.
+ * one, so no memory, graph or staging buffer is created.  The loop reads its scalars into the
+ * handle's pinned host buffer and synchronises the handle's stream once per iteration.  It is
+ * meant for callers that cannot allocate device memory when they solve: applications whose
+ * caching allocator has reserved nearly all device memory, and loops that cannot afford the
+ * device-wide synchronisation that cudaMalloc/cudaFree bring.  The paper has no counterpart; it
+ * is a deployment variant.
+ *  - f and x must be device pointers on the handle's device, and that device must be current;
+ *    otherwise INVALID_ARG.  n <= 262144 rows; larger systems are rejected with INVALID_ARG.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *    make that first call before any stream capture begins.
  *  - All calls share the array: calls whose work overlaps on the GPU (other host threads, other
  *    handles on other streams) race and must be serialised by the caller.
  * Returns as amgh_pcg_solve. */

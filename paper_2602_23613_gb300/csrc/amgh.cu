@@ -725,6 +725,7 @@ struct amgh_ctx {
     DevArray<int> waitflag;          // raised by a device-side barrier wait that gave up
     DevArray<int> symflag;           // overflow flag of the symbolic product
     int nsm = 0;
+    int dev = -1;                     // device current at setup; the handle's memory lives there
     Profiler prof;
     int64_t launches = 0;
     double host_ms = 0, dev_ms = 0;
@@ -1812,6 +1813,16 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// device that owns a device pointer (-1 for host memory or an unknown pointer)
+static int device_of(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? at.device : -1;
+}
+
 static double read_scalar(amgh_ctx* h, int slot) {
     AMGH_CUDA(cudaMemcpyAsync(h->hscal, h->scal.p, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, h->s));
     AMGH_CUDA(cudaStreamSynchronize(h->s));
@@ -2115,6 +2126,11 @@ static amgh_status pcg_scratch_impl(amgh_ctx* h, const double* f, double* x, dou
                                                     std::to_string(max_rows)};
     if (!is_device_ptr(f) || !is_device_ptr(x))
         throw StatusError{AMGH_ERR_INVALID_ARG, "the allocation-free solve takes device pointers only"};
+    int cur = -1;
+    AMGH_CUDA(cudaGetDevice(&cur));
+    if (cur != h->dev || device_of(f) != h->dev || device_of(x) != h->dev)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "the allocation-free solve needs the handle's device (" +
+                                                    std::to_string(h->dev) + ") current and f, x on it"};
     struct ProfOff {
         Profiler& p;
         bool was;
@@ -2125,11 +2141,10 @@ static amgh_status pcg_scratch_impl(amgh_ctx* h, const double* f, double* x, dou
     const bool flexible = h->prm.precision != AMGH_F64;
     double* r = h->eng->in64();
     double* z = h->eng->out64();
-    double hs[S_COUNT];
-    auto read = [&](int slot) {
-        AMGH_CUDA(cudaMemcpyAsync(hs, ks.scal, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    auto read = [&](int slot) {   // into the handle's pinned scalars, as read_scalar does
+        AMGH_CUDA(cudaMemcpyAsync(h->hscal, ks.scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaStreamSynchronize(s));
-        return hs[slot];
+        return h->hscal[slot];
     };
     AMGH_CUDA(cudaMemsetAsync(ks.scal, 0, sizeof(double) * S_COUNT, s));   // shared scalars start at zero
     launch_sell<double, double>(SELL_RESID, h->A0, x, f, nullptr, r, s);
@@ -2405,6 +2420,7 @@ amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* 
             AMGH_CUDA(cudaStreamCreate(&h->s));
             h->own_stream = true;
         }
+        AMGH_CUDA(cudaGetDevice(&h->dev));
         setup_impl(h, A, G);
         return AMGH_OK;
     });
@@ -2957,6 +2973,11 @@ void amgh_destroy(amgh_handle h) {
 }  // extern "C"
 
 namespace amgh {
+
+amgh_status fail_with(amgh_handle h, amgh_status st, const char* msg) {
+    if (h && msg) h->err = msg;
+    return st;
+}
 
 amgh_status pcg_with_scratch(amgh_handle h, const double* f, double* x, double tol, int maxit, int* iters,
                              double* relres, const KrylovScratch& ks, int64_t max_rows) {

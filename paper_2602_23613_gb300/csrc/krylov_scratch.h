@@ -15,6 +15,9 @@ struct KrylovScratch {
     double* scal;     // S_COUNT scalars
 };
 
+// records `msg` as the handle's last error and returns `st`
+amgh_status fail_with(amgh_handle h, amgh_status st, const char* msg);
+
 // PCG / flexible CG on the handle's finest level with the Krylov buffers in `ks`: host-driven
 // loop, eager kernel launches, no allocation.  f and x must be device pointers of n doubles with
 // n <= max_rows.

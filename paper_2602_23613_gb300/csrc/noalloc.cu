@@ -1,8 +1,7 @@
 // Allocation-free PCG solve: the Krylov buffers live in a fixed file-scope device array instead
 // of memory the library would allocate.  For callers that cannot allocate device memory at solve
-// time: code running while a stream capture in global mode is active (cudaMalloc is refused
-// there), applications whose caching allocator has reserved nearly all device memory, and
-// latency-bound loops that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+// time: applications whose caching allocator has reserved nearly all device memory, and loops
+// that cannot afford the device-wide synchronisation that cudaMalloc/cudaFree bring.
 #include <mutex>
 #include <string>
 
@@ -59,7 +58,7 @@ extern "C" amgh_status amgh_pcg_solve_noalloc(amgh_handle h, const double* f, do
     double* base = nullptr;
     const char* msg = nullptr;
     const amgh_status st = scratch_on_current_device(&base, &msg);
-    if (st != AMGH_OK) return st;
+    if (st != AMGH_OK) return fail_with(h, st, msg);
     KrylovScratch ks;
     ks.p = base;
     ks.q = base + NOALLOC_MAX_ROWS;

@@ -1,7 +1,7 @@
 """The allocation-free PCG entry point (for callers that cannot allocate device memory when they
-solve, e.g. inside a global-mode stream capture or under a caching allocator that holds nearly
-all memory) must give what amgh_pcg_solve gives, call after call, with its Krylov buffers in the
-library's fixed device array.  Kept in its own file, collected last."""
+solve, e.g. under a caching allocator that holds nearly all device memory) must give what
+amgh_pcg_solve gives, call after call, with its Krylov buffers in the library's fixed device
+array, and leave the device's free memory unchanged.  Kept in its own file, collected last."""
 import numpy as np
 import pytest
 
@@ -34,9 +34,16 @@ def test_noalloc_matches_pcg_twice(amgh, prec, case):
     it_ref, rel_ref, ok_ref = amgh.amgh_pcg_solve(h, f, ref, 1e-8, 300)
     assert ok_ref
     scale = float(ref.abs().max())
+    xs = [torch.zeros_like(f) for _ in range(2)]
+    torch.cuda.synchronize()
     for call in range(2):                      # the shared array keeps the last call's contents
-        x = torch.zeros_like(f)
+        x = xs[call]
+        free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
         it, rel, ok = amgh.amgh_pcg_solve_noalloc(h, f, x, 1e-8, 300)
+        torch.cuda.synchronize()
+        if call == 1:                          # the first call may load the module's device array
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_reserved() == reserved0
         assert ok and it == it_ref, (call, it, it_ref)
         assert abs(rel - rel_ref) <= TOL * max(rel_ref, 1e-300) + 1e-300 or rel == rel_ref
         assert float((x - ref).abs().max()) <= TOL * scale, call
