@@ -139,3 +139,27 @@ def test_bench_sweep_work_counts(amgh):
                 by2 += rowlen[e] * 12 + b * 8 + 3 * 8
                 fl2 += 2 * rowlen[e] + 2 * b + 2
     assert by == by2 and fl == fl2
+
+
+def test_host_structure_matches_oracle_golden_at_bench_size(amgh):
+    """Level 0 of the benchmark's workload (64^3 checkerboard): the library's host graph steps
+    against the oracle's stored structure digests (tests/golden/hex64_checker.json, written by
+    tests/golden/make_oracle_goldens.py from the oracle alone)."""
+    import hashlib
+    import json
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "hex64_checker.json")))
+    d = gold["levels"][0]["digests"]
+
+    def digest(arr, dtype):
+        return hashlib.sha256(np.ascontiguousarray(np.asarray(arr), dtype=np.dtype(dtype).newbyteorder("<"))
+                              .tobytes()).hexdigest()
+
+    p = W.make_config("hex64_checker")
+    h = amgh.amgh_setup_host_structure(p["A"], p["G"])
+    s = amgh.amgh_level_structure(h, 0)
+    assert digest(s["cf_state"], "i1") == d["cf_state"]
+    assert digest(s["edges"].astype(np.int64), "i4") == d["edges"]
+    assert digest(s["coarse_nodes"], "i4") == d["coarse_nodes"]
+    assert digest(s["patch_ptr"], "i4") == d["patch_ptr"]
+    assert digest(s["patch_idx"], "i4") == d["patch_idx"]
+    assert digest(s["colour"], "i4") == d["colour"]
