@@ -67,6 +67,18 @@ typedef struct {
  * accumulates in float, BF16 stores bfloat16 values and accumulates in float. */
 enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
 
+/* storage of the matrices A_l, P_l, P_l^T (and W_l = P_l^T A_l) that the residual, l1-Jacobi
+ * and transfer passes read, when a reduced precision is requested: SMOOTHER keeps them in the
+ * storage each level's smoother gets from the condition guard (one storage per level);
+ * REQUESTED stores them in the requested precision on every level, while the smoother's star
+ * rows and block inverses (and the vectors) still follow the guard.  Those passes solve no block
+ * system, so the contraction guard does not bind them; their rounding perturbs the coarse
+ * right-hand side by u |A| |y|, which reaches the V-cycle's output at about u sqrt(kappa) in the
+ * energy norm.  REQUESTED therefore takes the requested precision where u sqrt(kappa) <= 1/4,
+ * else FP32 where that holds, else the smoother's storage; the flexible CG of a reduced-precision
+ * request absorbs the remaining inexactness. */
+enum { AMGH_MATRIX_SMOOTHER = 0, AMGH_MATRIX_REQUESTED = 1 };
+
 /* interior extension of the coarse variables (Eq. sparseP): exact local solves on each coarse
  * edge's patch, or, on the finest level, the values predicted by a trained network (amgh_mlp_*)
  * on the same pattern.  A learned setup measures the convergence factor rho of 10 stand-alone
@@ -96,10 +108,19 @@ typedef struct {
     amgh_mlp mlp;         /* network for AMGH_INTERP_LEARNED (see amgh_mlp_*), else NULL        */
     double rho_ref;       /* reference convergence factor of the exact local solves for the
                              learned fallback test; <= 0: measure it with an exact setup       */
+    int fuse_restrict;    /* coarse right-hand side r_c = P^T (f - A y) of Eq. tl computed as
+                             P^T f - W y with W = P^T A formed at setup: one pass over the rows
+                             of P^T and W, no fine residual.  -1: on the Galerkin levels (all
+                             but the finest, whose W is about as large as A), where the
+                             autotuner keeps it when it times faster than the residual pass plus
+                             the restriction (default); 0: never (W is not formed); 1: on every
+                             level                                                             */
+    int matrix_storage;   /* AMGH_MATRIX_SMOOTHER (default) | AMGH_MATRIX_REQUESTED            */
 } amgh_params;
 
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict -1,
+ * matrix_storage SMOOTHER. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,
@@ -235,6 +256,11 @@ typedef struct {
     double rho;           /* measured convergence factor of the kept hierarchy (learned setups)  */
     double rho_exact;     /* the exact local solves' factor it was compared with               */
     double interp_ms;     /* wall time of filling the finest level's P values (solves or network) */
+    int matrix_precision[32]; /* storage of A_l, P_l, P_l^T (and W_l) in the residual, l1-Jacobi
+                                 and transfer passes (AMGH_F64/F32/BF16)                        */
+    int fused_rr[32];     /* 1 where the V-cycle computes the coarse right-hand side in the fused
+                             pass over P^T and W = P^T A, 0 where residual and restriction run
+                             apart                                                             */
 } amgh_hier_info;
 
 /* Hierarchy statistics (levels, sizes, complexities as defined in Section 5, setup time split). */
@@ -263,14 +289,16 @@ amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, i
 /* Single steps of the V-cycle on level l, for testing the kernels one by one.  Device pointers
  * of n_l (or n_{l+1}) doubles.  op = 0: y = A_l x;  1: y = f - A_l x;  2: x <- OSS-l1 pre-step
  * (x in/out, f the right-hand side);  3: x <- OSS-l1 post-step;  4: y = P_l^T x (restriction);
- * 5: y <- y + P_l x (prolongation);  6: y = A_L^{-1} x on the coarsest level L (l ignored). */
+ * 5: y <- y + P_l x (prolongation);  6: y = A_L^{-1} x on the coarsest level L (l ignored);
+ * 7: y = P_l^T (f - A_l x) by the fused pass (P_l^T f - W_l x, W_l = P_l^T A_l; Eq. tl), on a
+ * level that holds W_l (INVALID_ARG otherwise; params.fuse_restrict = 1 gives every level W). */
 amgh_status amgh_level_apply(amgh_handle h, int l, int op, const double* f, const double* x,
                              double* y);
 
 /* Kernel timing, for the roofline: when enabled the library brackets every launch of the
  * kernels of class `kind` on level `level` with CUDA events on its stream.  kind: 0 Schwarz
  * colour sweep, 1 l1-Jacobi, 2 residual, 3 restriction, 4 prolongation, 5 coarsest solve,
- * 6 outer SpMV.  amgh_kernel_stats returns the number of bracketed launches, their summed
+ * 6 outer SpMV, 7 fused residual + restriction.  amgh_kernel_stats returns the number of bracketed launches, their summed
  * duration (ms) and the algorithmic bytes they moved (sum over launches of the bytes each launch
  * must read and write once: matrix values and indices, block inverses, vectors). */
 amgh_status amgh_profile(amgh_handle h, int enable, int kind, int level);

@@ -86,18 +86,32 @@ static void build_sell(const HostCSR& pat, const DevCSR& dev, Sell<V>& S, cudaSt
 // V-cycle engine: every level carries its own storage precision (FP64, or FP32 / BF16 with FP32
 // vectors) and its own layouts, chosen at setup by the precision policy and the autotuner.
 // ---------------------------------------------------------------------------------------------
-template <class V, class T>
+// V: storage of the smoother (star rows and block inverses), decided by the condition guard;
+// T: vectors and accumulation; VA: storage of A, P, P^T and W = P^T A in the residual, l1-Jacobi
+// and transfer passes (the requested precision when the matrices are stored apart from the
+// smoother, else V).
+template <class V, class T, class VA = V>
 struct LevelX {
     using VT = V;
     using TT = T;
+    using AT = VA;
     int n = 0;
-    SellL<V> A, P, PT;
+    SellL<VA> A, P, PT, W;
+    bool fuse_rr = false;     // residual + restriction as one pass over P^T and W
     SmootherL<V> sm;
     DevArray<T> l1inv, f, x, y, r;
-    int64_t nnzA = 0, nnzP = 0;
+    int64_t nnzA = 0, nnzP = 0, nnzW = 0;
     std::vector<int64_t> col_nnz, col_inv, col_rows;   // per colour, for the algorithmic bytes
 };
-using LevelVar = std::variant<LevelX<double, double>, LevelX<float, float>, LevelX<__nv_bfloat16, float>>;
+using bf16 = __nv_bfloat16;
+using LevelVar = std::variant<LevelX<double, double>, LevelX<float, float>, LevelX<bf16, float>,
+                              LevelX<double, double, float>, LevelX<double, double, bf16>, LevelX<float, float, bf16>>;
+
+// whether a level's vectors are FP64
+static bool vectors_double(const LevelVar& v) {
+    return std::visit([](const auto& d) { return std::is_same<typename std::decay_t<decltype(d)>::TT, double>::value; },
+                      v);
+}
 
 struct LevelChoice {
     int prec = AMGH_F64;
@@ -114,6 +128,9 @@ struct LevelChoice {
     int resident_g = 1;    // ... of this many 256-thread chunk groups each
     bool resident_grid = false;   // ... as a cooperative grid of `resident` CTAs with x in global memory
     double kappa = 0.0;
+    int prec_ap = AMGH_F64;  // storage of A, P, P^T and W in the residual, l1 and transfer passes
+    bool fuse_rr = false;    // residual + restriction fused into one pass over P^T and W = P^T A
+    int L_RR = 1;            // lanes per row of that pass (P^T and W share it)
 };
 
 struct Engine : EngineBase {
@@ -140,12 +157,20 @@ struct Engine : EngineBase {
             }, v);
     }
 
-    bool level0_double() const { return std::holds_alternative<LevelX<double, double>>(L[0]); }
+    bool level0_double() const { return vectors_double(L[0]); }
+    // level 0's buffers as FP64 (null when its vectors are float)
+    template <class Pick>
+    double* level0_buf(Pick pick) {
+        return std::visit([&](auto& d) -> double* {
+            if constexpr (std::is_same<typename std::decay_t<decltype(d)>::TT, double>::value) return pick(d);
+            else return nullptr;
+        }, L[0]);
+    }
     double* in64() override {
-        return level0_double() ? std::get<LevelX<double, double>>(L[0]).f.p : io_in.p;
+        return level0_double() ? level0_buf([](auto& d) { return d.f.p; }) : io_in.p;
     }
     double* out64() override {
-        return level0_double() ? std::get<LevelX<double, double>>(L[0]).x.p : io_out.p;
+        return level0_double() ? level0_buf([](auto& d) { return d.x.p; }) : io_out.p;
     }
 
     template <class F>
@@ -171,7 +196,7 @@ struct Engine : EngineBase {
 
     template <class Lv>
     double bytes_pass(const Lv& d, int64_t nnz, int64_t rows, int vecs) const {
-        using V = typename Lv::VT;
+        using V = typename Lv::AT;
         using T = typename Lv::TT;
         return (double)nnz * (sizeof(V) + 4) + 4.0 * rows + (double)vecs * sizeof(T) * rows;
     }
@@ -204,7 +229,7 @@ struct Engine : EngineBase {
     }
     template <class Lv>
     void smooth_pre(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
-        using V = typename Lv::VT;
+        using V = typename Lv::AT;
         using T = typename Lv::TT;
         sweep(d, l, s, cnt);
         timed(K_L1, l, bytes_pass(d, d.nnzA, d.n, 4), s,
@@ -213,7 +238,7 @@ struct Engine : EngineBase {
     }
     template <class Lv>
     void smooth_post(Lv& d, int l, cudaStream_t s, int64_t& cnt) {
-        using V = typename Lv::VT;
+        using V = typename Lv::AT;
         using T = typename Lv::TT;
         timed(K_L1, l, bytes_pass(d, d.nnzA, d.n, 4), s,
               [&] { launch_sellL<V, T, T>(SM_L1, d.A, d.y.p, d.f.p, d.l1inv.p, d.x.p, s); });
@@ -221,30 +246,46 @@ struct Engine : EngineBase {
         sweep(d, l, s, cnt);
     }
 
+    // the fused pass's algorithmic bytes: P^T and W once each (values and columns, row pointers),
+    // f and y of the fine level read once, the coarse right-hand side written once
+    template <class Lv>
+    double bytes_rr(const Lv& a, int64_t nc, size_t tb) const {
+        using V = typename Lv::AT;
+        using T = typename Lv::TT;
+        return (double)(a.nnzP + a.nnzW) * (sizeof(V) + 4) + 8.0 * nc + 2.0 * sizeof(T) * a.n + (double)tb * nc;
+    }
+
     int64_t core(cudaStream_t s) {
         int64_t cnt = 0;
         if (!level0_double()) {
-            launch_convert<float>(io_in.p, std::get_if<LevelX<float, float>>(&L[0])
-                                               ? std::get<LevelX<float, float>>(L[0]).f.p
-                                               : std::get<LevelX<__nv_bfloat16, float>>(L[0]).f.p,
-                                  std::visit([](auto& d) { return (int64_t)d.n; }, L[0]), s);
+            std::visit([&](auto& d) {
+                using T = typename std::decay_t<decltype(d)>::TT;
+                if constexpr (!std::is_same<T, double>::value) launch_convert<T>(io_in.p, d.f.p, (int64_t)d.n, s);
+            }, L[0]);
             cnt++;
         }
         const int last = tail >= 0 ? tail : nlev - 1;
         for (int l = 0; l < last; ++l) {
             std::visit([&](auto& d) {
-                using V = typename std::decay_t<decltype(d)>::VT;
+                using V = typename std::decay_t<decltype(d)>::AT;
                 using T = typename std::decay_t<decltype(d)>::TT;
                 d.x.zero(s);
                 smooth_pre(d, l, s, cnt);
+                if (d.fuse_rr) return;
                 timed(K_RESID, l, bytes_pass(d, d.nnzA, d.n, 3), s,
                       [&] { launch_sellL<V, T, T>(SM_RESID, d.A, d.y.p, d.f.p, (const T*)nullptr, d.r.p, s); });
                 cnt++;
             }, L[l]);
             std::visit([&](auto& a, auto& b) {
-                using V = typename std::decay_t<decltype(a)>::VT;
+                using V = typename std::decay_t<decltype(a)>::AT;
                 using Ta = typename std::decay_t<decltype(a)>::TT;
                 using Tb = typename std::decay_t<decltype(b)>::TT;
+                if (a.fuse_rr) {
+                    timed(K_RR, l, bytes_rr(a, b.n, sizeof(Tb)), s,
+                          [&] { launch_rr<V, Ta, Tb>(a.PT, a.W, a.f.p, a.y.p, b.f.p, s); });
+                    cnt++;
+                    return;
+                }
                 const double by = bytes_pass(a, a.nnzP, b.n, 0) + sizeof(Ta) * (double)a.n + sizeof(Tb) * (double)b.n;
                 timed(K_RESTRICT, l, by, s, [&] {
                     launch_sellL<V, Ta, Tb>(SM_AX, a.PT, a.r.p, (const Tb*)nullptr, (const Tb*)nullptr, b.f.p, s);
@@ -264,7 +305,7 @@ struct Engine : EngineBase {
         }, L[last]);
         for (int l = last - 1; l >= 0; --l) {
             std::visit([&](auto& a, auto& b) {
-                using V = typename std::decay_t<decltype(a)>::VT;
+                using V = typename std::decay_t<decltype(a)>::AT;
                 using Ta = typename std::decay_t<decltype(a)>::TT;
                 using Tb = typename std::decay_t<decltype(b)>::TT;
                 const double by = bytes_pass(a, a.nnzP, a.n, 2) + sizeof(Tb) * (double)b.n;
@@ -276,9 +317,10 @@ struct Engine : EngineBase {
             std::visit([&](auto& d) { smooth_post(d, l, s, cnt); }, L[l]);
         }
         if (!level0_double()) {
-            const float* x0 = std::get_if<LevelX<float, float>>(&L[0]) ? std::get<LevelX<float, float>>(L[0]).x.p
-                                                                     : std::get<LevelX<__nv_bfloat16, float>>(L[0]).x.p;
-            launch_to_double<float>(x0, io_out.p, std::visit([](auto& d) { return (int64_t)d.n; }, L[0]), s);
+            std::visit([&](auto& d) {
+                using T = typename std::decay_t<decltype(d)>::TT;
+                if constexpr (!std::is_same<T, double>::value) launch_to_double<T>(d.x.p, io_out.p, (int64_t)d.n, s);
+            }, L[0]);
             cnt++;
         }
         return cnt;
@@ -382,12 +424,20 @@ struct Engine : EngineBase {
             using T = std::remove_cv_t<std::remove_pointer_t<decltype(src)>>;
             launch_to_double<T>(src, dst, cnt, s);
         };
-        if (op == 4 || op == 5) {
+        if (op == 4 || op == 5 || op == 7) {
             std::visit([&](auto& a, auto& b) {
-                using V = typename std::decay_t<decltype(a)>::VT;
+                using V = typename std::decay_t<decltype(a)>::AT;
                 using Ta = typename std::decay_t<decltype(a)>::TT;
                 using Tb = typename std::decay_t<decltype(b)>::TT;
-                if (op == 4) {
+                if (op == 7) {
+                    if (a.W.nrows != a.PT.nrows || a.W.nslices != a.PT.nslices)
+                        throw StatusError{AMGH_ERR_INVALID_ARG, "level " + std::to_string(l) +
+                                                                    " holds no W = P^T A (fused restriction off)"};
+                    in(f, a.f.p, a.n);
+                    in(x, a.y.p, a.n);
+                    launch_rr<V, Ta, Tb>(a.PT, a.W, a.f.p, a.y.p, b.f.p, s);
+                    out(b.f.p, y, b.n);
+                } else if (op == 4) {
                     in(x, a.r.p, a.n);
                     launch_sellL<V, Ta, Tb>(SM_AX, a.PT, a.r.p, (const Tb*)nullptr, (const Tb*)nullptr, b.f.p, s);
                     out(b.f.p, y, b.n);
@@ -401,7 +451,7 @@ struct Engine : EngineBase {
             return;
         }
         std::visit([&](auto& d) {
-            using V = typename std::decay_t<decltype(d)>::VT;
+            using V = typename std::decay_t<decltype(d)>::AT;
             using T = typename std::decay_t<decltype(d)>::TT;
             int64_t c = 0;
             switch (op) {
@@ -695,6 +745,8 @@ struct amgh_ctx {
     std::string err;
     std::vector<LevelHost> hl;
     std::vector<DevCSR> A64, P64, PT64;
+    std::vector<DevCSR> W64;              // W_l = P_l^T A_l for the fused residual + restriction
+    std::vector<HostCSR> Wrows;           // its row pointers on the host (the SELL-L slice widths)
     DevArray<double> cinv64;
     std::unique_ptr<EngineBase> eng;
     std::unique_ptr<MultiEngine> meng;   // built on the first multi-RHS call (or for a dense tail)
@@ -832,6 +884,13 @@ static void build_sellL(const HostCSR& pat, const DevCSR& dev, int L, SellL<V>& 
     S.col.alloc(S.stored);
     S.val.alloc(S.stored);
     launch_sellL_fill<V>(dev, S, s);
+}
+
+// the same for a matrix whose pattern lives on the device only (W = P^T A): the host holds its row
+// pointers, which the slice widths need
+template <class V>
+static void build_sellL_rows(const HostCSR& rows, const DevCSR& dev, int L, SellL<V>& S, cudaStream_t s) {
+    build_sellL<V>(rows, dev, L, S, s);
 }
 
 // name of a smoother launch mode (AMGH_SMOOTHER_MODE restricts the autotuner to one of them)
@@ -1029,9 +1088,10 @@ static bool tuning_enabled() {
 static std::mutex g_tune_mu;
 static std::map<std::string, LevelChoice> g_tune_cache;
 
-static std::string tune_key(const LevelHost& hl, size_t value_bytes) {
+static std::string tune_key(const LevelHost& hl, size_t value_bytes, size_t matrix_bytes, int fuse) {
     const char* forced = std::getenv("AMGH_SMOOTHER_MODE");
-    return std::string(forced ? forced : "") + "|" + std::to_string(value_bytes) + "|" + std::to_string(hl.A.nrows) +
+    return std::string(forced ? forced : "") + "|" + std::to_string(value_bytes) + "|" + std::to_string(matrix_bytes) +
+           "|" + std::to_string(fuse) + "|" + std::to_string(hl.A.nrows) +
            "|" + std::to_string(hl.A.nnz()) + "|" + std::to_string(hl.stars.ncolours) + "|" +
            std::to_string(hl.cz.P.nnz());
 }
@@ -1050,14 +1110,16 @@ static std::vector<int> lane_candidates(double avg_len, int n, int need_slots_fo
     return out;
 }
 
-template <class V, class T>
-static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
+template <class V, class T, class VA>
+static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch) {
     cudaStream_t s = h->s;
     const LevelHost& hl = h->hl[l];
     DevPhases ph;
     d.n = hl.A.nrows;
     d.nnzA = hl.A.nnz();
     d.nnzP = hl.cz.P.nnz();
+    const bool haveW = l < (int)h->W64.size() && h->W64[l].nrows > 0;
+    d.nnzW = haveW ? h->W64[l].nnz : 0;
     d.f.alloc(d.n);
     d.x.alloc(d.n);
     d.y.alloc(d.n);
@@ -1070,15 +1132,18 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
     launch_l1inv<T>(h->A64[l], d.l1inv.p, s);
     const double avg = d.n ? (double)d.nnzA / d.n : 1.0;
     const double avgPT = hl.cz.PT.nrows ? (double)hl.cz.PT.nnz() / hl.cz.PT.nrows : 1.0;
-    const std::string key = tune_key(hl, sizeof(V));
+    const std::string key = tune_key(hl, sizeof(V), sizeof(VA), haveW ? h->prm.fuse_restrict : 0);
     bool cached = false;
     if (tuning_enabled()) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             const double kap = ch.kappa;
+            const int pap = ch.prec_ap, prec = ch.prec;
             ch = it->second;
             ch.kappa = kap;
+            ch.prec_ap = pap;
+            ch.prec = prec;
             cached = true;
         }
     }
@@ -1090,44 +1155,67 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T>& d, LevelChoice& ch) {
         cvec.zero(s);
     }
     // ---- A (l1-Jacobi, residual) ----
+    float best_resid = 1e30f, best_restrict = 1e30f;
     if (tune) {
-        float best = 1e30f;
         for (int Lc : lane_candidates(avg, d.n, 0)) {
-            SellL<V> cand;
-            build_sellL<V>(hl.A, h->A64[l], Lc, cand, s);
+            SellL<VA> cand;
+            build_sellL<VA>(hl.A, h->A64[l], Lc, cand, s);
             const float ms = time_best(s, 3, [&] {
-                launch_sellL<V, T, T>(SM_RESID, cand, d.x.p, d.f.p, (const T*)nullptr, d.r.p, s);
+                launch_sellL<VA, T, T>(SM_RESID, cand, d.x.p, d.f.p, (const T*)nullptr, d.r.p, s);
             });
-            if (ms < best) { best = ms; ch.L_A = Lc; }
+            if (ms < best_resid) { best_resid = ms; ch.L_A = Lc; }
         }
     }
-    build_sellL<V>(hl.A, h->A64[l], ch.L_A, d.A, s);
+    build_sellL<VA>(hl.A, h->A64[l], ch.L_A, d.A, s);
     ph.mark(s, "  A layout", l);
     // ---- P (prolongation) and P^T (restriction) ----
     if (tune) {
         float best = 1e30f;
         for (int Lc : {1, 2}) {
-            SellL<V> cand;
-            build_sellL<V>(hl.cz.P, h->P64[l], Lc, cand, s);
+            SellL<VA> cand;
+            build_sellL<VA>(hl.cz.P, h->P64[l], Lc, cand, s);
             const float ms = time_best(s, 3, [&] {
-                launch_sellL<V, T, T>(SM_ADD, cand, cvec.p, (const T*)nullptr, (const T*)nullptr, d.y.p, s);
+                launch_sellL<VA, T, T>(SM_ADD, cand, cvec.p, (const T*)nullptr, (const T*)nullptr, d.y.p, s);
             });
             if (ms < best) { best = ms; ch.L_P = Lc; }
         }
-        best = 1e30f;
         for (int Lc : lane_candidates(avgPT, hl.cz.PT.nrows, 0)) {
             if (Lc > 8) continue;
-            SellL<V> cand;
-            build_sellL<V>(hl.cz.PT, h->PT64[l], Lc, cand, s);
+            SellL<VA> cand;
+            build_sellL<VA>(hl.cz.PT, h->PT64[l], Lc, cand, s);
             const float ms = time_best(s, 3, [&] {
-                launch_sellL<V, T, T>(SM_AX, cand, d.r.p, (const T*)nullptr, (const T*)nullptr, cvec.p, s);
+                launch_sellL<VA, T, T>(SM_AX, cand, d.r.p, (const T*)nullptr, (const T*)nullptr, cvec.p, s);
             });
-            if (ms < best) { best = ms; ch.L_PT = Lc; }
+            if (ms < best_restrict) { best_restrict = ms; ch.L_PT = Lc; }
+        }
+        // the fused pass over P^T and W = P^T A, against the residual pass plus the restriction
+        ch.fuse_rr = false;
+        if (haveW) {
+            const double avgW = hl.cz.PT.nrows ? (double)(d.nnzW + hl.cz.PT.nnz()) / hl.cz.PT.nrows : 1.0;
+            float best_rr = 1e30f;
+            for (int Lc : lane_candidates(avgW, hl.cz.PT.nrows, 0)) {
+                SellL<VA> cpt, cw;
+                build_sellL<VA>(hl.cz.PT, h->PT64[l], Lc, cpt, s);
+                build_sellL_rows<VA>(h->Wrows[l], h->W64[l], Lc, cw, s);
+                const float ms = time_best(s, 3, [&] { launch_rr<VA, T, T>(cpt, cw, d.f.p, d.y.p, cvec.p, s); });
+                if (ms < best_rr) { best_rr = ms; ch.L_RR = Lc; }
+            }
+            ch.fuse_rr = h->prm.fuse_restrict > 0 || best_rr < best_resid + best_restrict;
+            if (ph.on)
+                std::fprintf(stderr, "[amgh] L%d residual %.4f + restriction %.4f ms, fused (L %d) %.4f ms -> %s\n", l,
+                             best_resid, best_restrict, ch.L_RR, best_rr, ch.fuse_rr ? "fused" : "apart");
         }
     }
-    build_sellL<V>(hl.cz.P, h->P64[l], ch.L_P, d.P, s);
-    build_sellL<V>(hl.cz.PT, h->PT64[l], ch.L_PT, d.PT, s);
-    ph.mark(s, "  P, P^T layouts", l);
+    if (haveW && !tuning_enabled()) {
+        ch.fuse_rr = h->prm.fuse_restrict > 0;
+        ch.L_RR = ch.L_PT;
+    }
+    d.fuse_rr = haveW && ch.fuse_rr;
+    build_sellL<VA>(hl.cz.P, h->P64[l], ch.L_P, d.P, s);
+    build_sellL<VA>(hl.cz.PT, h->PT64[l], d.fuse_rr ? ch.L_RR : ch.L_PT, d.PT, s);
+    // W is kept when the fused pass runs, or when it is forced on (then every level has it)
+    if (haveW && (d.fuse_rr || h->prm.fuse_restrict > 0)) build_sellL_rows<VA>(h->Wrows[l], h->W64[l], d.PT.L, d.W, s);
+    ph.mark(s, "  P, P^T, W layouts", l);
     // ---- smoother ----
     // Each lane count is built once; its launch modes only differ in how the same layout is
     // swept: per-colour launches, per-colour streaming launches (chunks staged in shared memory),
@@ -1336,6 +1424,45 @@ static int level_precision(int requested, double kappa) {
     return AMGH_F64;
 }
 
+// storage of a level's A, P, P^T and W: the smoother's (coupled), or, stored apart, the widest
+// of the requested precision, FP32 and the smoother's storage that keeps u sqrt(kappa) <= 1/4.
+// Rounding the matrices perturbs the residual by u |A| |y|; the coarse correction carries that
+// perturbation into the V-cycle's output, where it weighs about u sqrt(kappa) against the output
+// in the energy norm (kappa: the level's star-block condition estimate, standing in for the
+// level operator's); the guard keeps it at the smoother guard's margin.
+static int matrix_precision(const amgh_params& prm, int smoother_prec, double kappa) {
+    if (prm.precision == AMGH_F64 || prm.matrix_storage != AMGH_MATRIX_REQUESTED) return smoother_prec;
+    if (smoother_prec == AMGH_BF16) return AMGH_BF16;
+    const double u32 = 5.9604644775390625e-08, u16 = 3.90625e-03, sk = std::sqrt(std::max(kappa, 0.0));
+    if (prm.precision == AMGH_BF16 && sk * u16 <= 0.25) return AMGH_BF16;
+    if (sk * u32 <= 0.25) return AMGH_F32;
+    return smoother_prec;
+}
+
+template <class T>
+struct TypeTag {
+    using type = T;
+};
+
+// the engine level of a (smoother storage, matrix storage) pair
+static void emplace_level(amgh_ctx* h, Engine* e, int l, LevelChoice& ch) {
+    auto make = [&](auto tag) {
+        using Lv = typename decltype(tag)::type;
+        e->L.emplace_back(std::in_place_type<Lv>);
+        build_level(h, l, std::get<Lv>(e->L.back()), ch);
+    };
+    const int sp = ch.prec, ap = ch.prec_ap;
+    if (sp == AMGH_F64 && ap == AMGH_F64) make(TypeTag<LevelX<double, double>>{});
+    else if (sp == AMGH_F64 && ap == AMGH_F32) make(TypeTag<LevelX<double, double, float>>{});
+    else if (sp == AMGH_F64) make(TypeTag<LevelX<double, double, bf16>>{});
+    else if (sp == AMGH_F32 && ap == AMGH_BF16) make(TypeTag<LevelX<float, float, bf16>>{});
+    else if (sp == AMGH_F32) make(TypeTag<LevelX<float, float>>{});
+    else {
+        ch.prec_ap = AMGH_BF16;
+        make(TypeTag<LevelX<bf16, float>>{});
+    }
+}
+
 static double level_kappa(amgh_ctx* h, int l) {
     cudaStream_t s = h->s;
     const StarLayout& st = h->hl[l].stars;
@@ -1365,16 +1492,10 @@ static void build_engine(amgh_ctx* h, Engine* e) {
         // the condition estimate only decides a reduced precision; an FP64 request skips it
         ch.kappa = h->prm.precision == AMGH_F64 ? 0.0 : level_kappa(h, l);
         ch.prec = level_precision(h->prm.precision, ch.kappa);
-        if (ch.prec == AMGH_F64) {
-            e->L.emplace_back(std::in_place_type<LevelX<double, double>>);
-            build_level(h, l, std::get<LevelX<double, double>>(e->L.back()), ch);
-        } else if (ch.prec == AMGH_F32) {
-            e->L.emplace_back(std::in_place_type<LevelX<float, float>>);
-            build_level(h, l, std::get<LevelX<float, float>>(e->L.back()), ch);
-        } else {
-            e->L.emplace_back(std::in_place_type<LevelX<__nv_bfloat16, float>>);
-            build_level(h, l, std::get<LevelX<__nv_bfloat16, float>>(e->L.back()), ch);
-        }
+        ch.prec_ap = matrix_precision(h->prm, ch.prec, ch.kappa);
+        // a float smoother with FP64 matrices does not occur: the matrices are at most as wide
+        if (ch.prec != AMGH_F64 && ch.prec_ap == AMGH_F64) ch.prec_ap = ch.prec;
+        emplace_level(h, e, l, ch);
     }
     // coarsest level: dense inverse, precision from its 1-norm condition estimate
     const HostCSR& Ac = h->hl.back().A;
@@ -1686,6 +1807,27 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             upload_csr(hc, Ac, s, false);
         }
         launch_ac_numeric(PT, AP, Ac, s);
+        // W = P^T A for the fused residual + restriction (Eq. tl's coarse right-hand side by
+        // associativity); same symbolic and numeric products as the Galerkin one
+        h->W64.emplace_back();
+        h->Wrows.emplace_back();
+        // tuned (-1): Galerkin levels only.  On the finest level W is about as large as A
+        // (0.95 of its entries on hex meshes), so the fused pass saves little there while forming
+        // and tuning W costs more than that over a solve; on Galerkin levels W holds 0.04-0.5 of
+        // A's entries.
+        if (prm.fuse_restrict > 0 || (prm.fuse_restrict < 0 && l > 0)) {
+            DevCSR& Wd = h->W64.back();
+            if (!spgemm_symbolic(PT, h->A64[l], Wd, h->symflag.p, s)) {
+                HostCSR hw = symbolic_product(cz.PT, cur.A, nthreads);
+                upload_csr(hw, Wd, s, false);
+            }
+            launch_ap_numeric(PT, h->A64[l], Wd, s);
+            HostCSR& wr = h->Wrows.back();
+            wr.nrows = Wd.nrows;
+            wr.ncols = Wd.ncols;
+            wr.ptr.resize(Wd.nrows + 1);
+            AMGH_CUDA(cudaMemcpyAsync(wr.ptr.data(), Wd.ptr.p, sizeof(int32_t) * (Wd.nrows + 1), cudaMemcpyDeviceToHost, s));
+        }
         HostCSR An;   // the next level's matrix, on the host for its graph steps
         An.nrows = Ac.nrows;
         An.ncols = Ac.ncols;
@@ -1737,7 +1879,9 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         if (overlap && tuning_enabled()) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             for (int l = 0; l + 1 < nlev && overlap; ++l)
-                overlap = g_tune_cache.count(tune_key(h->hl[l], sizeof(double))) > 0;
+                overlap = g_tune_cache.count(tune_key(h->hl[l], sizeof(double), sizeof(double),
+                                                      l < (int)h->W64.size() && h->W64[l].nrows > 0
+                                                          ? prm.fuse_restrict : 0)) > 0;
         }
         if (overlap) {
             int dev = 0;
@@ -1774,7 +1918,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             h->dense_tail_level = t;
             e->tail = t;
             const int nt = h->hl[t].A.nrows;
-            if (std::holds_alternative<LevelX<double, double>>(e->L[t])) {
+            if (vectors_double(e->L[t])) {
                 e->tail_d = std::move(h->dense_tail_B);   // FP64 level: the engine keeps the operator
             } else {
                 e->tail_f.alloc((size_t)nt * nt);
@@ -2399,6 +2543,8 @@ void amgh_default_params(amgh_params* p) {
     p->dense_tail = 8192;
     p->mlp = nullptr;
     p->rho_ref = 0.0;
+    p->fuse_restrict = -1;
+    p->matrix_storage = AMGH_MATRIX_SMOOTHER;
 }
 
 amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params, amgh_handle* out) {
@@ -2675,6 +2821,8 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
                            : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
                            : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
+            info->matrix_precision[l] = cl.prec_ap;
+            info->fused_rr[l] = cl.fuse_rr && l + 1 < nlev && (e->tail < 0 || l < e->tail) ? 1 : 0;
         }
         return AMGH_OK;
     });
@@ -2760,7 +2908,7 @@ amgh_status amgh_level_apply(amgh_handle h, int l, int op, const double* f, cons
 }
 
 amgh_status amgh_profile(amgh_handle h, int enable, int kind, int level) {
-    if (!h || kind < 0 || kind > 6 || level < 0 || h->structure_only) return AMGH_ERR_INVALID_ARG;
+    if (!h || kind < 0 || kind > 7 || level < 0 || h->structure_only) return AMGH_ERR_INVALID_ARG;
     return guarded(h, [&] {
         h->prof.enabled = enable != 0;
         h->prof.gen++;

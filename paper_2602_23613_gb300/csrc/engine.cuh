@@ -8,7 +8,7 @@
 namespace amgh {
 
 // kernel classes for the roofline timing
-enum KernelKind { K_SCHWARZ = 0, K_L1 = 1, K_RESID = 2, K_RESTRICT = 3, K_PROLONG = 4, K_COARSE = 5, K_SPMV = 6 };
+enum KernelKind { K_SCHWARZ = 0, K_L1 = 1, K_RESID = 2, K_RESTRICT = 3, K_PROLONG = 4, K_COARSE = 5, K_SPMV = 6, K_RR = 7 };
 
 struct Profiler {
     bool enabled = false;

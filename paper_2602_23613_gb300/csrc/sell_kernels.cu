@@ -69,6 +69,42 @@ void launch_mode(int L, const SellL<V>& M, const TX* x, const TY* f, const TY* d
     AMGH_LAUNCHED();
 }
 
+// Fused residual and restriction, r_c = P^T (f - A y), written by associativity as
+// P^T f - W y with W = P^T A formed at setup: one row-gather pass over the rows of P^T and W, no
+// fine residual written anywhere and no atomics.  PT and W have the same rows and the same L, so
+// one lane group owns row c in both.
+template <class V, class TX, class TY, int L>
+__global__ void __launch_bounds__(256) rr_kernel(SellLView<V> PT, SellLView<V> W, const TX* __restrict__ f,
+                                                 const TX* __restrict__ y, TY* __restrict__ out) {
+    using Acc = typename std::conditional<std::is_same<TX, double>::value || std::is_same<TY, double>::value,
+                                          double, float>::type;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slice = gt >> 5, lane = threadIdx.x & 31;
+    if (slice >= PT.nslices) return;                     // uniform over the warp
+    const int row = slice * (32 / L) + lane / L;
+    Acc s = Acc(0);
+    {
+        const int64_t st = PT.slice_ptr[slice];
+        const int w = (int)((PT.slice_ptr[slice + 1] - st) >> 5);
+        const int32_t* __restrict__ c = PT.col + st + lane;
+        const V* __restrict__ v = PT.val + st + lane;
+#pragma unroll 4
+        for (int t = 0; t < w; ++t) s = fma(widen<Acc>(v[32 * t]), (Acc)f[c[32 * t]], s);
+    }
+    {
+        const int64_t st = W.slice_ptr[slice];
+        const int w = (int)((W.slice_ptr[slice + 1] - st) >> 5);
+        const int32_t* __restrict__ c = W.col + st + lane;
+        const V* __restrict__ v = W.val + st + lane;
+#pragma unroll 4
+        for (int t = 0; t < w; ++t) s = fma(-widen<Acc>(v[32 * t]), (Acc)y[c[32 * t]], s);
+    }
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((lane % L) != 0 || row >= PT.nrows) return;
+    out[row] = (TY)s;
+}
+
 template <class V>
 __global__ void sellL_fill_kernel(int n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                   const double* __restrict__ val, int nslices, int L,
@@ -107,6 +143,26 @@ void launch_sellL(int mode, const SellL<V>& M, const TX* x, const TY* f, const T
     }
 }
 
+template <class V, class TX, class TY>
+void launch_rr(const SellL<V>& PT, const SellL<V>& W, const TX* f, const TX* y, TY* out, cudaStream_t s) {
+    if (PT.nslices == 0) return;
+    if (W.nslices != PT.nslices || W.L != PT.L || W.nrows != PT.nrows)
+        throw CudaError{cudaErrorInvalidValue, "launch_rr: P^T and W layouts differ"};
+    const int threads = 256;
+    const int blocks = (int)(((int64_t)PT.nslices * 32 + threads - 1) / threads);
+    auto a = view(PT);
+    auto b = view(W);
+    switch (PT.L) {
+        case 1: rr_kernel<V, TX, TY, 1><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+        case 2: rr_kernel<V, TX, TY, 2><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+        case 4: rr_kernel<V, TX, TY, 4><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+        case 8: rr_kernel<V, TX, TY, 8><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+        case 16: rr_kernel<V, TX, TY, 16><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+        default: rr_kernel<V, TX, TY, 32><<<blocks, threads, 0, s>>>(a, b, f, y, out); break;
+    }
+    AMGH_LAUNCHED();
+}
+
 template <class V>
 void launch_sellL_fill(const DevCSR& M, SellL<V>& S, cudaStream_t s) {
     if (S.nslices == 0) return;
@@ -130,6 +186,18 @@ INST_SELL(__nv_bfloat16, float, float)
 INST_SELL(__nv_bfloat16, float, double)
 INST_SELL(__nv_bfloat16, double, float)
 INST_SELL(__nv_bfloat16, double, double)
+#define INST_RR(V, TX, TY) \
+    template void launch_rr<V, TX, TY>(const SellL<V>&, const SellL<V>&, const TX*, const TX*, TY*, cudaStream_t);
+INST_RR(double, double, double)
+INST_RR(double, double, float)
+INST_RR(float, double, double)
+INST_RR(float, double, float)
+INST_RR(float, float, float)
+INST_RR(float, float, double)
+INST_RR(__nv_bfloat16, double, double)
+INST_RR(__nv_bfloat16, double, float)
+INST_RR(__nv_bfloat16, float, float)
+INST_RR(__nv_bfloat16, float, double)
 template void launch_sellL_fill<double>(const DevCSR&, SellL<double>&, cudaStream_t);
 template void launch_sellL_fill<float>(const DevCSR&, SellL<float>&, cudaStream_t);
 template void launch_sellL_fill<__nv_bfloat16>(const DevCSR&, SellL<__nv_bfloat16>&, cudaStream_t);

@@ -12,6 +12,12 @@ enum SellModeL { SM_AX = 0, SM_RESID = 1, SM_L1 = 2, SM_ADD = 3 };
 template <class V, class TX, class TY>
 void launch_sellL(int mode, const SellL<V>& M, const TX* x, const TY* f, const TY* dinv, TY* y, cudaStream_t s);
 
+// fused residual and restriction: out = PT f - W y with W = P^T A (so out = P^T (f - A y)), one
+// pass over the rows of PT and W, which must share L and the row count.  V: storage of both;
+// TX: type of f and y; TY: type of out; accumulation as in launch_sellL.
+template <class V, class TX, class TY>
+void launch_rr(const SellL<V>& PT, const SellL<V>& W, const TX* f, const TX* y, TY* out, cudaStream_t s);
+
 // one colour of the multiplicative Schwarz sweep (chunks [cta_begin, cta_end) of the colour); with
 // S.stream_grid > 0 as a streaming launch of at most that many CTAs
 template <class V, class T>

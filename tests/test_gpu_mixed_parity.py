@@ -1,0 +1,224 @@
+"""Reduced-precision levels (FP32 or BF16 storage, FP32 accumulation) kernel by kernel, with every
+level run in its own storage (no dense tail).
+
+Single-pass kernels (SpMV, residual, restriction, prolongation, fused restriction) are compared
+with the oracle's formula evaluated in FP64 on the SAME rounded operands: the level's FP64
+matrices as the library computed them (held to the oracle's by the FP64 parity tests), rounded
+to the level's matrix storage, and the vectors rounded to its vector type.  What may then differ
+is only the summation in the accumulation type and the final rounding to the vector type,
+bounded componentwise by
+  |err_i| <= 2 ((k_i + 2) u_acc (sum_j |a_ij x_j| + |f_i|) + u_vec |y_i|),
+k_i the row length, u_acc and u_vec the unit roundoffs of the accumulation and vector types.
+
+Whole smoothing steps and the V-cycle are compared with the FP64 oracle on unrounded data:
+every block solve of a level with condition kappa and smoother storage u_s moves by up to about
+kappa u_s, the errors of the 2C-1 sequential colour steps add up (the sweep is a contraction, so
+none is amplified), and the l1-Jacobi pass moves by the matrix storage's u_A, so the bound per
+level is 8 ((2C-1) kappa u_s + u_A), and 4 times the largest level bound for the V-cycle.  The
+achieved errors are printed."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import amg as O
+
+pytestmark = pytest.mark.gpu
+U = {0: 2.0 ** -53, 1: 2.0 ** -24, 2: 2.0 ** -8}       # AMGH_F64, AMGH_F32, AMGH_BF16
+
+
+@pytest.fixture(scope="module")
+def amgh():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2602_23613_gb300 import build, amgh as mod
+    build.build()
+    mod.load()
+    return mod
+
+
+def cuda(x):
+    import torch
+    return torch.tensor(np.asarray(x, dtype=np.float64), device="cuda")
+
+
+def to_f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def to_bf16(x):
+    """double -> float (round to nearest even) -> bfloat16 (round to nearest even on the float's
+    bits), the library's narrowing; finite inputs only."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def rounder(code):
+    return {0: lambda v: np.asarray(v, dtype=np.float64), 1: to_f32, 2: to_bf16}[code]
+
+
+def rounded(M, code):
+    M = sp.csr_matrix(M, copy=True)
+    M.data = rounder(code)(M.data)
+    return M
+
+
+def bound(Mr, xr, fr, y, k_rows, u_acc, u_vec):
+    s = abs(Mr) @ np.abs(xr)
+    if fr is not None:
+        s = s + np.abs(fr)
+    return 2.0 * ((k_rows + 2) * u_acc * s + u_vec * np.abs(y)) + 1e-300
+
+
+CASES = {
+    "hex12_lognormal": lambda: W.hex_problem(12, W.fields.log_uniform(12, 3, lo=-2, hi=2), 0.1),
+    "hex16_checker": lambda: W.make_config("hex16_checker"),
+    "hex12_unit": lambda: W.hex_problem(12, 1.0, 1.0),
+}
+
+
+@pytest.fixture(scope="module", params=[(c, p, m) for c in CASES for p in ("f32", "bf16") for m in (0, 1)],
+                ids=lambda t: "%s-%s-%s" % (t[0], t[1], "coupled" if t[2] == 0 else "requested"))
+def mixed(request, amgh):
+    case, prec, storage = request.param
+    p = CASES[case]()
+    code = {"f32": amgh.AMGH_F32, "bf16": amgh.AMGH_BF16}[prec]
+    H = O.setup(p["A"], p["G"], coarse_size=100)
+    h = amgh.amgh_setup(p["A"], p["G"], precision=code, dense_tail=0, matrix_storage=storage, fuse_restrict=1)
+    info = amgh.amgh_info(h)
+    print("mixed %s %s %s: smoother %s, matrices %s, kappa %s" % (
+        case, prec, "coupled" if storage == 0 else "requested", info["precision"], info["matrix_precision"],
+        ["%.1e" % k for k in info["block_kappa"]]))
+    return case, prec, storage, p, H, h, info
+
+
+def test_storage_policy(amgh, mixed):
+    """Smoother storage: reduced only where kappa u <= 1/4.  Matrix storage stored apart: the
+    requested precision where u sqrt(kappa) <= 1/4, else FP32 where that holds, else the
+    smoother's; coupled: the smoother's."""
+    case, prec, storage, p, H, h, info = mixed
+    req = {"f32": 1, "bf16": 2}[prec]
+    for l, (q, k) in enumerate(zip(info["precision"][:-1], info["block_kappa"][:-1])):
+        if q == 2:
+            assert k * 2.0 ** -8 <= 0.25
+        elif q == 1:
+            assert k * 2.0 ** -24 <= 0.25
+        else:
+            assert k * 2.0 ** -24 > 0.25
+        mq = info["matrix_precision"][l]
+        if storage == 0 or q == 2:
+            assert mq == q
+            continue
+        if req == 2 and np.sqrt(k) * 2.0 ** -8 <= 0.25:
+            assert mq == 2
+        elif np.sqrt(k) * 2.0 ** -24 <= 0.25:
+            assert mq == 1
+        else:
+            assert mq == q
+
+
+def test_single_pass_kernels_on_rounded_operands(amgh, mixed):
+    import torch
+    case, prec, storage, p, H, h, info = mixed
+    worst = 0.0
+    for l in range(len(H) - 1):
+        A, P = amgh.amgh_level_matrix(h, l, 0), amgh.amgh_level_matrix(h, l, 1)
+        n, nc = A.shape[0], P.shape[1]
+        sm, mat = info["precision"][l], info["matrix_precision"][l]
+        vec = 0 if sm == 0 else 1                     # FP64 vectors only on FP64-smoother levels
+        u_acc = U[0] if vec == 0 else U[1]
+        u_vec = U[vec]
+        rv = rounder(vec)
+        Ar, Pr = rounded(A, mat), rounded(P, mat)
+        kA = np.diff(Ar.indptr)
+        x, f = W.uniform("probe", 800 + l, n), W.uniform("probe", 900 + l, n)
+        xr, fr = rv(x), rv(f)
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        checks = []
+        amgh.amgh_level_apply(h, l, 0, None, cuda(x), y)
+        want = Ar @ xr
+        checks.append(("spmv", y.cpu().numpy(), want, bound(Ar, xr, None, want, kA, u_acc, u_vec)))
+        amgh.amgh_level_apply(h, l, 1, cuda(f), cuda(x), y)
+        want = fr - Ar @ xr
+        checks.append(("residual", y.cpu().numpy(), want, bound(Ar, xr, fr, want, kA, u_acc, u_vec)))
+        # restriction into the next level's vector type
+        vec_c = 0 if info["precision"][l + 1] == 0 else 1
+        u_c = U[vec_c]
+        u_acc_t = U[0] if (vec == 0 or vec_c == 0) else U[1]
+        yc = torch.zeros(nc, dtype=torch.float64, device="cuda")
+        amgh.amgh_level_apply(h, l, 4, None, cuda(x), yc)
+        PTr = sp.csr_matrix(Pr.T)
+        want = PTr @ xr
+        checks.append(("restrict", yc.cpu().numpy(), want,
+                       bound(PTr, xr, None, want, np.diff(PTr.indptr), u_acc_t, u_c)))
+        e = W.uniform("probe", 950 + l, nc)
+        er = rounder(vec_c)(e)
+        y0 = cuda(f)
+        amgh.amgh_level_apply(h, l, 5, None, cuda(e), y0)
+        want = fr + Pr @ er
+        checks.append(("prolong", y0.cpu().numpy(), want,
+                       bound(Pr, er, fr, want, np.diff(Pr.indptr), u_acc_t, u_vec)))
+        # fused restriction: W = P^T A formed in FP64 by the library, then rounded; a rounding
+        # boundary may fall differently for W's entries, so one storage unit of |W| |x| is added
+        Wr = rounded(sp.csr_matrix(P.T @ A), mat)
+        amgh.amgh_level_apply(h, l, 7, cuda(f), cuda(x), yc)
+        want = PTr @ fr - Wr @ xr
+        kw = np.diff(PTr.indptr) + np.diff(Wr.indptr)
+        b = bound(sp.hstack([PTr, Wr]).tocsr(), np.concatenate([fr, xr]), None, want, kw, u_acc_t, u_c)
+        b += 2 * U[mat] * (abs(Wr) @ np.abs(xr))
+        checks.append(("fused", yc.cpu().numpy(), want, b))
+        for what, got, want, bd in checks:
+            r = float((np.abs(got - want) / bd).max())
+            worst = max(worst, r)
+            assert r <= 1.0, (case, prec, l, what, r)
+    print("mixed %s %s: worst single-pass error / bound %.3f" % (case, prec, worst))
+
+
+def test_smoothing_steps_and_vcycle_against_fp64_oracle(amgh, mixed):
+    import torch
+    case, prec, storage, p, H, h, info = mixed
+    tols = []
+    for l in range(len(H) - 1):
+        L = H[l]
+        n = L["A"].shape[0]
+        kappa = max(np.linalg.cond(L["A"][b][:, b].toarray()) for b in L["stars"] if len(b))
+        steps = 2 * L["ncolours"] - 1
+        tol = 8 * (steps * kappa * U[info["precision"][l]] + U[info["matrix_precision"][l]])
+        tols.append(tol)
+        x, f = W.uniform("probe", 10 + l, n), W.uniform("probe", 40 + l, n)
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for op, ref in ((2, O.smooth_pre), (3, O.smooth_post)):
+            amgh.amgh_level_apply(h, l, op, cuda(f), cuda(x), y)
+            want = ref(L, f, x.copy())
+            e = float(np.abs(y.cpu().numpy() - want).max() / np.abs(want).max())
+            print("mixed %s %s level %d op %d: rel err %.2e (bound %.2e, kappa %.1e)" % (case, prec, l, op, e, tol, kappa))
+            assert e < tol, (case, prec, l, op, e, tol)
+    r = W.uniform("probe", 7, p["ndof"])
+    z = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
+    amgh.amgh_vcycle(h, cuda(r), z)
+    zo = O.vcycle(H, r)
+    e = float(np.abs(z.cpu().numpy() - zo).max() / np.abs(zo).max())
+    tv = 4 * max(tols)
+    print("mixed %s %s V-cycle rel err %.2e (bound %.2e)" % (case, prec, e, tv))
+    assert e < tv
+
+
+def test_flexible_cg_reaches_fp64_tolerance(amgh, mixed):
+    import torch
+    case, prec, storage, p, H, h, info = mixed
+    f = p["f"] if "f" in p else W.fields.rhs(p["ndof"], 0)
+    x = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
+    it, rel, ok = amgh.amgh_pcg_solve(h, cuda(f), x, 1e-8, 800)
+    xo, ito, _ = O.pcg(H, f, tol=1e-8)
+    A = p["A"]
+    d = x.cpu().numpy() - xo
+    sol_err = np.sqrt(d @ (A @ d) / (xo @ (A @ xo)))
+    true_rel = np.linalg.norm(f - A @ x.cpu().numpy()) / np.linalg.norm(f)
+    print("mixed %s %s FCG %d iterations (FP64 oracle PCG %d), solution A-norm err %.2e, true residual %.2e"
+          % (case, prec, it, ito, sol_err, true_rel))
+    assert ok and rel <= 1e-8
+    assert it <= 2 * ito + 5
+    assert sol_err < 1e-5
