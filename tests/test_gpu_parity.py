@@ -228,8 +228,9 @@ def full(amgh):
 
 
 def test_full_size_sampled(amgh, full):
-    """The bench workload (64^3 checkerboard): kernels on sampled rows/columns against the oracle's
-    formulas, and structural invariants of the hierarchy."""
+    """The bench workload (64^3 checkerboard): the residual kernel on sampled rows against the
+    oracle's formula, structural invariants of the hierarchy, and convergence with the true
+    residual checked on the host."""
     import torch
     p, h = full
     A = p["A"]
@@ -248,19 +249,8 @@ def test_full_size_sampled(amgh, full):
     assert len(np.unique(edges[:, 5])) == len(edges)                 # one path per middle node
     ext = np.concatenate([edges[:, 0], edges[:, 2]])
     assert len(np.unique(ext)) == len(ext)                            # distinct pairing
-    P = amgh.amgh_level_matrix(h, 0, 1)
-    cols = rng.choice(len(edges), 50, replace=False)
-    tuples = [tuple(int(v) for v in edges[c]) for c in range(len(edges))]
-    tuples = [(t[0], float(t[1]), t[2], float(t[3]), t[4], t[5], t[6]) for t in tuples]
-    patches = O.interior_patches(A, tuples, n)
-    Pc = P.tocsc()
-    for c in cols:
-        sub = [tuples[c]]
-        q = patches[c]
-        Po = O.interpolation_local(A, sub, [q], n)
-        got = Pc[:, c].toarray().ravel()
-        tol = max(TOL, 8 * EPS * np.linalg.cond(A[q][:, q].toarray()))
-        assert rel(got, Po[:, 0].toarray().ravel()) < tol
+    # the structure, the level matrices, a V-cycle and the PCG count against the oracle's own
+    # hierarchy of this workload: tests/test_gpu_bench_golden.py
     # convergence through the public entry point, with the true residual checked on the host
     xs = np.zeros(n)
     it, relres, ok = amgh.amgh_pcg_solve(h, p["f"], xs, 1e-8, 500)
