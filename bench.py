@@ -36,6 +36,13 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dense-tail", type=int, default=None,
                     help="rows at or below which the V-cycle tail is one dense operator (library default if unset)")
+    ap.add_argument("--matrix-storage", default=None, choices=["smoother", "requested"],
+                    help="storage of A, P, P^T in the residual, l1 and transfer passes (library default if unset)")
+    ap.add_argument("--fuse-restrict", type=int, default=None, choices=[-1, 0, 1],
+                    help="fused residual + restriction: -1 tuned per level, 0 off, 1 on (library default if unset)")
+    ap.add_argument("--variants", default="hex128_spheres",
+                    help="workload of the FP64 / FP32 / BF16 comparison reported in the line ('none' to skip)")
+    ap.add_argument("--variant-steps", type=int, default=1)
     ap.add_argument("--profile-setup", action="store_true",
                     help="set up once, then once more between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -100,8 +107,111 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# GB300 dense FP64 rate (nominal): the finest colour step is bound by it as much as by HBM
+# GB300 dense FP64 rate (nominal), used only when the live measurement below fails
 FP64_NOMINAL_TFLOPS = 1.25
+
+
+def fp64_peak_tflops(dev):
+    """FP64 rate measured live: the best of five cuBLAS FP64 GEMMs (4096^3, 2 n^3 flops), the same
+    kind of library figure as the measured bf16 peak; the nominal rate if it cannot run."""
+    import torch
+    try:
+        n = 4096
+        a = torch.rand(n, n, dtype=torch.float64, device=dev)
+        b = torch.rand(n, n, dtype=torch.float64, device=dev)
+        torch.matmul(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1000.0)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12, "measured (cuBLAS FP64 GEMM 4096^3, best of 5)"
+    except Exception as e:   # noqa: BLE001
+        return FP64_NOMINAL_TFLOPS, "nominal (%s)" % type(e).__name__
+
+
+def level_profile(amgh, h, A0, G0, hbm_peak, fp64_peak, nvc=10):
+    """Per level of a built hierarchy: the Schwarz sweep's time (CUDA events on the handle's
+    stream around each of its launches over `nvc` V-cycles), its colour steps, algorithmic bytes
+    and FP64 work (counted like the library counts bytes), and the fraction of the HBM and FP64
+    peaks; a sweep far below both is bound by the latency of its sequential colour steps."""
+    import numpy as np
+    import torch
+    info = amgh.amgh_info(h)
+    n0 = info["n"][0]
+    r = torch.tensor(np.linspace(-1.0, 1.0, n0), device="cuda")
+    z = torch.zeros_like(r)
+    last = info["dense_tail"] if info["dense_tail"] >= 0 else info["levels"] - 1
+    out, total = [], 0.0
+    for l in range(last):
+        amgh.amgh_profile(h, 1, "schwarz", l)
+        for _ in range(nvc):
+            amgh.amgh_vcycle(h, r, z)
+        ks = amgh.amgh_kernel_stats(h)
+        amgh.amgh_profile(h, 0, "schwarz", l)
+        A = A0 if l == 0 else amgh.amgh_level_matrix(h, l, 0)
+        G = G0 if l == 0 else amgh.amgh_level_matrix(h, l, 2)
+        colour = amgh.amgh_level_structure(h, l)["colour"]
+        vb = 8 if info["precision"][l] == 0 else (4 if info["precision"][l] == 1 else 2)
+        tb = 8 if info["precision"][l] == 0 else 4
+        by, fl = finest_sweep_work(A, G, colour, vb, tb)
+        sweeps = 2 * nvc
+        ms = ks["total_ms"] / sweeps if sweeps else 0.0
+        steps = 2 * info["ncolours"][l] - 1
+        gbs = by / (ms / 1000.0) / 1e9 if ms > 0 else 0.0
+        tfl = fl / (ms / 1000.0) / 1e12 if ms > 0 else 0.0
+        fh, ff = gbs / hbm_peak, tfl / fp64_peak if info["precision"][l] == 0 else None
+        bound = "hbm" if fh >= 0.3 else ("alu" if ff is not None and ff >= 0.3 else "latency")
+        total += ms
+        out.append({"level": l, "rows": info["n"][l], "nnz": info["nnz"][l], "mode": info["fused"][l],
+                    "lanes": info["lanes"][l], "steps_per_sweep": steps, "ms_per_sweep": ms,
+                    "us_per_step": 1000.0 * ms / steps, "bytes_per_sweep": by, "GBps": gbs, "hbm_frac": fh,
+                    "fp64_TFLOPs": tfl if info["precision"][l] == 0 else None, "fp64_frac": ff,
+                    "bound": bound, "launches": ks["launches"]})
+    for o in out:
+        o["share_of_sweeps"] = o["ms_per_sweep"] / total if total > 0 else None
+    return out
+
+
+def time_variant(amgh, prob, dev_inputs, precision, matrix_storage, steps, warmup):
+    """Setup + flexible CG to 1e-8 on a workload with a requested storage precision: wall time
+    of whole steps (synchronised) after warm-up ones, with the level storages the handle chose."""
+    import numpy as np
+    import torch
+    A, f = prob["A"], prob["f"]
+    Ad, Gd, fd = dev_inputs
+    xd = torch.zeros_like(fd)
+    code = {"f64": amgh.AMGH_F64, "f32": amgh.AMGH_F32, "bf16": amgh.AMGH_BF16}[precision]
+    ms = {"smoother": amgh.AMGH_MATRIX_SMOOTHER, "requested": amgh.AMGH_MATRIX_REQUESTED}[matrix_storage]
+    res = []
+    for i in range(warmup + steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = amgh.amgh_setup(Ad, Gd, precision=code, matrix_storage=ms)
+        t1 = time.perf_counter()
+        xd.zero_()
+        it, rel, ok = amgh.amgh_pcg_solve(h, fd, xd, 1e-8, 5000)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        info = amgh.amgh_info(h)
+        amgh.amgh_destroy(h)
+        if i >= warmup:
+            res.append((t2 - t0, t1 - t0, t2 - t1, it, rel, ok, info))
+    xs = xd.cpu().numpy()
+    true_rel = float(np.linalg.norm(f - A @ xs) / np.linalg.norm(f))
+    names = {0: "f64", 1: "f32", 2: "bf16"}
+    info = res[-1][6]
+    return {"workload": prob["name"], "precision": precision, "matrix_storage": matrix_storage,
+            "s_per_step": statistics.mean(r[0] for r in res), "setup_s": statistics.mean(r[1] for r in res),
+            "solve_s": statistics.mean(r[2] for r in res), "pcg_iters": res[-1][3], "relres": res[-1][4],
+            "converged": res[-1][5], "true_relres": true_rel,
+            "level_precision": [names[q] for q in info["precision"]],
+            "matrix_precision": [names[q] for q in info["matrix_precision"]],
+            "block_kappa": info["block_kappa"], "levels": info["n"], "steps": steps, "warmup": warmup}
 
 
 def last_colour(res):
@@ -162,27 +272,80 @@ def traffic_for(kernel, workload, mode):
 # ----------------------------------------------------------------------------------------------
 # CPU oracle leg (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------------------------
-def oracle_sample(gpu_iters=None, workload=WORKLOAD):
-    """Oracle setup + PCG on the 16^3 member of the workload family, scaled to the full workload
-    by the DoF ratio (both are O(n) per iteration) and by the iteration ratio."""
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def scaling_exponents():
+    """Growth exponents of the oracle's setup time and per-iteration PCG time with the DoFs,
+    from its measured 24^3 and 64^3 runs (tests/golden/oracle_scaling.json); 1 when absent."""
+    try:
+        rows = {r["n"]: r for r in json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_scaling.json")))["rows"]}
+        import math
+        a, b = rows[24], rows[64]
+        lr = math.log(b["ndof"] / a["ndof"])
+        return (math.log(b["setup_s"] / a["setup_s"]) / lr,
+                math.log((b["pcg_s"] / b["iters"]) / (a["pcg_s"] / a["iters"])) / lr, "measured 24^3 -> 64^3")
+    except (OSError, ValueError, KeyError, ZeroDivisionError):
+        return 1.0, 1.0, "linear (no measured exponents)"
+
+
+def full_iterations(workload):
+    """The oracle's own PCG iteration count on the full workload (stored by the oracle-only golden
+    script), or None."""
+    try:
+        return json.load(open(os.path.join(ROOT, "tests", "golden", workload + ".json")))["pcg"]["iterations"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def oracle_sample(workload=WORKLOAD, sample=None, pool=None, cores=1):
+    """The oracle (setup, then PCG to 1e-8) on a smaller member of the workload family, extrapolated
+    to the full workload by one rule that both CPU legs use: setup time x (N/n)^a plus time per
+    PCG iteration x (N/n)^b x the full workload's iteration count, with a and b the oracle's measured
+    growth exponents and the iteration count the oracle's own at full size (the sample's when that
+    is unknown).  pool: a process pool whose map spreads the setup's independent local solves and
+    star inverses (the PCG stays on one core)."""
     import workloads as W
     from oracle import amg as O
-    _, sample = W.describe(workload)
+    sample = sample or W.describe(workload)[1]
     s = W.make_config(sample)
     nfull = W.CONFIGS[workload]["n"]
     full_n = 3 * nfull * (nfull - 1) ** 2
+    kw = {} if pool is None else {"pmap": pool.map, "nchunks": 8 * cores}
     t0 = time.perf_counter()
-    H = O.setup(s["A"], s["G"], coarse_size=100)
+    H = O.setup(s["A"], s["G"], coarse_size=100, **kw)
+    t1 = time.perf_counter()
     _, it, _ = O.pcg(H, s["f"], tol=1e-8, maxit=1000)
-    t = time.perf_counter() - t0
-    scale = full_n / s["ndof"]
-    if gpu_iters:
-        scale *= gpu_iters / max(it, 1)
-    return {"value": t * scale, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": "%s (%d DoFs): oracle setup + PCG to 1e-8 took %.2f s in %d iterations; scaled by "
-                      "DoFs %d/%d%s" % (sample, s["ndof"], t, it, full_n, s["ndof"],
-                                        " and iterations %d/%d" % (gpu_iters, it) if gpu_iters else ""),
-            "sample_seconds": t, "sample_iters": it}
+    t2 = time.perf_counter()
+    a, b, src = scaling_exponents()
+    r = full_n / s["ndof"]
+    it_full = full_iterations(workload) or it
+    value = (t1 - t0) * r ** a + (t2 - t1) / max(it, 1) * r ** b * it_full
+    return {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": "%s (%d DoFs): oracle setup %.2f s%s + PCG %.2f s in %d iterations; extrapolated to %d DoFs "
+                      "as setup x (N/n)^%.2f + s/iteration x (N/n)^%.2f x %d iterations (%s exponents; the "
+                      "oracle's own full-size iteration count)" % (
+                          sample, s["ndof"], t1 - t0, " on %d processes" % cores if pool else "", t2 - t1, it,
+                          full_n, a, b, it_full, src),
+            "sample_seconds": t2 - t0, "sample_iters": it, "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+def oracle_all_cores(workload=WORKLOAD):
+    """The same sample with the setup's independent loops over a pool of all host cores (spawned
+    processes: the GPU context of this process must not be forked)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(n) as pool:
+        pool.map(abs, range(n))                    # workers started before the timed region
+        return oracle_sample(workload=workload, pool=pool, cores=n)
 
 
 def max_over_ranks(value, device):
@@ -202,7 +365,7 @@ def run_reference(args, rank, world):
         return 0
     import workloads as W
     for _ in range(args.warmup):
-        oracle_sample(workload=args.workload)
+        oracle_sample(workload=args.workload, sample="hex8_unit")   # loads the modules only
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -248,6 +411,11 @@ def run_gpu(args, rank, world, local_rank):
     fd = torch.tensor(f, device=dev)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
     extra = {} if args.dense_tail is None else {"dense_tail": args.dense_tail}
+    if args.matrix_storage is not None:
+        extra["matrix_storage"] = {"smoother": amgh.AMGH_MATRIX_SMOOTHER, "requested": amgh.AMGH_MATRIX_REQUESTED}[
+            args.matrix_storage]
+    if args.fuse_restrict is not None:
+        extra["fuse_restrict"] = args.fuse_restrict
 
     if args.profile_setup:
         h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
@@ -341,12 +509,13 @@ def run_gpu(args, rank, world, local_rank):
     # the same launches' FP64 work: counted like the library counts their bytes (per colour step:
     # every row of every star of the colour with its entries, its star's block-inverse row and two
     # additions), summed over one sweep (colours 0..C-1, C-2..0)
+    fp64_peak, fp64_src = fp64_peak_tflops(dev)
     fp64 = None
     if achieved and last_colour(res) is not None and res[-1]["info"]["precision"][0] == amgh.AMGH_F64:
         sw_bytes, sw_flops = finest_sweep_work(A, G, last_colour(res), 8, 8)
         fl_rate = achieved * 1e9 * (sw_flops / sw_bytes) / 1e12
-        fp64 = {"achieved": fl_rate, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": fl_rate / FP64_NOMINAL_TFLOPS, "peak_source": "nominal",
+        fp64 = {"achieved": fl_rate, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": fl_rate / fp64_peak, "peak_source": fp64_src,
                 "flops_per_byte": sw_flops / sw_bytes,
                 "sweep_bytes_vs_library": sw_bytes / (ks_bytes / ks_launch * launches_per_sweep(res)) if ks_launch else None}
     modes = {0: "colour", 1: "fused", 2: "persistent", 3: "staged", 4: "stream"}
@@ -370,9 +539,26 @@ def run_gpu(args, rank, world, local_rank):
     h2d = csr_bytes(A) + csr_bytes(G) + 8 * n + 8 * n
     d2h = 8 * n
 
+    # per-level sweep profile on one more hierarchy (outside the timed region)
+    hl = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
+    levels = level_profile(amgh, hl, A, G, peak, fp64_peak)
+    amgh.amgh_destroy(hl)
+    variants = None
+    if args.variants != "none" and world == 1:
+        vp = W.make_config(args.variants)
+        vin = (dcsr(vp["A"]), dcsr(vp["G"]), torch.tensor(vp["f"], device=dev))
+        variants = [time_variant(amgh, vp, vin, pr, ms, args.variant_steps, 1)
+                    for pr, ms in (("f64", "smoother"), ("f32", "smoother"), ("f32", "requested"),
+                                   ("bf16", "smoother"), ("bf16", "requested"))]
+        del vin, vp
+        base = variants[0]["s_per_step"]
+        for v in variants:
+            v["speedup_vs_f64"] = base / v["s_per_step"]
+
     if rank != 0:
         return 0
-    cpu = oracle_sample(gpu_iters=last["iters"], workload=args.workload)
+    cpu = oracle_sample(workload=args.workload)
+    cpu_all = oracle_all_cores(workload=args.workload)
     info = last["info"]
     line = {
         "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -383,6 +569,8 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
                    "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
                    "level_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["precision"]],
+                   "matrix_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["matrix_precision"]],
+                   "fused_restrict": info["fused_rr"],
                    "smoother_lanes": info["lanes"], "smoother_fused": info["fused"],
                    "dense_tail_level": info["dense_tail"]},
         "pcg_iters": last["iters"], "relres": last["relres"], "converged": last["ok"],
@@ -397,10 +585,14 @@ def run_gpu(args, rank, world, local_rank):
                      "ms_per_launch": ks_ms / ks_launch if ks_launch else None,
                      "timed_on": "CUDA events on the handle's stream, last timed step",
                      "fp64": fp64},
-        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu", "nproc")},
+        "cpu_baseline_all_cores": {k: cpu_all[k] for k in ("value", "unit", "cores", "kind", "sample", "cpu", "nproc")},
         "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(gpu_launches), "clocks": clk,
     }
+    line["roofline"]["levels"] = levels
+    if variants is not None:
+        line["variants"] = variants
     print(json.dumps(line), flush=True)
     return 0
 

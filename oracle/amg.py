@@ -338,11 +338,12 @@ def interior_patches(A, edges, ndof, p_max=128, ring=1):
     return patches
 
 
-def interpolation_local(A, edges, patches, ndof):
-    """Eq. sparseP with R1: column c = R^T e_c - S_p A_pp^{-1} A_{p,E_c} r_c on patch p."""
-    A = sp.csr_matrix(A)
+def _local_columns(task):
+    """Columns c0, c0+1, ... of Eq. sparseP with R1 (one run of coarse edges and their patches):
+    R^T e_c on the pair, -A_pp^{-1} A_{p,E_c} r_c on the patch.  Returns (rows, cols, vals)."""
+    A, c0, edges, patches = task
     rows, cols, vals = [], [], []
-    for c, (e, p) in enumerate(zip(edges, patches)):
+    for c, (e, p) in enumerate(zip(edges, patches), c0):
         d1, s1, d2, s2 = e[0], e[1], e[2], e[3]
         rows += [d1, d2]
         cols += [c, c]
@@ -354,6 +355,24 @@ def interpolation_local(A, edges, patches, ndof):
             rows += p.tolist()
             cols += [c] * len(p)
             vals += x.tolist()
+    return rows, cols, vals
+
+
+def _runs(count, nchunks):
+    b = np.linspace(0, count, max(1, nchunks) + 1).astype(int)
+    return list(zip(b[:-1], b[1:]))
+
+
+def interpolation_local(A, edges, patches, ndof, pmap=map, nchunks=1):
+    """Eq. sparseP with R1: column c = R^T e_c - S_p A_pp^{-1} A_{p,E_c} r_c on patch p.  The
+    columns are independent; `pmap` (a map over runs of columns, e.g. a process pool's) may
+    compute the nchunks runs in parallel; the result does not depend on it."""
+    A = sp.csr_matrix(A)
+    rows, cols, vals = [], [], []
+    for r, c, v in pmap(_local_columns, [(A, a, edges[a:b], patches[a:b]) for a, b in _runs(len(edges), nchunks)]):
+        rows += r
+        cols += c
+        vals += v
     P = sp.csr_matrix((vals, (rows, cols)), shape=(ndof, len(edges)))
     P.sort_indices()
     return P
@@ -409,9 +428,19 @@ def colour_stars(A, G):
     return colour
 
 
-def star_inverses(A, st):
+def _inverses(task):
+    A, blocks = task
+    return [np.linalg.inv(A[b][:, b].toarray()) for b in blocks]
+
+
+def star_inverses(A, st, pmap=map, nchunks=1):
+    """Dense inverses of the star blocks A[B_j, B_j] (independent; `pmap` as in
+    interpolation_local)."""
     A = sp.csr_matrix(A)
-    return [np.linalg.inv(A[b][:, b].toarray()) for b in st]
+    out = []
+    for part in pmap(_inverses, [(A, st[a:b]) for a, b in _runs(len(st), nchunks)]):
+        out += part
+    return out
 
 
 def l1_diagonal(A):
@@ -450,7 +479,7 @@ def smooth_post(L, f, x):
 # ----------------------------------------------------------------------------------------------
 
 
-def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta=0.25):
+def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta=0.25, pmap=map, nchunks=1):
     """One application of the two-level setup of Sec. 4: augment G (Alg. 1), split the nodal dual
     operator (Alg. 2), pair edges (Alg. 3), interpolate (Eq. sparseP), form G_c (Eq. Gc)."""
     A = sp.csr_matrix(A)
@@ -471,37 +500,39 @@ def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta
         P = interpolation_global(A, edges, ndof)
     else:
         patches = interior_patches(A, edges, ndof, p_max=p_max, ring=ring)
-        P = interpolation_local(A, edges, patches, ndof)
+        P = interpolation_local(A, edges, patches, ndof, pmap=pmap, nchunks=nchunks)
     out.update(R=R, Gc=Gc, coarse_nodes=keep, patches=patches, P=P)
     return out
 
 
-def smoother_level(A, G):
+def smoother_level(A, G, pmap=map, nchunks=1):
     A = sp.csr_matrix(A)
     st = stars(G)
     colour = colour_stars(A, G)
     ncol = int(colour.max()) + 1 if len(colour) else 0
     return dict(A=A, stars=st, colour=colour, ncolours=ncol,
                 colour_members=[np.flatnonzero(colour == c) for c in range(ncol)],
-                inv=star_inverses(A, st), l1=l1_diagonal(A))
+                inv=star_inverses(A, st, pmap=pmap, nchunks=nchunks), l1=l1_diagonal(A))
 
 
 def setup(A, G, coarse_size=100, max_levels=20, interp="local", p_max=128, ring=1,
-          stall_ratio=0.9, strength="classical", theta=0.25):
+          stall_ratio=0.9, strength="classical", theta=0.25, pmap=map, nchunks=1):
     """Build the multilevel hierarchy (R9).  Returns a list of level dicts; every level but the
-    last carries P, the last carries the dense Cholesky factor of its matrix."""
+    last carries P, the last carries the dense Cholesky factor of its matrix.  pmap / nchunks
+    spread the independent local solves and star inverses over a parallel map (same result)."""
     A = sp.csr_matrix(A)
     A.sort_indices()
     G = sp.csr_matrix(G)
     levels = []
     while True:
         n = A.shape[0]
-        L = smoother_level(A, G)
+        L = smoother_level(A, G, pmap=pmap, nchunks=nchunks)
         L["G"] = G
         levels.append(L)
         if n <= coarse_size or len(levels) == max_levels:
             break
-        cz = coarsen(A, G, interp=interp, p_max=p_max, ring=ring, strength=strength, theta=theta)
+        cz = coarsen(A, G, interp=interp, p_max=p_max, ring=ring, strength=strength, theta=theta,
+                     pmap=pmap, nchunks=nchunks)
         L["coarsening"] = cz
         nc = len(cz["edges"])
         if nc == 0 or nc > stall_ratio * n:

@@ -13,18 +13,21 @@ CONFIGS = {
     "hex32_checker": dict(n=32, alpha="checker", beta=1e-2, rhs_seed=1),
     # 16^3 version (10,800 DoFs)
     "hex16_checker": dict(n=16, alpha="checker", beta=1e-2, rhs_seed=1),
+    # 24^3 version (38,088 DoFs): the bounded CPU sample of the family
+    "hex24_checker": dict(n=24, alpha="checker", beta=1e-2, rhs_seed=1),
     # 128^3, log10 alpha ~ U(-3,3) per element with 64 inclusions alpha = 1e6, beta = 1 (6,193,536 DoFs)
     "hex128_spheres": dict(n=128, alpha="spheres", beta=1.0, rhs_seed=2),
     # 96^3 checkerboard (12^3-element blocks), for 64 right-hand sides with seeds 0..63
     "hex96_checker": dict(n=96, alpha="checker", beta=1e-2, rhs_seed=0),
-    # 16^3 member of the inclusion family (bounded CPU samples)
+    # 16^3 and 24^3 members of the inclusion family (bounded CPU samples)
     "hex16_spheres": dict(n=16, alpha="spheres", beta=1.0, rhs_seed=2),
+    "hex24_spheres": dict(n=24, alpha="spheres", beta=1.0, rhs_seed=2),
 }
 
-# one-line descriptions and the 16^3 member of each family (bounded CPU samples)
+# one-line descriptions and the 24^3 member of each family (bounded CPU samples)
 DESCRIPTIONS = {
-    "checker": ("alpha on an 8^3 checkerboard of blocks {1, 1e4}", "hex16_checker"),
-    "spheres": ("log10 alpha ~ U(-3,3) per element with 64 spherical inclusions of alpha = 1e6", "hex16_spheres"),
+    "checker": ("alpha on an 8^3 checkerboard of blocks {1, 1e4}", "hex24_checker"),
+    "spheres": ("log10 alpha ~ U(-3,3) per element with 64 spherical inclusions of alpha = 1e6", "hex24_spheres"),
     "one": ("alpha = 1", "hex8_unit"),
 }
 
