@@ -36,8 +36,6 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dense-tail", type=int, default=None,
                     help="rows at or below which the V-cycle tail is one dense operator (library default if unset)")
-    ap.add_argument("--matrix-storage", default=None, choices=["smoother", "requested"],
-                    help="storage of A, P, P^T in the residual, l1 and transfer passes (library default if unset)")
     ap.add_argument("--fuse-restrict", type=int, default=None, choices=[-1, 0, 1],
                     help="fused residual + restriction: -1 tuned per level, 0 off, 1 on (library default if unset)")
     ap.add_argument("--variants", default="hex128_spheres",
@@ -177,7 +175,7 @@ def level_profile(amgh, h, A0, G0, hbm_peak, fp64_peak, nvc=10):
     return out
 
 
-def time_variant(amgh, prob, dev_inputs, precision, matrix_storage, steps, warmup):
+def time_variant(amgh, prob, dev_inputs, precision, steps, warmup):
     """Setup + flexible CG to 1e-8 on a workload with a requested storage precision: wall time
     of whole steps (synchronised) after warm-up ones, with the level storages the handle chose."""
     import numpy as np
@@ -186,12 +184,11 @@ def time_variant(amgh, prob, dev_inputs, precision, matrix_storage, steps, warmu
     Ad, Gd, fd = dev_inputs
     xd = torch.zeros_like(fd)
     code = {"f64": amgh.AMGH_F64, "f32": amgh.AMGH_F32, "bf16": amgh.AMGH_BF16}[precision]
-    ms = {"smoother": amgh.AMGH_MATRIX_SMOOTHER, "requested": amgh.AMGH_MATRIX_REQUESTED}[matrix_storage]
     res = []
     for i in range(warmup + steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = amgh.amgh_setup(Ad, Gd, precision=code, matrix_storage=ms)
+        h = amgh.amgh_setup(Ad, Gd, precision=code)
         t1 = time.perf_counter()
         xd.zero_()
         it, rel, ok = amgh.amgh_pcg_solve(h, fd, xd, 1e-8, 5000)
@@ -205,12 +202,11 @@ def time_variant(amgh, prob, dev_inputs, precision, matrix_storage, steps, warmu
     true_rel = float(np.linalg.norm(f - A @ xs) / np.linalg.norm(f))
     names = {0: "f64", 1: "f32", 2: "bf16"}
     info = res[-1][6]
-    return {"workload": prob["name"], "precision": precision, "matrix_storage": matrix_storage,
+    return {"workload": prob["name"], "precision": precision,
             "s_per_step": statistics.mean(r[0] for r in res), "setup_s": statistics.mean(r[1] for r in res),
             "solve_s": statistics.mean(r[2] for r in res), "pcg_iters": res[-1][3], "relres": res[-1][4],
             "converged": res[-1][5], "true_relres": true_rel,
             "level_precision": [names[q] for q in info["precision"]],
-            "matrix_precision": [names[q] for q in info["matrix_precision"]],
             "block_kappa": info["block_kappa"], "levels": info["n"], "steps": steps, "warmup": warmup}
 
 
@@ -273,13 +269,21 @@ def traffic_for(kernel, workload, mode):
 # CPU oracle leg (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------------------------
 def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), with the architecture."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         for line in open("/proc/cpuinfo"):
             if line.lower().startswith(("model name", "cpu model")):
-                return line.split(":", 1)[1].strip()
+                return "%s (%s)" % (line.split(":", 1)[1].strip(), platform.machine())
     except OSError:
         pass
-    import platform
     return platform.machine()
 
 
@@ -411,9 +415,6 @@ def run_gpu(args, rank, world, local_rank):
     fd = torch.tensor(f, device=dev)
     xd = torch.zeros(n, dtype=torch.float64, device=dev)
     extra = {} if args.dense_tail is None else {"dense_tail": args.dense_tail}
-    if args.matrix_storage is not None:
-        extra["matrix_storage"] = {"smoother": amgh.AMGH_MATRIX_SMOOTHER, "requested": amgh.AMGH_MATRIX_REQUESTED}[
-            args.matrix_storage]
     if args.fuse_restrict is not None:
         extra["fuse_restrict"] = args.fuse_restrict
 
@@ -547,9 +548,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.variants != "none" and world == 1:
         vp = W.make_config(args.variants)
         vin = (dcsr(vp["A"]), dcsr(vp["G"]), torch.tensor(vp["f"], device=dev))
-        variants = [time_variant(amgh, vp, vin, pr, ms, args.variant_steps, 1)
-                    for pr, ms in (("f64", "smoother"), ("f32", "smoother"), ("f32", "requested"),
-                                   ("bf16", "smoother"), ("bf16", "requested"))]
+        variants = [time_variant(amgh, vp, vin, pr, args.variant_steps, 1) for pr in ("f64", "f32", "bf16")]
         del vin, vp
         base = variants[0]["s_per_step"]
         for v in variants:
@@ -569,7 +568,6 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
                    "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
                    "level_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["precision"]],
-                   "matrix_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["matrix_precision"]],
                    "fused_restrict": info["fused_rr"],
                    "smoother_lanes": info["lanes"], "smoother_fused": info["fused"],
                    "dense_tail_level": info["dense_tail"]},

@@ -67,18 +67,6 @@ typedef struct {
  * accumulates in float, BF16 stores bfloat16 values and accumulates in float. */
 enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
 
-/* storage of the matrices A_l, P_l, P_l^T (and W_l = P_l^T A_l) that the residual, l1-Jacobi
- * and transfer passes read, when a reduced precision is requested: SMOOTHER keeps them in the
- * storage each level's smoother gets from the condition guard (one storage per level);
- * REQUESTED stores them in the requested precision on every level, while the smoother's star
- * rows and block inverses (and the vectors) still follow the guard.  Those passes solve no block
- * system, so the contraction guard does not bind them; their rounding perturbs the coarse
- * right-hand side by u |A| |y|, which reaches the V-cycle's output at about u sqrt(kappa) in the
- * energy norm.  REQUESTED therefore takes the requested precision where u sqrt(kappa) <= 1/4,
- * else FP32 where that holds, else the smoother's storage; the flexible CG of a reduced-precision
- * request absorbs the remaining inexactness. */
-enum { AMGH_MATRIX_SMOOTHER = 0, AMGH_MATRIX_REQUESTED = 1 };
-
 /* interior extension of the coarse variables (Eq. sparseP): exact local solves on each coarse
  * edge's patch, or, on the finest level, the values predicted by a trained network (amgh_mlp_*)
  * on the same pattern.  A learned setup measures the convergence factor rho of 10 stand-alone
@@ -115,12 +103,10 @@ typedef struct {
                              autotuner keeps it when it times faster than the residual pass plus
                              the restriction (default); 0: never (W is not formed); 1: on every
                              level                                                             */
-    int matrix_storage;   /* AMGH_MATRIX_SMOOTHER (default) | AMGH_MATRIX_REQUESTED            */
 } amgh_params;
 
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict -1,
- * matrix_storage SMOOTHER. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict -1. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,
@@ -256,8 +242,6 @@ typedef struct {
     double rho;           /* measured convergence factor of the kept hierarchy (learned setups)  */
     double rho_exact;     /* the exact local solves' factor it was compared with               */
     double interp_ms;     /* wall time of filling the finest level's P values (solves or network) */
-    int matrix_precision[32]; /* storage of A_l, P_l, P_l^T (and W_l) in the residual, l1-Jacobi
-                                 and transfer passes (AMGH_F64/F32/BF16)                        */
     int fused_rr[32];     /* 1 where the V-cycle computes the coarse right-hand side in the fused
                              pass over P^T and W = P^T A, 0 where residual and restriction run
                              apart                                                             */

@@ -15,7 +15,6 @@ from . import build as _build
 AMGH_OK, AMGH_ERR_INVALID_ARG, AMGH_ERR_NOT_SPD, AMGH_ERR_NOT_CONVERGED = 0, 1, 2, 3
 AMGH_ERR_CUDA, AMGH_ERR_OOM, AMGH_ERR_TIMEOUT, AMGH_ERR_SETUP_STALL, AMGH_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 AMGH_F64, AMGH_F32, AMGH_BF16 = 0, 1, 2
-AMGH_MATRIX_SMOOTHER, AMGH_MATRIX_REQUESTED = 0, 1
 AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED = 0, 1
 KIND = {"schwarz": 0, "l1": 1, "residual": 2, "restrict": 3, "prolong": 4, "coarse": 5, "spmv": 6, "rr": 7}
 
@@ -31,7 +30,7 @@ class amgh_params(ctypes.Structure):
                 ("interp", ctypes.c_int), ("ring", ctypes.c_int), ("p_max", ctypes.c_int),
                 ("theta", ctypes.c_double), ("stall_ratio", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("dense_tail", ctypes.c_int), ("mlp", ctypes.c_void_p), ("rho_ref", ctypes.c_double),
-                ("fuse_restrict", ctypes.c_int), ("matrix_storage", ctypes.c_int)]
+                ("fuse_restrict", ctypes.c_int)]
 
 
 class amgh_hier_info(ctypes.Structure):
@@ -43,7 +42,7 @@ class amgh_hier_info(ctypes.Structure):
                 ("lanes", ctypes.c_int * 32), ("fused", ctypes.c_int * 32), ("block_kappa", ctypes.c_double * 32),
                 ("dense_tail", ctypes.c_int), ("interp_used", ctypes.c_int), ("rho", ctypes.c_double),
                 ("rho_exact", ctypes.c_double), ("interp_ms", ctypes.c_double),
-                ("matrix_precision", ctypes.c_int * 32), ("fused_rr", ctypes.c_int * 32)]
+                ("fused_rr", ctypes.c_int * 32)]
 
 
 _LIB = None
@@ -298,8 +297,7 @@ def amgh_info(h):
                 setup_device_ms=info.setup_device_ms, precision=list(info.precision[:L]),
                 lanes=list(info.lanes[:L]), fused=list(info.fused[:L]), block_kappa=list(info.block_kappa[:L]),
                 dense_tail=info.dense_tail, interp_used=info.interp_used, rho=info.rho, rho_exact=info.rho_exact,
-                interp_ms=info.interp_ms, matrix_precision=list(info.matrix_precision[:L]),
-                fused_rr=list(info.fused_rr[:L]))
+                interp_ms=info.interp_ms, fused_rr=list(info.fused_rr[:L]))
 
 
 def amgh_level_structure(h, l):

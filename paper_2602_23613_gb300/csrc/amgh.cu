@@ -86,10 +86,9 @@ static void build_sell(const HostCSR& pat, const DevCSR& dev, Sell<V>& S, cudaSt
 // V-cycle engine: every level carries its own storage precision (FP64, or FP32 / BF16 with FP32
 // vectors) and its own layouts, chosen at setup by the precision policy and the autotuner.
 // ---------------------------------------------------------------------------------------------
-// V: storage of the smoother (star rows and block inverses), decided by the condition guard;
-// T: vectors and accumulation; VA: storage of A, P, P^T and W = P^T A in the residual, l1-Jacobi
-// and transfer passes (the requested precision when the matrices are stored apart from the
-// smoother, else V).
+// V: storage of the level (star rows, block inverses, A, P, P^T and W = P^T A), decided by the
+// condition guard; T: vectors and accumulation.  AT names the storage the residual, l1-Jacobi and
+// transfer passes read (the same V).
 template <class V, class T, class VA = V>
 struct LevelX {
     using VT = V;
@@ -104,8 +103,7 @@ struct LevelX {
     std::vector<int64_t> col_nnz, col_inv, col_rows;   // per colour, for the algorithmic bytes
 };
 using bf16 = __nv_bfloat16;
-using LevelVar = std::variant<LevelX<double, double>, LevelX<float, float>, LevelX<bf16, float>,
-                              LevelX<double, double, float>, LevelX<double, double, bf16>, LevelX<float, float, bf16>>;
+using LevelVar = std::variant<LevelX<double, double>, LevelX<float, float>, LevelX<bf16, float>>;
 
 // whether a level's vectors are FP64
 static bool vectors_double(const LevelVar& v) {
@@ -128,7 +126,6 @@ struct LevelChoice {
     int resident_g = 1;    // ... of this many 256-thread chunk groups each
     bool resident_grid = false;   // ... as a cooperative grid of `resident` CTAs with x in global memory
     double kappa = 0.0;
-    int prec_ap = AMGH_F64;  // storage of A, P, P^T and W in the residual, l1 and transfer passes
     bool fuse_rr = false;    // residual + restriction fused into one pass over P^T and W = P^T A
     int L_RR = 1;            // lanes per row of that pass (P^T and W share it)
 };
@@ -1139,10 +1136,9 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             const double kap = ch.kappa;
-            const int pap = ch.prec_ap, prec = ch.prec;
+            const int prec = ch.prec;
             ch = it->second;
             ch.kappa = kap;
-            ch.prec_ap = pap;
             ch.prec = prec;
             cached = true;
         }
@@ -1424,43 +1420,21 @@ static int level_precision(int requested, double kappa) {
     return AMGH_F64;
 }
 
-// storage of a level's A, P, P^T and W: the smoother's (coupled), or, stored apart, the widest
-// of the requested precision, FP32 and the smoother's storage that keeps u sqrt(kappa) <= 1/4.
-// Rounding the matrices perturbs the residual by u |A| |y|; the coarse correction carries that
-// perturbation into the V-cycle's output, where it weighs about u sqrt(kappa) against the output
-// in the energy norm (kappa: the level's star-block condition estimate, standing in for the
-// level operator's); the guard keeps it at the smoother guard's margin.
-static int matrix_precision(const amgh_params& prm, int smoother_prec, double kappa) {
-    if (prm.precision == AMGH_F64 || prm.matrix_storage != AMGH_MATRIX_REQUESTED) return smoother_prec;
-    if (smoother_prec == AMGH_BF16) return AMGH_BF16;
-    const double u32 = 5.9604644775390625e-08, u16 = 3.90625e-03, sk = std::sqrt(std::max(kappa, 0.0));
-    if (prm.precision == AMGH_BF16 && sk * u16 <= 0.25) return AMGH_BF16;
-    if (sk * u32 <= 0.25) return AMGH_F32;
-    return smoother_prec;
-}
-
 template <class T>
 struct TypeTag {
     using type = T;
 };
 
-// the engine level of a (smoother storage, matrix storage) pair
+// the engine level of a storage precision
 static void emplace_level(amgh_ctx* h, Engine* e, int l, LevelChoice& ch) {
     auto make = [&](auto tag) {
         using Lv = typename decltype(tag)::type;
         e->L.emplace_back(std::in_place_type<Lv>);
         build_level(h, l, std::get<Lv>(e->L.back()), ch);
     };
-    const int sp = ch.prec, ap = ch.prec_ap;
-    if (sp == AMGH_F64 && ap == AMGH_F64) make(TypeTag<LevelX<double, double>>{});
-    else if (sp == AMGH_F64 && ap == AMGH_F32) make(TypeTag<LevelX<double, double, float>>{});
-    else if (sp == AMGH_F64) make(TypeTag<LevelX<double, double, bf16>>{});
-    else if (sp == AMGH_F32 && ap == AMGH_BF16) make(TypeTag<LevelX<float, float, bf16>>{});
-    else if (sp == AMGH_F32) make(TypeTag<LevelX<float, float>>{});
-    else {
-        ch.prec_ap = AMGH_BF16;
-        make(TypeTag<LevelX<bf16, float>>{});
-    }
+    if (ch.prec == AMGH_F64) make(TypeTag<LevelX<double, double>>{});
+    else if (ch.prec == AMGH_F32) make(TypeTag<LevelX<float, float>>{});
+    else make(TypeTag<LevelX<bf16, float>>{});
 }
 
 static double level_kappa(amgh_ctx* h, int l) {
@@ -1492,9 +1466,6 @@ static void build_engine(amgh_ctx* h, Engine* e) {
         // the condition estimate only decides a reduced precision; an FP64 request skips it
         ch.kappa = h->prm.precision == AMGH_F64 ? 0.0 : level_kappa(h, l);
         ch.prec = level_precision(h->prm.precision, ch.kappa);
-        ch.prec_ap = matrix_precision(h->prm, ch.prec, ch.kappa);
-        // a float smoother with FP64 matrices does not occur: the matrices are at most as wide
-        if (ch.prec != AMGH_F64 && ch.prec_ap == AMGH_F64) ch.prec_ap = ch.prec;
         emplace_level(h, e, l, ch);
     }
     // coarsest level: dense inverse, precision from its 1-norm condition estimate
@@ -2544,7 +2515,6 @@ void amgh_default_params(amgh_params* p) {
     p->mlp = nullptr;
     p->rho_ref = 0.0;
     p->fuse_restrict = -1;
-    p->matrix_storage = AMGH_MATRIX_SMOOTHER;
 }
 
 amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params, amgh_handle* out) {
@@ -2821,7 +2791,6 @@ amgh_status amgh_info(amgh_handle h, amgh_hier_info* info) {
                            : cl.persist > 0 ? (cl.cluster ? 5 : cl.staged ? 3 : 2) : cl.stream > 0 ? 4
                            : cl.pdl ? 6 : 0;
             info->block_kappa[l] = e->choice[l].kappa;
-            info->matrix_precision[l] = cl.prec_ap;
             info->fused_rr[l] = cl.fuse_rr && l + 1 < nlev && (e->tail < 0 || l < e->tail) ? 1 : 0;
         }
         return AMGH_OK;

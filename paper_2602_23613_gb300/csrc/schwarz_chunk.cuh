@@ -34,19 +34,22 @@ __device__ __forceinline__ void schwarz_chunk(const SmootherLView<V>& S, int cta
     const int w = (int)((S.rows.slice_ptr[slice + 1] - st) >> 5);
     const int32_t* c = S.rows.col + st + lane;
     const V* v = S.rows.val + st + lane;
-    T s = T(0);
+    // the residual f_i - sum_j a_ij x_j as one FMA chain started at f_i (the row's first lane
+    // carries f_i; the lanes' partial sums meet below), and the block update x_i + sum_k
+    // (A_BB^-1)_ik r_k as one chain started at x_i: no separate subtraction or addition
+    T s = (sub == 0 && row >= 0) ? f[row] : T(0);
 #pragma unroll 8
-    for (int t = 0; t < w; ++t) s = fma(widen<T>(v[32 * t]), x[c[32 * t]], s);
+    for (int t = 0; t < w; ++t) s = fma(-widen<T>(v[32 * t]), x[c[32 * t]], s);
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (sub == 0) smem_r[slot] = row >= 0 ? f[row] - s : T(0);
+    if (sub == 0) smem_r[slot] = row >= 0 ? s : T(0);
     __syncthreads();
     if (sub == 0 && row >= 0) {
         const int base = S.slot_base[gslot], bs = S.slot_bsize[gslot];
         const V* iv = S.inv + (int64_t)cta * S.bmax * SLOTS + slot;
-        T d = T(0);
+        T d = x[row];
         for (int k = 0; k < bs; ++k) d = fma(widen<T>(iv[(int64_t)k * SLOTS]), smem_r[base + k], d);
-        x[row] += d;
+        x[row] = d;
     }
     __syncthreads();
 }

@@ -199,14 +199,14 @@ __global__ void __launch_bounds__(G* CTA_THREADS, 1)
             const int wn = (int)((mn.s1 - mn.s0) >> 5);
             const int32_t* cpn = S.rows.col + mn.s0 + lane;
             const V* vpn = S.rows.val + mn.s0 + lane;
-            // residual of the current item; each register is refilled with the next item's
-            // entry as soon as it has been used
-            T s0 = T(0), s1 = T(0);
+            // residual of the current item, started at f_i on the row's first lane; each
+            // register is refilled with the next item's entry as soon as it has been used
+            T s0 = fr, s1 = T(0);
 #pragma unroll
             for (int t = 0; t < PF; ++t) {
                 if (t < w) {
-                    if (t & 1) s1 = fma(widen<T>(vv[t]), xs[cc[t]], s1);
-                    else s0 = fma(widen<T>(vv[t]), xs[cc[t]], s0);
+                    if (t & 1) s1 = fma(-widen<T>(vv[t]), xs[cc[t]], s1);
+                    else s0 = fma(-widen<T>(vv[t]), xs[cc[t]], s0);
                 }
                 if (t < wn) {
                     cc[t] = cpn[32 * t];
@@ -217,24 +217,25 @@ __global__ void __launch_bounds__(G* CTA_THREADS, 1)
                 const int32_t* cp = S.rows.col + mc.s0 + lane;
                 const V* vp = S.rows.val + mc.s0 + lane;
                 for (int t = PF; t < w; ++t) {
-                    if (t & 1) s1 = fma(widen<T>(vp[32 * t]), xs[cp[32 * t]], s1);
-                    else s0 = fma(widen<T>(vp[32 * t]), xs[cp[32 * t]], s0);
+                    if (t & 1) s1 = fma(-widen<T>(vp[32 * t]), xs[cp[32 * t]], s1);
+                    else s0 = fma(-widen<T>(vp[32 * t]), xs[cp[32 * t]], s0);
                 }
             }
             T s = s0 + s1;
 #pragma unroll
             for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (sub == 0) smem_r[g][slot] = mc.row >= 0 ? fr - s : T(0);
+            if (sub == 0) smem_r[g][slot] = mc.row >= 0 ? s : T(0);
             rs_group_sync<G>(g);
             T xn = T(0);
             if (sub == 0 && mc.row >= 0) {
-                T d = T(0);
+                // the block update as one chain started at x_i
+                T d = xs[mc.row];
 #pragma unroll
                 for (int j = 0; j < BM; ++j)
                     if (j < mc.bs) d = fma(ivr[j], smem_r[g][mc.base + j], d);
                 const V* iv = S.inv + (int64_t)mc.k * S.bmax * SLOTS + slot;
                 for (int j = BM; j < mc.bs; ++j) d = fma(widen<T>(iv[(int64_t)j * SLOTS]), smem_r[g][mc.base + j], d);
-                xn = xs[mc.row] + d;
+                xn = d;
             }
             if (GRID) {
                 if (sub == 0 && mc.row >= 0) x[mc.row] = xn;

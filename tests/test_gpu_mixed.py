@@ -58,11 +58,11 @@ def test_mixed_vcycle_and_fcg(amgh, prec, u, case):
     A = p["A"]
     e = z.cpu().numpy() - zo
     err_A = np.sqrt(e @ (A @ e) / (zo @ (A @ zo)))
-    # the per-level bound 8 (kappa u_s + u_A) of test_gpu_mixed_parity.py (1-norm condition
+    # the per-level bound 8 ((2C-1) kappa u + u) of test_gpu_mixed_parity.py (1-norm condition
     # estimates here), four times its largest value for the V-cycle, in the max norm
     U = {0: 2.0 ** -53, 1: 2.0 ** -24, 2: 2.0 ** -8}
-    tv = 4 * max(8 * (k * U[q] + U[m]) for q, m, k in
-                 zip(info["precision"][:-1], info["matrix_precision"][:-1], info["block_kappa"][:-1]))
+    tv = 4 * max(8 * (2 * c * k * U[q] + U[q]) for q, c, k in
+                 zip(info["precision"][:-1], info["ncolours"][:-1], info["block_kappa"][:-1]))
     err_max = float(np.abs(e).max() / np.abs(zo).max())
     print("mixed %s %s V-cycle vs FP64 oracle: A-norm rel err %.3e, max-norm %.3e (bound %.2e)"
           % (case, prec, err_A, err_max, tv))

@@ -1,21 +1,22 @@
 """Reduced-precision levels (FP32 or BF16 storage, FP32 accumulation) kernel by kernel, with every
-level run in its own storage (no dense tail).
+level run in its own storage (no dense tail), BF16 levels included (the 12^3 and 16^3 workloads
+have coarse levels whose star blocks pass kappa 2^-8 <= 1/4).
 
 Single-pass kernels (SpMV, residual, restriction, prolongation, fused restriction) are compared
 with the oracle's formula evaluated in FP64 on the SAME rounded operands: the level's FP64
 matrices as the library computed them (held to the oracle's by the FP64 parity tests), rounded
-to the level's matrix storage, and the vectors rounded to its vector type.  What may then differ
+to the level's storage, and the vectors rounded to its vector type.  What may then differ
 is only the summation in the accumulation type and the final rounding to the vector type,
 bounded componentwise by
   |err_i| <= 2 ((k_i + 2) u_acc (sum_j |a_ij x_j| + |f_i|) + u_vec |y_i|),
 k_i the row length, u_acc and u_vec the unit roundoffs of the accumulation and vector types.
 
 Whole smoothing steps and the V-cycle are compared with the FP64 oracle on unrounded data:
-every block solve of a level with condition kappa and smoother storage u_s moves by up to about
-kappa u_s, the errors of the 2C-1 sequential colour steps add up (the sweep is a contraction, so
-none is amplified), and the l1-Jacobi pass moves by the matrix storage's u_A, so the bound per
-level is 8 ((2C-1) kappa u_s + u_A), and 4 times the largest level bound for the V-cycle.  The
-achieved errors are printed."""
+every block solve of a level with condition kappa and storage unit roundoff u moves by up to
+about kappa u, the errors of the 2C-1 sequential colour steps add up (the sweep is a contraction,
+so none is amplified), and the l1-Jacobi pass moves by about u, so the bound per level is
+8 ((2C-1) kappa u + u), and 4 times the largest level bound for the V-cycle.  The achieved errors
+are printed."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -80,54 +81,43 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module", params=[(c, p, m) for c in CASES for p in ("f32", "bf16") for m in (0, 1)],
-                ids=lambda t: "%s-%s-%s" % (t[0], t[1], "coupled" if t[2] == 0 else "requested"))
+@pytest.fixture(scope="module", params=[(c, p) for c in CASES for p in ("f32", "bf16")],
+                ids=lambda t: "%s-%s" % t)
 def mixed(request, amgh):
-    case, prec, storage = request.param
+    case, prec = request.param
     p = CASES[case]()
     code = {"f32": amgh.AMGH_F32, "bf16": amgh.AMGH_BF16}[prec]
     H = O.setup(p["A"], p["G"], coarse_size=100)
-    h = amgh.amgh_setup(p["A"], p["G"], precision=code, dense_tail=0, matrix_storage=storage, fuse_restrict=1)
+    h = amgh.amgh_setup(p["A"], p["G"], precision=code, dense_tail=0, fuse_restrict=1)
     info = amgh.amgh_info(h)
-    print("mixed %s %s %s: smoother %s, matrices %s, kappa %s" % (
-        case, prec, "coupled" if storage == 0 else "requested", info["precision"], info["matrix_precision"],
-        ["%.1e" % k for k in info["block_kappa"]]))
-    return case, prec, storage, p, H, h, info
+    print("mixed %s %s: storage %s, kappa %s" % (case, prec, info["precision"],
+                                                 ["%.1e" % k for k in info["block_kappa"]]))
+    return case, prec, p, H, h, info
 
 
 def test_storage_policy(amgh, mixed):
-    """Smoother storage: reduced only where kappa u <= 1/4.  Matrix storage stored apart: the
-    requested precision where u sqrt(kappa) <= 1/4, else FP32 where that holds, else the
-    smoother's; coupled: the smoother's."""
-    case, prec, storage, p, H, h, info = mixed
-    req = {"f32": 1, "bf16": 2}[prec]
+    """A level is stored reduced only where kappa u <= 1/4 (BF16 first when requested, then FP32),
+    and the BF16 request does run BF16 levels on these workloads."""
+    case, prec, p, H, h, info = mixed
     for l, (q, k) in enumerate(zip(info["precision"][:-1], info["block_kappa"][:-1])):
         if q == 2:
-            assert k * 2.0 ** -8 <= 0.25
+            assert prec == "bf16" and k * 2.0 ** -8 <= 0.25
         elif q == 1:
-            assert k * 2.0 ** -24 <= 0.25
+            assert k * 2.0 ** -24 <= 0.25 and (prec == "f32" or k * 2.0 ** -8 > 0.25)
         else:
             assert k * 2.0 ** -24 > 0.25
-        mq = info["matrix_precision"][l]
-        if storage == 0 or q == 2:
-            assert mq == q
-            continue
-        if req == 2 and np.sqrt(k) * 2.0 ** -8 <= 0.25:
-            assert mq == 2
-        elif np.sqrt(k) * 2.0 ** -24 <= 0.25:
-            assert mq == 1
-        else:
-            assert mq == q
+    if prec == "bf16" and case != "hex12_lognormal":
+        assert 2 in info["precision"]
 
 
 def test_single_pass_kernels_on_rounded_operands(amgh, mixed):
     import torch
-    case, prec, storage, p, H, h, info = mixed
+    case, prec, p, H, h, info = mixed
     worst = 0.0
     for l in range(len(H) - 1):
         A, P = amgh.amgh_level_matrix(h, l, 0), amgh.amgh_level_matrix(h, l, 1)
         n, nc = A.shape[0], P.shape[1]
-        sm, mat = info["precision"][l], info["matrix_precision"][l]
+        sm = mat = info["precision"][l]
         vec = 0 if sm == 0 else 1                     # FP64 vectors only on FP64-smoother levels
         u_acc = U[0] if vec == 0 else U[1]
         u_vec = U[vec]
@@ -179,14 +169,14 @@ def test_single_pass_kernels_on_rounded_operands(amgh, mixed):
 
 def test_smoothing_steps_and_vcycle_against_fp64_oracle(amgh, mixed):
     import torch
-    case, prec, storage, p, H, h, info = mixed
+    case, prec, p, H, h, info = mixed
     tols = []
     for l in range(len(H) - 1):
         L = H[l]
         n = L["A"].shape[0]
         kappa = max(np.linalg.cond(L["A"][b][:, b].toarray()) for b in L["stars"] if len(b))
         steps = 2 * L["ncolours"] - 1
-        tol = 8 * (steps * kappa * U[info["precision"][l]] + U[info["matrix_precision"][l]])
+        tol = 8 * (steps * kappa + 1) * U[info["precision"][l]]
         tols.append(tol)
         x, f = W.uniform("probe", 10 + l, n), W.uniform("probe", 40 + l, n)
         y = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -208,7 +198,7 @@ def test_smoothing_steps_and_vcycle_against_fp64_oracle(amgh, mixed):
 
 def test_flexible_cg_reaches_fp64_tolerance(amgh, mixed):
     import torch
-    case, prec, storage, p, H, h, info = mixed
+    case, prec, p, H, h, info = mixed
     f = p["f"] if "f" in p else W.fields.rhs(p["ndof"], 0)
     x = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
     it, rel, ok = amgh.amgh_pcg_solve(h, cuda(f), x, 1e-8, 800)
