@@ -101,12 +101,25 @@ typedef struct {
                              of P^T and W, no fine residual.  -1: on the Galerkin levels (all
                              but the finest, whose W is about as large as A), where the
                              autotuner keeps it when it times faster than the residual pass plus
-                             the restriction (default); 0: never (W is not formed); 1: on every
-                             level                                                             */
+                             the restriction; 0: never, W is not formed (default: on the 64^3
+                             checkerboard forming W costs more setup time than the pass saves
+                             over a 63-iteration solve); 1: on every level                     */
 } amgh_params;
 
+/* Set up nsys independent systems (A[i], G[i]) with the same parameters (params may be NULL for
+ * the defaults; a stream in params is shared by all handles, NULL gives each its own), as
+ * amgh_setup would one by one: out[i] receives system i's handle.  Up to four setups run at
+ * once on their own host threads and streams, so one system's host graph steps overlap another's
+ * device work; the host's cores are split between them.  Launch choices not yet tuned in this
+ * process are timed while other setups run, so they may differ from a lone setup's (results then
+ * agree to rounding, not bitwise).  On any failure every handle is destroyed, out[] is NULL and
+ * the status of the first failing system is returned (amgh_last_error(NULL) names it).  The
+ * batch counterpart of Section 4's setup for the many-systems workload. */
+amgh_status amgh_batch_setup(int nsys, const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
+                             amgh_handle* out);
+
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict -1. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict 0. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,

@@ -46,7 +46,7 @@ class amgh_hier_info(ctypes.Structure):
 
 
 _LIB = None
-EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve",
+EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_batch_setup", "amgh_setup_host_structure", "amgh_vcycle", "amgh_pcg_solve",
            "amgh_batch_pcg_solve", "amgh_pcg_solve_noalloc", "amgh_pcg_solve_multi", "amgh_vcycle_multi",
            "amgh_amg_solve", "amgh_info",
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
@@ -76,6 +76,8 @@ def load():
     L.amgh_default_params.restype = None
     L.amgh_setup.argtypes = [ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_params), ctypes.POINTER(P)]
     L.amgh_setup_host_structure.argtypes = L.amgh_setup.argtypes
+    L.amgh_batch_setup.argtypes = [I, ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_csr), ctypes.POINTER(amgh_params),
+                                   ctypes.POINTER(P)]
     L.amgh_vcycle.argtypes = [P, P, P]
     L.amgh_pcg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
     L.amgh_amg_solve.argtypes = [P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
@@ -196,6 +198,21 @@ def amgh_setup(A, G, params=None, **kw):
     out = ctypes.c_void_p()
     _check(L.amgh_setup(ctypes.byref(a), ctypes.byref(g), ctypes.byref(p), ctypes.byref(out)))
     return Handle(out.value, a.nrows)
+
+
+def amgh_batch_setup(As, Gs, params=None, **kw):
+    """Set up many systems at once (see include/amgh.h); returns one Handle per system."""
+    L = load()
+    p = params if params is not None else amgh_default_params()
+    for k, v in kw.items():
+        setattr(p, k, v.ptr if isinstance(v, Mlp) else v)
+    keep = []
+    n = len(As)
+    arrA = (amgh_csr * n)(*[_csr(A, keep) for A in As])
+    arrG = (amgh_csr * n)(*[_csr(G, keep) for G in Gs])
+    out = (ctypes.c_void_p * n)()
+    _check(L.amgh_batch_setup(n, arrA, arrG, ctypes.byref(p), out))
+    return [Handle(out[i], arrA[i].nrows) for i in range(n)]
 
 
 def amgh_setup_host_structure(A, G, params=None, **kw):

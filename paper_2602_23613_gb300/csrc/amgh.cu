@@ -16,6 +16,7 @@
 #include <map>
 #include <tuple>
 #include <mutex>
+#include <condition_variable>
 #include <thread>
 #include <variant>
 
@@ -40,6 +41,56 @@ struct StatusError {
 
 static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Process-wide pool of the large host arrays of the level matrices (their columns and values):
+// a new setup takes the pages of a destroyed handle's arrays instead of faulting in fresh ones.
+// An array taken back keeps its size, so a later take of at most that size writes nothing.
+template <class T>
+class HostArrayPool {
+   public:
+    std::vector<T> take(size_t n) {
+        std::vector<T> v;
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            size_t best = free_.size();
+            for (size_t i = 0; i < free_.size(); ++i)
+                if (free_[i].size() >= n && (best == free_.size() || free_[i].size() < free_[best].size())) best = i;
+            if (best < free_.size()) {
+                v = std::move(free_[best]);
+                bytes_ -= v.capacity() * sizeof(T);
+                free_.erase(free_.begin() + (std::ptrdiff_t)best);
+            }
+        }
+        v.resize(n);
+        return v;
+    }
+    void give(std::vector<T>&& v) {
+        const size_t b = v.capacity() * sizeof(T);
+        if (b < (size_t(1) << 20)) return;
+        std::lock_guard<std::mutex> lock(mu_);
+        free_.push_back(std::move(v));
+        bytes_ += b;
+        while (bytes_ > kLimit && !free_.empty()) {   // the oldest arrays go first
+            bytes_ -= free_.front().capacity() * sizeof(T);
+            free_.erase(free_.begin());
+        }
+    }
+
+   private:
+    static constexpr size_t kLimit = size_t(4) << 30;
+    std::mutex mu_;
+    std::vector<std::vector<T>> free_;
+    size_t bytes_ = 0;
+};
+// never destroyed: a handle released during process exit may still hand its arrays back
+static HostArrayPool<int32_t>& pool_i32() {
+    static auto* p = new HostArrayPool<int32_t>();
+    return *p;
+}
+static HostArrayPool<double>& pool_f64() {
+    static auto* p = new HostArrayPool<double>();
+    return *p;
 }
 
 static void upload_csr(const HostCSR& h, DevCSR& d, cudaStream_t s, bool values) {
@@ -789,6 +840,10 @@ struct amgh_ctx {
         drop_solve_graph();
         eng.reset();
         meng.reset();
+        for (auto& L : hl) {   // the level matrices' host arrays go back to the pool
+            pool_i32().give(std::move(L.A.idx));
+            pool_f64().give(std::move(L.A.val));
+        }
         if (hscal) cudaFreeHost(hscal);
         if (own_stream && s) cudaStreamDestroy(s);
     }
@@ -925,8 +980,8 @@ static void set_smoother_mode(SmootherL<V>& sm, const LevelChoice& m) {
 
 template <class V>
 static void build_smoother(amgh_ctx* h, int l, int L, bool fused, int persist, bool staged, SmootherL<V>& sm,
-                           std::vector<int64_t>* cn, std::vector<int64_t>* ci, std::vector<int64_t>* cr) {
-    cudaStream_t s = h->s;
+                           std::vector<int64_t>* cn, std::vector<int64_t>* ci, std::vector<int64_t>* cr,
+                           cudaStream_t s) {
     const LevelHost& hl = h->hl[l];
     const StarLayout& st = hl.stars;
     StarPacking pk = pack_stars(st, L);
@@ -1040,13 +1095,14 @@ static bool cooperative_ok(amgh_ctx* h) {
 }
 
 // read and clear the flag a device-side barrier wait raises when it gives up
-static bool take_wait_flag(amgh_ctx* h) {
+static bool take_wait_flag(amgh_ctx* h, cudaStream_t s) {
     int flag = 0;
-    AMGH_CUDA(cudaMemcpyAsync(&flag, h->waitflag.p, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    AMGH_CUDA(cudaStreamSynchronize(h->s));
-    if (flag) h->waitflag.zero(h->s);
+    AMGH_CUDA(cudaMemcpyAsync(&flag, h->waitflag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    if (flag) h->waitflag.zero(s);
     return flag != 0;
 }
+static bool take_wait_flag(amgh_ctx* h) { return take_wait_flag(h, h->s); }
 
 // after a solve: a barrier wait that gave up invalidates the result; reset the barriers and report
 static void check_wait(amgh_ctx* h) {
@@ -1108,8 +1164,7 @@ static std::vector<int> lane_candidates(double avg_len, int n, int need_slots_fo
 }
 
 template <class V, class T, class VA>
-static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch) {
-    cudaStream_t s = h->s;
+static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch, cudaStream_t s) {
     const LevelHost& hl = h->hl[l];
     DevPhases ph;
     d.n = hl.A.nrows;
@@ -1224,7 +1279,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch
         const bool small = d.nnzA <= 3000000 && d.n <= 60000;
         for (int Lc : lane_candidates(avg, d.n, hl.stars.max_block)) {
             SmootherL<V> cand;
-            build_smoother<V>(h, l, Lc, false, 0, false, cand, nullptr, nullptr, nullptr);
+            build_smoother<V>(h, l, Lc, false, 0, false, cand, nullptr, nullptr, nullptr, s);
             int maxc = 1;
             for (int c = 0; c < cand.ncolours; ++c)
                 maxc = std::max(maxc, cand.colour_cta_begin[c + 1] - cand.colour_cta_begin[c]);
@@ -1359,7 +1414,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch
                     if (cudaStreamSynchronize(s) != cudaSuccess) throw;
                     continue;
                 }
-                if (take_wait_flag(h)) {   // a bounded wait gave up: never choose this mode
+                if (take_wait_flag(h, s)) {   // a bounded wait gave up: never choose this mode
                     cand.bar.zero(s);
                     continue;
                 }
@@ -1387,7 +1442,7 @@ static void build_level(amgh_ctx* h, int l, LevelX<V, T, VA>& d, LevelChoice& ch
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = ch;
     }
-    build_smoother<V>(h, l, ch.L_sm, false, 0, false, d.sm, &d.col_nnz, &d.col_inv, &d.col_rows);
+    build_smoother<V>(h, l, ch.L_sm, false, 0, false, d.sm, &d.col_nnz, &d.col_inv, &d.col_rows, s);
     // a mode whose shared-memory staging no longer fits (another device) falls back to per-colour
     // launches; the capacity queries also raise the kernels' shared-memory limits
     d.sm.persist = ch.persist;
@@ -1425,20 +1480,19 @@ struct TypeTag {
     using type = T;
 };
 
-// the engine level of a storage precision
-static void emplace_level(amgh_ctx* h, Engine* e, int l, LevelChoice& ch) {
+// the engine level of a storage precision, built on stream s
+static void emplace_level(amgh_ctx* h, Engine* e, int l, LevelChoice& ch, cudaStream_t s) {
     auto make = [&](auto tag) {
         using Lv = typename decltype(tag)::type;
         e->L.emplace_back(std::in_place_type<Lv>);
-        build_level(h, l, std::get<Lv>(e->L.back()), ch);
+        build_level(h, l, std::get<Lv>(e->L.back()), ch, s);
     };
     if (ch.prec == AMGH_F64) make(TypeTag<LevelX<double, double>>{});
     else if (ch.prec == AMGH_F32) make(TypeTag<LevelX<float, float>>{});
     else make(TypeTag<LevelX<bf16, float>>{});
 }
 
-static double level_kappa(amgh_ctx* h, int l) {
-    cudaStream_t s = h->s;
+static double level_kappa(amgh_ctx* h, int l, cudaStream_t s) {
     const StarLayout& st = h->hl[l].stars;
     DevArray<double> kap;
     kap.alloc(1);
@@ -1453,21 +1507,150 @@ static double level_kappa(amgh_ctx* h, int l) {
     return k;
 }
 
-static void build_engine(amgh_ctx* h, Engine* e) {
+// W = P^T A of level l for the fused residual + restriction (Eq. tl's coarse right-hand side by
+// associativity), by the same symbolic and numeric products as the Galerkin operator.  Tuned
+// (fuse_restrict -1): Galerkin levels only.  On the finest level W is about as large as A (0.95
+// of its entries on hex meshes), so the fused pass saves little there; on Galerkin levels W
+// holds 0.04-0.5 of A's entries.
+static bool wants_w(const amgh_params& prm, int l) { return prm.fuse_restrict > 0 || (prm.fuse_restrict < 0 && l > 0); }
+
+static void form_w(amgh_ctx* h, int l, cudaStream_t s) {
+    if (!wants_w(h->prm, l) || h->W64[l].nrows > 0) return;
+    const DevCSR& PT = h->PT64[l];
+    DevCSR Wd;
+    if (!spgemm_symbolic(PT, h->A64[l], Wd, h->symflag.p, s)) {
+        HostCSR hw = symbolic_product(h->hl[l].cz.PT, h->hl[l].A, 1);
+        upload_csr(hw, Wd, s, false);
+    }
+    launch_ap_numeric(PT, h->A64[l], Wd, s);
+    HostCSR wr;
+    wr.nrows = Wd.nrows;
+    wr.ncols = Wd.ncols;
+    wr.ptr.resize(Wd.nrows + 1);
+    AMGH_CUDA(cudaMemcpyAsync(wr.ptr.data(), Wd.ptr.p, sizeof(int32_t) * (Wd.nrows + 1), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
+    h->W64[l] = std::move(Wd);
+    h->Wrows[l] = std::move(wr);
+}
+
+// the tuning-cache key level l will look up for the storage precision prec
+static std::string level_key(amgh_ctx* h, int l, int prec) {
+    const size_t vb = prec == AMGH_F64 ? sizeof(double) : prec == AMGH_F32 ? sizeof(float) : sizeof(bf16);
+    return tune_key(h->hl[l], vb, vb, wants_w(h->prm, l) ? h->prm.fuse_restrict : 0);
+}
+
+// engine level l (its precision from the condition estimate, W, layouts, smoother), on stream s.
+// With only_cached, a level whose launch choices are not cached yet is left alone (its tuning
+// must time kernels without other work on the device): returns false then.
+static bool build_engine_level(amgh_ctx* h, Engine* e, int l, cudaStream_t s, bool only_cached) {
+    LevelChoice ch;
+    // the condition estimate only decides a reduced precision; an FP64 request skips it
+    ch.kappa = h->prm.precision == AMGH_F64 ? 0.0 : level_kappa(h, l, s);
+    ch.prec = level_precision(h->prm.precision, ch.kappa);
+    if (only_cached && tuning_enabled()) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (!g_tune_cache.count(level_key(h, l, ch.prec))) return false;
+    }
+    form_w(h, l, s);
+    if ((int)e->choice.size() <= l) e->choice.resize(l + 1);
+    e->choice[l] = ch;
+    emplace_level(h, e, l, e->choice[l], s);
+    return true;
+}
+
+// Builds the engine levels of a hierarchy while the setup loop coarsens further: level l is
+// handed over once its P, P^T and smoother stars are final (an event on the setup stream), and
+// built on the worker's own stream and host thread.  Only levels whose launch choices are cached
+// are built here; the first level that would tune stops the worker, and the setup builds it and
+// the rest afterwards, with nothing else running on the device.
+struct EngineWorker {
+    amgh_ctx* h;
+    Engine* e;
+    int dev = 0;
+    cudaStream_t ws = nullptr;
+    std::vector<cudaEvent_t> ev;
+    std::mutex mu;
+    std::condition_variable cv;
+    int ready = 0;        // levels [0, ready) may be built
+    bool closed = false;  // no further level will be handed over
+    int built = 0;        // levels [0, built) were built here
+    std::exception_ptr err;
+    std::thread th;
+
+    EngineWorker(amgh_ctx* hh, Engine* ee, int max_levels) : h(hh), e(ee), ev(max_levels, nullptr) {
+        AMGH_CUDA(cudaGetDevice(&dev));
+        AMGH_CUDA(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+        for (auto& x : ev) AMGH_CUDA(cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        th = std::thread([this] { run(); });
+    }
+    void run() {
+        try {
+            AMGH_CUDA(cudaSetDevice(dev));
+            for (int l = 0;; ++l) {
+                {
+                    std::unique_lock<std::mutex> lock(mu);
+                    cv.wait(lock, [&] { return ready > l || closed; });
+                    if (ready <= l) return;
+                }
+                AMGH_CUDA(cudaStreamWaitEvent(ws, ev[l], 0));
+                if (!build_engine_level(h, e, l, ws, true)) return;
+                AMGH_CUDA(cudaStreamSynchronize(ws));
+                built = l + 1;
+            }
+        } catch (...) {
+            err = std::current_exception();
+        }
+    }
+    // level l's inputs are enqueued on the setup stream s
+    void hand_over(int l, cudaStream_t s) {
+        AMGH_CUDA(cudaEventRecord(ev[l], s));
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            ready = l + 1;
+        }
+        cv.notify_one();
+    }
+    // waits for the worker; returns the number of levels it built
+    int finish() {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            closed = true;
+        }
+        cv.notify_one();
+        if (th.joinable()) th.join();
+        if (err) std::rethrow_exception(err);
+        return built;
+    }
+    ~EngineWorker() {
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            closed = true;
+        }
+        cv.notify_one();
+        if (th.joinable()) th.join();
+        if (ws) {
+            cudaStreamSynchronize(ws);
+            cudaStreamDestroy(ws);
+        }
+        for (auto x : ev)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+static void build_engine(amgh_ctx* h, Engine* e, int from = 0) {
     cudaStream_t s = h->s;
     const int nlev = (int)h->hl.size();
     e->nlev = nlev;
-    e->L.clear();
-    e->choice.assign(nlev, LevelChoice());
-    DevPhases ph;
-    for (int l = 0; l + 1 < nlev; ++l) {
-        if (l > 0) ph.mark(s, "engine level", l - 1);
-        LevelChoice& ch = e->choice[l];
-        // the condition estimate only decides a reduced precision; an FP64 request skips it
-        ch.kappa = h->prm.precision == AMGH_F64 ? 0.0 : level_kappa(h, l);
-        ch.prec = level_precision(h->prm.precision, ch.kappa);
-        emplace_level(h, e, l, ch);
+    if (from == 0) {
+        e->L.clear();
+        e->choice.clear();
     }
+    DevPhases ph;
+    for (int l = from; l + 1 < nlev; ++l) {
+        if (l > from) ph.mark(s, "engine level", l - 1);
+        build_engine_level(h, e, l, s, false);
+    }
+    e->choice.resize(nlev);
     // coarsest level: dense inverse, precision from its 1-norm condition estimate
     const HostCSR& Ac = h->hl.back().A;
     const int nL = Ac.nrows;
@@ -1529,8 +1712,8 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
     h.ncols = (int)M->ncols;
     const double t0 = now_ms();
     h.ptr.resize(h.nrows + 1);
-    h.idx.resize(M->nnz);
-    h.val.resize(M->nnz);
+    h.idx = pool_i32().take((size_t)M->nnz);
+    h.val = pool_f64().take((size_t)M->nnz);
     const double t1 = now_ms();
     if (!M->on_device) {
         std::memcpy(h.ptr.data(), M->row_ptr, sizeof(int32_t) * (h.nrows + 1));
@@ -1645,6 +1828,22 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         AMGH_CUDA(cudaMemcpyAsync(dA.val.p, Ain->val, sizeof(double) * dA.nnz, cudaMemcpyDeviceToDevice, s));
     } else {
         upload_csr(A, dA, s, true);
+    }
+    // level arrays keep their addresses while the engine worker reads finished levels
+    const size_t cap = (size_t)prm.max_levels + 1;
+    h->hl.reserve(cap);
+    h->A64.reserve(cap);
+    h->P64.reserve(cap);
+    h->PT64.reserve(cap);
+    h->W64.reserve(cap);
+    h->Wrows.reserve(cap);
+    auto* e = new Engine();
+    h->eng.reset(e);
+    e->prof = &h->prof;
+    std::unique_ptr<EngineWorker> worker;
+    {
+        const char* ov = std::getenv("AMGH_ENGINE_OVERLAP");
+        if (!(ov && std::string(ov) == "0")) worker.reset(new EngineWorker(h, e, (int)cap));
     }
     for (int l = 0;; ++l) {
         h->hl.emplace_back();
@@ -1778,37 +1977,20 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             upload_csr(hc, Ac, s, false);
         }
         launch_ac_numeric(PT, AP, Ac, s);
-        // W = P^T A for the fused residual + restriction (Eq. tl's coarse right-hand side by
-        // associativity); same symbolic and numeric products as the Galerkin one
+        // placeholders of W = P^T A, formed with the level's engine (form_w)
         h->W64.emplace_back();
         h->Wrows.emplace_back();
-        // tuned (-1): Galerkin levels only.  On the finest level W is about as large as A
-        // (0.95 of its entries on hex meshes), so the fused pass saves little there while forming
-        // and tuning W costs more than that over a solve; on Galerkin levels W holds 0.04-0.5 of
-        // A's entries.
-        if (prm.fuse_restrict > 0 || (prm.fuse_restrict < 0 && l > 0)) {
-            DevCSR& Wd = h->W64.back();
-            if (!spgemm_symbolic(PT, h->A64[l], Wd, h->symflag.p, s)) {
-                HostCSR hw = symbolic_product(cz.PT, cur.A, nthreads);
-                upload_csr(hw, Wd, s, false);
-            }
-            launch_ap_numeric(PT, h->A64[l], Wd, s);
-            HostCSR& wr = h->Wrows.back();
-            wr.nrows = Wd.nrows;
-            wr.ncols = Wd.ncols;
-            wr.ptr.resize(Wd.nrows + 1);
-            AMGH_CUDA(cudaMemcpyAsync(wr.ptr.data(), Wd.ptr.p, sizeof(int32_t) * (Wd.nrows + 1), cudaMemcpyDeviceToHost, s));
-        }
         HostCSR An;   // the next level's matrix, on the host for its graph steps
         An.nrows = Ac.nrows;
         An.ncols = Ac.ncols;
         An.ptr.resize(Ac.nrows + 1);
-        An.idx.resize(Ac.nnz);
-        An.val.resize(Ac.nnz);
+        An.idx = pool_i32().take((size_t)Ac.nnz);
+        An.val = pool_f64().take((size_t)Ac.nnz);
         AMGH_CUDA(cudaMemcpyAsync(An.ptr.data(), Ac.ptr.p, sizeof(int32_t) * (Ac.nrows + 1), cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaMemcpyAsync(An.idx.data(), Ac.idx.p, sizeof(int32_t) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaStreamSynchronize(s));
+        if (worker) worker->hand_over(l, s);   // level l's P, P^T and stars are final
         h->dev_ms += std::max(0.0, now_ms() - t0 - t_stars);
         ph.mark(s, "Galerkin + download", l);
         A = std::move(An);
@@ -1827,10 +2009,10 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         check_flag(h, "the coarsest factorisation");
     }
     ph.mark(s, "coarsest inverse");
+    const int built = worker ? worker->finish() : 0;
+    worker.reset();
+    ph.mark(s, "engine levels built beside the setup loop");
     {
-        auto* e = new Engine();
-        h->eng.reset(e);
-        e->prof = &h->prof;
         // the sub-cycle below the first small level is linear in its right-hand side: apply it as
         // one dense operator, computed column block by column block with the multi-RHS V-cycle
         const int nlev = (int)h->hl.size();
@@ -1849,10 +2031,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         bool overlap = t > 0 && prm.precision == AMGH_F64;
         if (overlap && tuning_enabled()) {
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            for (int l = 0; l + 1 < nlev && overlap; ++l)
-                overlap = g_tune_cache.count(tune_key(h->hl[l], sizeof(double), sizeof(double),
-                                                      l < (int)h->W64.size() && h->W64[l].nrows > 0
-                                                          ? prm.fuse_restrict : 0)) > 0;
+            for (int l = built; l + 1 < nlev && overlap; ++l) overlap = g_tune_cache.count(level_key(h, l, AMGH_F64)) > 0;
         }
         if (overlap) {
             int dev = 0;
@@ -1870,7 +2049,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             });
             std::exception_ptr engine_error;
             try {
-                build_engine(h, e);
+                build_engine(h, e, built);
             } catch (...) {
                 engine_error = std::current_exception();
             }
@@ -1880,7 +2059,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             if (tail_error) std::rethrow_exception(tail_error);
             ph.mark(s, "V-cycle engine + dense tail (concurrent)");
         } else {
-            build_engine(h, e);
+            build_engine(h, e, built);
             ph.mark(s, "V-cycle engine");
             if (t > 0) build_tail(s);
         }
@@ -2514,7 +2693,67 @@ void amgh_default_params(amgh_params* p) {
     p->dense_tail = 8192;
     p->mlp = nullptr;
     p->rho_ref = 0.0;
-    p->fuse_restrict = -1;
+    p->fuse_restrict = 0;
+}
+
+amgh_status amgh_batch_setup(int nsys, const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
+                             amgh_handle* out) {
+    if (nsys < 1 || !A || !G || !out) {
+        g_setup_error = "batch setup needs nsys >= 1 and non-null arrays";
+        return AMGH_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < nsys; ++i) out[i] = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        g_setup_error = "no usable current CUDA device";
+        return AMGH_ERR_CUDA;
+    }
+    // a few setups at a time, each on its own host thread and stream; their host graph steps
+    // split the host's cores between them
+    const int conc = std::min(nsys, 4);
+    int cores = 1;
+#ifdef _OPENMP
+    cores = omp_get_max_threads();
+#endif
+    const int per = std::max(1, cores / conc);
+    std::atomic<int> next{0};
+    std::vector<amgh_status> st(nsys, AMGH_OK);
+    std::vector<std::string> msg(nsys);
+    auto work = [&] {
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            cudaGetLastError();
+            for (int i; (i = next++) < nsys;) {
+                st[i] = AMGH_ERR_CUDA;
+                msg[i] = "cudaSetDevice failed on a batch thread";
+            }
+            return;
+        }
+#ifdef _OPENMP
+        omp_set_num_threads(per);
+#endif
+        for (int i; (i = next++) < nsys;) {
+            st[i] = amgh_setup(&A[i], &G[i], params, &out[i]);
+            if (st[i] != AMGH_OK) msg[i] = g_setup_error;
+        }
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int t = 1; t < conc; ++t) pool.emplace_back(work);
+    } catch (...) {
+    }
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < nsys; ++i)
+        if (st[i] != AMGH_OK) {
+            for (int j = 0; j < nsys; ++j) {
+                amgh_destroy(out[j]);
+                out[j] = nullptr;
+            }
+            g_setup_error = "system " + std::to_string(i) + ": " + msg[i];
+            return st[i];
+        }
+    return AMGH_OK;
 }
 
 amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* params, amgh_handle* out) {

@@ -676,53 +676,69 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
             if (comp[r] >= 0) cmem[cur[comp[r]]++] = r;   // ascending within a component
     }
     clk.mark("G_c + components");
-    std::vector<std::vector<int32_t>> patches(nc);
-#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
-    for (int c = 0; c < nc; ++c) {
-        const auto& e = out.edges[c];
-        std::vector<int32_t> seeds;
-        for (int32_t d : {e.d1, e.d2})
-            for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t)
-                if (!ext[A.idx[t]]) seeds.push_back(A.idx[t]);
-        std::sort(seeds.begin(), seeds.end());
-        seeds.erase(std::unique(seeds.begin(), seeds.end()), seeds.end());
-        std::vector<int32_t> comps;
-        for (int32_t s : seeds) comps.push_back(comp[s]);
-        std::sort(comps.begin(), comps.end());
-        comps.erase(std::unique(comps.begin(), comps.end()), comps.end());
-        int64_t tot = 0;
-        for (int32_t q : comps) tot += csize[q];
-        auto& pt = patches[c];
-        if (tot <= prm.p_max) {
-            for (int32_t q : comps) pt.insert(pt.end(), cmem.begin() + cptr[q], cmem.begin() + cptr[q + 1]);
-        } else {
-            std::vector<int32_t> order = seeds, level = seeds;
-            std::vector<int32_t> seen = seeds;   // sorted
-            for (int r = 1; r < prm.ring && (int)order.size() < prm.p_max; ++r) {
-                std::vector<int32_t> nxt;
-                for (int32_t d : level)
-                    for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t) {
-                        int32_t x = A.idx[t];
-                        if (!ext[x] && !std::binary_search(seen.begin(), seen.end(), x)) nxt.push_back(x);
-                    }
-                std::sort(nxt.begin(), nxt.end());
-                nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
-                order.insert(order.end(), nxt.begin(), nxt.end());
-                std::vector<int32_t> merged;
-                std::merge(seen.begin(), seen.end(), nxt.begin(), nxt.end(), std::back_inserter(merged));
-                seen.swap(merged);
-                level.swap(nxt);
+    // each thread keeps its scratch lists across coarse edges and appends the patches it builds
+    // to its own flat buffer; a patch is found through (thread, offset, length)
+    std::vector<std::vector<int32_t>> pbuf(nthreads);
+    std::vector<int32_t> pthread(nc), poff(nc), plen(nc);
+#pragma omp parallel num_threads(nthreads)
+    {
+        const int tid = thread_id();
+        auto& buf = pbuf[tid];
+        std::vector<int32_t> seeds, comps, order, level, seen, nxt, merged;
+#pragma omp for schedule(dynamic, 64)
+        for (int c = 0; c < nc; ++c) {
+            const auto& e = out.edges[c];
+            seeds.clear();
+            for (int32_t d : {e.d1, e.d2})
+                for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t)
+                    if (!ext[A.idx[t]]) seeds.push_back(A.idx[t]);
+            std::sort(seeds.begin(), seeds.end());
+            seeds.erase(std::unique(seeds.begin(), seeds.end()), seeds.end());
+            comps.clear();
+            for (int32_t sd : seeds) comps.push_back(comp[sd]);
+            std::sort(comps.begin(), comps.end());
+            comps.erase(std::unique(comps.begin(), comps.end()), comps.end());
+            int64_t tot = 0;
+            for (int32_t q : comps) tot += csize[q];
+            const size_t b = buf.size();
+            if (tot <= prm.p_max) {
+                for (int32_t q : comps) buf.insert(buf.end(), cmem.begin() + cptr[q], cmem.begin() + cptr[q + 1]);
+            } else {
+                order = seeds;
+                level = seeds;
+                seen = seeds;   // sorted
+                for (int r = 1; r < prm.ring && (int)order.size() < prm.p_max; ++r) {
+                    nxt.clear();
+                    for (int32_t d : level)
+                        for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t) {
+                            int32_t x = A.idx[t];
+                            if (!ext[x] && !std::binary_search(seen.begin(), seen.end(), x)) nxt.push_back(x);
+                        }
+                    std::sort(nxt.begin(), nxt.end());
+                    nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
+                    order.insert(order.end(), nxt.begin(), nxt.end());
+                    merged.clear();
+                    std::merge(seen.begin(), seen.end(), nxt.begin(), nxt.end(), std::back_inserter(merged));
+                    seen.swap(merged);
+                    level.swap(nxt);
+                }
+                if ((int)order.size() > prm.p_max) order.resize(prm.p_max);
+                buf.insert(buf.end(), order.begin(), order.end());
             }
-            if ((int)order.size() > prm.p_max) order.resize(prm.p_max);
-            pt = order;
+            std::sort(buf.begin() + (std::ptrdiff_t)b, buf.end());
+            pthread[c] = tid;
+            poff[c] = (int32_t)b;
+            plen[c] = (int32_t)(buf.size() - b);
         }
-        std::sort(pt.begin(), pt.end());
     }
     out.patch_ptr.assign(nc + 1, 0);
-    for (int c = 0; c < nc; ++c) out.patch_ptr[c + 1] = out.patch_ptr[c] + (int32_t)patches[c].size();
+    for (int c = 0; c < nc; ++c) out.patch_ptr[c + 1] = out.patch_ptr[c] + plen[c];
     out.patch_idx.resize(out.patch_ptr[nc]);
-    for (int c = 0; c < nc; ++c)
-        std::copy(patches[c].begin(), patches[c].end(), out.patch_idx.begin() + out.patch_ptr[c]);
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int c = 0; c < nc; ++c) {
+        const int32_t* src = pbuf[pthread[c]].data() + poff[c];
+        std::copy(src, src + plen[c], out.patch_idx.begin() + out.patch_ptr[c]);
+    }
 
     clk.mark("patches");
     // ---- patterns of P^T (row c: the patch and the two exterior DoFs, ascending) and of P (its
@@ -846,36 +862,48 @@ std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
     for (int j = 0; j < ns; ++j) L.max_block = std::max(L.max_block, GT.ptr[j + 1] - GT.ptr[j]);
     if (L.max_block > 32) return "smoother star of " + std::to_string(L.max_block) + " DoFs exceeds 32";
     // conflict lists in parallel (star j ~ j' when an entry of A couples them), then the greedy
-    // pass in ascending j, which is inherently sequential
-    std::vector<std::vector<int32_t>> nbr(ns);
+    // pass in ascending j, which is inherently sequential.  Each thread takes contiguous blocks of
+    // stars and appends their (lower) conflict lists to its own flat buffer; a star's list is
+    // found through (thread, offset, length), so no per-star allocation is made.
     int nthreads = 1;
 #ifdef _OPENMP
     nthreads = std::max(1, std::min(omp_get_max_threads(), 32));
 #endif
-    std::vector<std::vector<int32_t>> stamps(nthreads, std::vector<int32_t>(ns, -1));
-#pragma omp parallel for schedule(dynamic, 512) num_threads(nthreads)
-    for (int j = 0; j < ns; ++j) {
-        auto& stamp = stamps[thread_id()];
-        auto& v = nbr[j];
-        for (int32_t t = GT.ptr[j]; t < GT.ptr[j + 1]; ++t) {
-            int32_t e = GT.idx[t];
-            for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
-                int32_t f = A.idx[q];
-                for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
-                    int32_t jj = G.idx[u];
-                    if (jj < j && stamp[jj] != j) { stamp[jj] = j; v.push_back(jj); }
+    std::vector<std::vector<int32_t>> stamps(nthreads), lists(nthreads);
+    std::vector<int32_t> lthread(ns), loff(ns), llen(ns);
+#pragma omp parallel num_threads(nthreads)
+    {
+        const int tid = thread_id();
+        auto& stamp = stamps[tid];
+        stamp.assign(ns, -1);
+        auto& buf = lists[tid];
+#pragma omp for schedule(dynamic, 512)
+        for (int j = 0; j < ns; ++j) {
+            const size_t b = buf.size();
+            for (int32_t t = GT.ptr[j]; t < GT.ptr[j + 1]; ++t) {
+                int32_t e = GT.idx[t];
+                for (int32_t q = A.ptr[e]; q < A.ptr[e + 1]; ++q) {
+                    int32_t f = A.idx[q];
+                    for (int32_t u = G.ptr[f]; u < G.ptr[f + 1]; ++u) {
+                        int32_t jj = G.idx[u];
+                        if (jj < j && stamp[jj] != j) { stamp[jj] = j; buf.push_back(jj); }
+                    }
                 }
             }
+            lthread[j] = tid;
+            loff[j] = (int32_t)b;
+            llen[j] = (int32_t)(buf.size() - b);
         }
     }
     L.colour.assign(ns, -1);
-    std::vector<int32_t> mark;
+    std::vector<int32_t> mark;   // mark[c] == j: colour c is taken by a neighbour of star j
     int ncol = 0;
     for (int j = 0; j < ns; ++j) {
-        mark.assign(ncol + 1, -1);
-        for (int32_t jj : nbr[j]) mark[L.colour[jj]] = j;
+        if ((int)mark.size() < ncol + 1) mark.resize(ncol + 1, -1);
+        const int32_t* nb = lists[lthread[j]].data() + loff[j];
+        for (int32_t q = 0; q < llen[j]; ++q) mark[L.colour[nb[q]]] = j;
         int c = 0;
-        while (mark[c] == j) ++c;
+        while (c < ncol && mark[c] == j) ++c;
         L.colour[j] = c;
         ncol = std::max(ncol, c + 1);
     }

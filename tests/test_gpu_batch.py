@@ -76,3 +76,41 @@ def test_batch_of_uneven_systems_in_one_launch(amgh, prec):
             _, ito, _ = O.pcg(H, p["f"], tol=1e-8)
             assert abs(ito - its[i]) <= 1, (i, its[i], ito)
     print("batch %s sizes %s iterations %s" % (prec, [p["ndof"] for p in probs], its))
+
+
+def test_batch_setup_equals_one_by_one(amgh):
+    """amgh_batch_setup builds the same hierarchies as amgh_setup one by one: same levels, same
+    structure, and (launch choices cached by the one-by-one setups first) bitwise the same PCG
+    solves; the wall times of both are printed."""
+    import time
+    import torch
+    probs = _batch_problems(8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs1 = [amgh.amgh_setup(p["A"], p["G"]) for p in probs]
+    t1 = time.perf_counter()
+    hs2 = amgh.amgh_batch_setup([p["A"] for p in probs], [p["G"] for p in probs])
+    t2 = time.perf_counter()
+    print("batch setup of %d systems: one by one %.1f ms, batch %.1f ms" % (len(probs), 1e3 * (t1 - t0),
+                                                                           1e3 * (t2 - t1)))
+    for i, (p, a, b) in enumerate(zip(probs, hs1, hs2)):
+        ia, ib = amgh.amgh_info(a), amgh.amgh_info(b)
+        assert ia["n"] == ib["n"] and ia["nnz"] == ib["nnz"] and ia["fused"] == ib["fused"], i
+        sa, sb = amgh.amgh_level_structure(a, 0), amgh.amgh_level_structure(b, 0)
+        assert np.array_equal(sa["edges"], sb["edges"]) and np.array_equal(sa["colour"], sb["colour"])
+        f = cuda(p["f"])
+        xa, xb = torch.zeros_like(f), torch.zeros_like(f)
+        ita, _, oka = amgh.amgh_pcg_solve(a, f, xa, 1e-8, 300)
+        itb, _, okb = amgh.amgh_pcg_solve(b, f, xb, 1e-8, 300)
+        assert oka and okb and ita == itb and torch.equal(xa, xb), i
+
+
+def test_batch_setup_reports_the_failing_system(amgh):
+    import scipy.sparse as sp
+    probs = _batch_problems(3)
+    bad = sp.csr_matrix(probs[1]["G"], copy=True)
+    bad.data[0] = 3.0
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_batch_setup([p["A"] for p in probs], [probs[0]["G"], bad, probs[2]["G"]])
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+    assert "system 1" in str(e.value)
