@@ -43,56 +43,6 @@ static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Process-wide pool of the large host arrays of the level matrices (their columns and values):
-// a new setup takes the pages of a destroyed handle's arrays instead of faulting in fresh ones.
-// An array taken back keeps its size, so a later take of at most that size writes nothing.
-template <class T>
-class HostArrayPool {
-   public:
-    std::vector<T> take(size_t n) {
-        std::vector<T> v;
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            size_t best = free_.size();
-            for (size_t i = 0; i < free_.size(); ++i)
-                if (free_[i].size() >= n && (best == free_.size() || free_[i].size() < free_[best].size())) best = i;
-            if (best < free_.size()) {
-                v = std::move(free_[best]);
-                bytes_ -= v.capacity() * sizeof(T);
-                free_.erase(free_.begin() + (std::ptrdiff_t)best);
-            }
-        }
-        v.resize(n);
-        return v;
-    }
-    void give(std::vector<T>&& v) {
-        const size_t b = v.capacity() * sizeof(T);
-        if (b < (size_t(1) << 20)) return;
-        std::lock_guard<std::mutex> lock(mu_);
-        free_.push_back(std::move(v));
-        bytes_ += b;
-        while (bytes_ > kLimit && !free_.empty()) {   // the oldest arrays go first
-            bytes_ -= free_.front().capacity() * sizeof(T);
-            free_.erase(free_.begin());
-        }
-    }
-
-   private:
-    static constexpr size_t kLimit = size_t(4) << 30;
-    std::mutex mu_;
-    std::vector<std::vector<T>> free_;
-    size_t bytes_ = 0;
-};
-// never destroyed: a handle released during process exit may still hand its arrays back
-static HostArrayPool<int32_t>& pool_i32() {
-    static auto* p = new HostArrayPool<int32_t>();
-    return *p;
-}
-static HostArrayPool<double>& pool_f64() {
-    static auto* p = new HostArrayPool<double>();
-    return *p;
-}
-
 static void upload_csr(const HostCSR& h, DevCSR& d, cudaStream_t s, bool values) {
     d.nrows = h.nrows;
     d.ncols = h.ncols;
@@ -840,10 +790,6 @@ struct amgh_ctx {
         drop_solve_graph();
         eng.reset();
         meng.reset();
-        for (auto& L : hl) {   // the level matrices' host arrays go back to the pool
-            pool_i32().give(std::move(L.A.idx));
-            pool_f64().give(std::move(L.A.val));
-        }
         if (hscal) cudaFreeHost(hscal);
         if (own_stream && s) cudaStreamDestroy(s);
     }
@@ -1712,8 +1658,8 @@ static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false
     h.ncols = (int)M->ncols;
     const double t0 = now_ms();
     h.ptr.resize(h.nrows + 1);
-    h.idx = pool_i32().take((size_t)M->nnz);
-    h.val = pool_f64().take((size_t)M->nnz);
+    h.idx.resize(M->nnz);
+    h.val.resize(M->nnz);
     const double t1 = now_ms();
     if (!M->on_device) {
         std::memcpy(h.ptr.data(), M->row_ptr, sizeof(int32_t) * (h.nrows + 1));
@@ -1984,8 +1930,8 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         An.nrows = Ac.nrows;
         An.ncols = Ac.ncols;
         An.ptr.resize(Ac.nrows + 1);
-        An.idx = pool_i32().take((size_t)Ac.nnz);
-        An.val = pool_f64().take((size_t)Ac.nnz);
+        An.idx.resize(Ac.nnz);
+        An.val.resize(Ac.nnz);
         AMGH_CUDA(cudaMemcpyAsync(An.ptr.data(), Ac.ptr.p, sizeof(int32_t) * (Ac.nrows + 1), cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaMemcpyAsync(An.idx.data(), Ac.idx.p, sizeof(int32_t) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * Ac.nnz, cudaMemcpyDeviceToHost, s));
