@@ -175,9 +175,10 @@ def level_profile(amgh, h, A0, G0, hbm_peak, fp64_peak, nvc=10):
     return out
 
 
-def time_variant(amgh, prob, dev_inputs, precision, steps, warmup):
-    """Setup + flexible CG to 1e-8 on a workload with a requested storage precision: wall time
-    of whole steps (synchronised) after warm-up ones, with the level storages the handle chose."""
+def time_variant(amgh, prob, dev_inputs, precision, steps, warmup, **kw):
+    """Setup + (flexible) CG to 1e-8 on a workload with a requested storage precision (and other
+    setup parameters): wall time of whole steps (synchronised) after warm-up ones, with the level
+    storages the handle chose."""
     import numpy as np
     import torch
     A, f = prob["A"], prob["f"]
@@ -188,7 +189,7 @@ def time_variant(amgh, prob, dev_inputs, precision, steps, warmup):
     for i in range(warmup + steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        h = amgh.amgh_setup(Ad, Gd, precision=code)
+        h = amgh.amgh_setup(Ad, Gd, precision=code, **kw)
         t1 = time.perf_counter()
         xd.zero_()
         it, rel, ok = amgh.amgh_pcg_solve(h, fd, xd, 1e-8, 5000)
@@ -207,7 +208,8 @@ def time_variant(amgh, prob, dev_inputs, precision, steps, warmup):
             "solve_s": statistics.mean(r[2] for r in res), "pcg_iters": res[-1][3], "relres": res[-1][4],
             "converged": res[-1][5], "true_relres": true_rel,
             "level_precision": [names[q] for q in info["precision"]],
-            "block_kappa": info["block_kappa"], "levels": info["n"], "steps": steps, "warmup": warmup}
+            "block_kappa": info["block_kappa"], "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
+            "steps": steps, "warmup": warmup}
 
 
 def last_colour(res):
@@ -544,6 +546,21 @@ def run_gpu(args, rank, world, local_rank):
     hl = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
     levels = level_profile(amgh, hl, A, G, peak, fp64_peak)
     amgh.amgh_destroy(hl)
+    # the paper's three interpolations on this workload (Sec. 5's comparison): the algebraic one
+    # timed above ("Alg"), the refinement-based one ("Ref") and geometric Nedelec ("Geo")
+    comparison = None
+    if world == 1 and W.CONFIGS[args.workload]["n"] % 4 == 0:
+        mesh_n = W.CONFIGS[args.workload]["n"]
+        din = (Ad, Gd, fd)
+        comparison = {}
+        for label, kw in (("Ref", dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=mesh_n)),
+                          ("Geo", dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=mesh_n,
+                                       interp=amgh.AMGH_INTERP_GEOMETRIC))):
+            v = time_variant(amgh, prob, din, args.precision, 3, 1, **kw)
+            comparison[label] = {k: v[k] for k in ("s_per_step", "setup_s", "solve_s", "pcg_iters", "relres",
+                                                   "converged", "levels", "op_complexity")}
+        comparison["Alg"] = {"s_per_step": t_step, "pcg_iters": last["iters"], "levels": last["info"]["n"],
+                             "op_complexity": round(last["info"]["op_complexity"], 4)}
     variants = None
     if args.variants != "none" and world == 1:
         vp = W.make_config(args.variants)
@@ -589,6 +606,8 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": int(gpu_launches), "clocks": clk,
     }
     line["roofline"]["levels"] = levels
+    if comparison is not None:
+        line["comparison"] = comparison
     if variants is not None:
         line["variants"] = variants
     print(json.dumps(line), flush=True)

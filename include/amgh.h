@@ -73,7 +73,20 @@ enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
  * V-cycles on A x = 0 (x0 ~ U(-1,1), SplitMix64 stream 8, seed 0) and falls back to the exact
  * local solves when rho exceeds 1.1 times the exact solves' factor (params.rho_ref, or measured
  * on an exact setup); amgh_info reports which interpolation was kept. */
-enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1 };
+enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1, AMGH_INTERP_GEOMETRIC = 2 };
+
+/* coarse variables: ALGEBRAIC (Section 4: Alg. 1-3 on the nodal dual operator, the default) or
+ * REFINEMENT (Section 3, "Ref"): A and G must be the lowest-order Nedelec system of the structured
+ * hex mesh of the unit cube with params.mesh_n intervals per side (interior edges numbered x, y,
+ * z, each lexicographic by start node with the x index fastest, oriented +axis; interior nodes
+ * lexicographic; boundary edges and nodes eliminated), and each coarse edge of the (mesh_n/2)^3
+ * mesh pairs its two fine halves with signs (+1, +1); the coarse edges take the coarse mesh's own
+ * numbering, so every coarse level is again such a mesh, halved while mesh_n stays even.  With
+ * REFINEMENT, interp may also be AMGH_INTERP_GEOMETRIC ("Geo", the comparison of Section 5): the
+ * geometric Nedelec interpolation of the coarse mesh, scaled so that its rows on the halves are
+ * R^T (a fine edge parallel to its coarse edge one fine step across takes 1/2, two steps 1/4),
+ * in place of the local harmonic extensions. */
+enum { AMGH_COARSEN_ALGEBRAIC = 0, AMGH_COARSEN_REFINEMENT = 1 };
 
 typedef struct {
     int max_levels;       /* at most this many levels, finest included (Section 5: 20)          */
@@ -82,7 +95,7 @@ typedef struct {
                              keeps FP64 unless kappa * u <= 1/4 for the largest 1-norm condition
                              estimate kappa of its smoother blocks and the unit roundoff u of the
                              reduced format (BF16 falls back to FP32 first)                     */
-    int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED                            */
+    int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED | AMGH_INTERP_GEOMETRIC     */
     int ring;             /* rings of interior A-neighbours in a truncated patch (>= 1)        */
     int p_max;            /* largest patch of one local harmonic extension (<= 256)            */
     double theta;         /* strength-of-connection threshold of the nodal C/F split (0.25)    */
@@ -104,6 +117,8 @@ typedef struct {
                              the restriction; 0: never, W is not formed (default: on the 64^3
                              checkerboard forming W costs more setup time than the pass saves
                              over a 63-iteration solve); 1: on every level                     */
+    int coarsening;       /* AMGH_COARSEN_ALGEBRAIC (default) | AMGH_COARSEN_REFINEMENT        */
+    int mesh_n;           /* hex mesh intervals per side, for AMGH_COARSEN_REFINEMENT          */
 } amgh_params;
 
 /* Set up nsys independent systems (A[i], G[i]) with the same parameters (params may be NULL for
@@ -119,7 +134,8 @@ amgh_status amgh_batch_setup(int nsys, const amgh_csr* A, const amgh_csr* G, con
                              amgh_handle* out);
 
 /* Fill *p with the defaults: max_levels 20, coarse_size 100, F64, LOCAL, ring 1, p_max 128,
- * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict 0. */
+ * theta 0.25, stall_ratio 0.9, stream NULL, dense_tail 8192, fuse_restrict 0, coarsening ALGEBRAIC,
+ * mesh_n 0. */
 void amgh_default_params(amgh_params* p);
 
 /* Build the hierarchy for A (n x n, SPD, symmetric pattern) and the discrete gradient G (n x m,

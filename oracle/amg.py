@@ -479,18 +479,147 @@ def smooth_post(L, f, x):
 # ----------------------------------------------------------------------------------------------
 
 
-def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta=0.25, pmap=map, nchunks=1):
-    """One application of the two-level setup of Sec. 4: augment G (Alg. 1), split the nodal dual
-    operator (Alg. 2), pair edges (Alg. 3), interpolate (Eq. sparseP), form G_c (Eq. Gc)."""
+# ----------------------------------------------------------------------------------------------
+# Sec. 3 and Sec. 5: refinement-based coarse variables ("Ref") and geometric Nedelec
+# interpolation ("Geo") on the structured n^3 hex mesh
+# ----------------------------------------------------------------------------------------------
+
+
+def hex_numbering(n):
+    """Interior edge and node ids of the n^3 hex mesh of the unit cube, as the inputs number them:
+    x-edges, then y, then z, each lexicographic by start node (i fastest), oriented +axis; edges
+    lying in a boundary face and boundary nodes are eliminated (id -1).  Returns (edge_id(d, i, j,
+    k), node_id(i, j, k)) for integer node coordinates 0..n."""
+    m = n - 1
+    nx = n * m * m
+
+    def edge_id(d, i, j, k):
+        if d == 0:
+            ok = 0 <= i < n and 1 <= j <= m and 1 <= k <= m
+            return i + n * ((j - 1) + m * (k - 1)) if ok else -1
+        if d == 1:
+            ok = 1 <= i <= m and 0 <= j < n and 1 <= k <= m
+            return nx + (i - 1) + m * (j + n * (k - 1)) if ok else -1
+        ok = 1 <= i <= m and 1 <= j <= m and 0 <= k < n
+        return 2 * nx + (i - 1) + m * ((j - 1) + m * k) if ok else -1
+
+    def node_id(i, j, k):
+        ok = 1 <= i <= m and 1 <= j <= m and 1 <= k <= m
+        return (i - 1) + m * ((j - 1) + m * (k - 1)) if ok else -1
+
+    return edge_id, node_id
+
+
+def refinement_edges(n):
+    """Sec. 3: the coarse variables follow the geometric refinement of the n^3 mesh (n even).  Every
+    interior edge of the (n/2)^3 coarse mesh, in the coarse mesh's own numbering, is the pair of
+    its two fine halves: DoF1 the half at its tail, DoF2 the half at its head, both oriented like
+    the coarse edge, so the row of R is (+1, +1) (the orthogonal complement of the middle node's
+    gradient column, signs following G).  Returns (dof1, s1, dof2, s2, i, k, j) with i, k, j the
+    tail, middle and head node ids (-1 for a boundary node)."""
+    if n % 2 or n < 2:
+        raise ValueError("refinement needs an even mesh size")
+    N = n // 2
+    fe, fn = hex_numbering(n)
+    ce, _ = hex_numbering(N)
+    steps = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    out = {}
+    for d in range(3):
+        a, b, c = steps[d]
+        for K in range(N + 1):
+            for J in range(N + 1):
+                for I in range(N + 1):
+                    cid = ce(d, I, J, K)
+                    if cid < 0:
+                        continue
+                    x, y, z = 2 * I, 2 * J, 2 * K
+                    d1 = fe(d, x, y, z)
+                    d2 = fe(d, x + a, y + b, z + c)
+                    out[cid] = (d1, 1.0, d2, 1.0, fn(x, y, z), fn(x + a, y + b, z + c),
+                                fn(x + 2 * a, y + 2 * b, z + 2 * c))
+    return [out[c] for c in range(len(out))]
+
+
+def interpolation_geometric(n, edges, ndof):
+    """Geometric Nedelec interpolation ("Geo", Sec. 5) of the (n/2)^3 mesh's edge space into the
+    n^3 mesh's, scaled by 2 so that its rows on the coarse edges' halves are R^T (Eq. sparseP's
+    exterior rows).  A coarse edge's basis function points along the edge and decays linearly to
+    zero one coarse cell away across it; a fine edge parallel to it at transverse offsets (dy, dz)
+    in fine steps (-1, 0, 1) takes the value of that hat product at the fine edge, 1, 1/2 or 1/4,
+    times the ratio of the line integrals (fine over coarse length, 1/2), times 2; fine edges across
+    the coarse edge get 0."""
+    fe, _ = hex_numbering(n)
+    steps = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    N = n // 2
+    ce, _ = hex_numbering(N)
+    rows, cols, vals = [], [], []
+    # the start node of every coarse edge, from its id
+    starts = {}
+    for d in range(3):
+        for K in range(N + 1):
+            for J in range(N + 1):
+                for I in range(N + 1):
+                    cid = ce(d, I, J, K)
+                    if cid >= 0:
+                        starts[cid] = (d, I, J, K)
+    hat = {-1: 0.5, 0: 1.0, 1: 0.5}
+    for c in range(len(edges)):
+        d, I, J, K = starts[c]
+        a, b, cc = steps[d]
+        t1, t2 = [ax for ax in range(3) if ax != d]
+        for half in (0, 1):
+            base = [2 * I + half * a, 2 * J + half * b, 2 * K + half * cc]
+            for o1 in (-1, 0, 1):
+                for o2 in (-1, 0, 1):
+                    q = list(base)
+                    q[t1] += o1
+                    q[t2] += o2
+                    e = fe(d, *q)
+                    if e >= 0:
+                        rows.append(e)
+                        cols.append(c)
+                        vals.append(hat[o1] * hat[o2])
+    P = sp.csr_matrix((vals, (rows, cols)), shape=(ndof, len(edges)))
+    P.sort_indices()
+    return P
+
+
+def geometric_patches(n, edges, ndof):
+    """Interior support of every column of the geometric interpolation (the fine edges parallel to
+    the coarse edge other than its two halves), sorted."""
+    Pg = interpolation_geometric(n, edges, ndof).tocsc()
+    out = []
+    for c, e in enumerate(edges):
+        rows = Pg.indices[Pg.indptr[c]:Pg.indptr[c + 1]]
+        out.append(np.array(sorted(r for r in rows if r not in (e[0], e[2])), dtype=np.int64))
+    return out
+
+
+def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta=0.25, pmap=map, nchunks=1,
+            splitting="algebraic", mesh_n=None):
+    """One application of the two-level setup.  splitting="algebraic" (Sec. 4): augment G
+    (Alg. 1), split the nodal dual operator (Alg. 2), pair edges (Alg. 3).  splitting="refinement"
+    (Sec. 3): the pairs of the geometric refinement of the mesh_n^3 hex mesh.  Then interpolate
+    (Eq. sparseP; interp="geometric": the geometric Nedelec interpolation instead) and form G_c
+    (Eq. Gc)."""
     A = sp.csr_matrix(A)
     G = sp.csr_matrix(G)
     ndof = A.shape[0]
-    Gt, B = augment_G(G)
-    N = nodal_graph(A, Gt, nB=len(B), strength=strength, theta=theta)
-    M = incidence_graph(Gt)
-    cG, fG, state = nodal_cf(N, B)
-    edges = match_coarse_edges(Gt, N, M, cG, B, ndof)
-    out = dict(Gt=Gt, B=B, cG=cG, fG=fG, edges=edges)
+    if splitting == "refinement":
+        edges = refinement_edges(mesh_n)
+        keep_nodes = sorted({e[4] for e in edges if e[4] >= 0} | {e[6] for e in edges if e[6] >= 0})
+        cG = np.array(keep_nodes, dtype=np.int64)
+        fG = np.setdiff1d(np.arange(G.shape[1]), cG)
+        out = dict(Gt=G, B=np.zeros(0, dtype=np.int64), cG=cG, fG=fG, edges=edges)
+    else:
+        if interp == "geometric":
+            raise ValueError("the geometric interpolation needs the refinement splitting")
+        Gt, B = augment_G(G)
+        N = nodal_graph(A, Gt, nB=len(B), strength=strength, theta=theta)
+        M = incidence_graph(Gt)
+        cG, fG, state = nodal_cf(N, B)
+        edges = match_coarse_edges(Gt, N, M, cG, B, ndof)
+        out = dict(Gt=Gt, B=B, cG=cG, fG=fG, edges=edges)
     if not edges:
         return out
     R = restriction(edges, ndof)
@@ -498,6 +627,9 @@ def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta
     if interp == "global":
         patches = None
         P = interpolation_global(A, edges, ndof)
+    elif interp == "geometric":
+        patches = geometric_patches(mesh_n, edges, ndof)
+        P = interpolation_geometric(mesh_n, edges, ndof)
     else:
         patches = interior_patches(A, edges, ndof, p_max=p_max, ring=ring)
         P = interpolation_local(A, edges, patches, ndof, pmap=pmap, nchunks=nchunks)
@@ -516,10 +648,13 @@ def smoother_level(A, G, pmap=map, nchunks=1):
 
 
 def setup(A, G, coarse_size=100, max_levels=20, interp="local", p_max=128, ring=1,
-          stall_ratio=0.9, strength="classical", theta=0.25, pmap=map, nchunks=1):
+          stall_ratio=0.9, strength="classical", theta=0.25, pmap=map, nchunks=1, splitting="algebraic",
+          mesh_n=None):
     """Build the multilevel hierarchy (R9).  Returns a list of level dicts; every level but the
     last carries P, the last carries the dense Cholesky factor of its matrix.  pmap / nchunks
-    spread the independent local solves and star inverses over a parallel map (same result)."""
+    spread the independent local solves and star inverses over a parallel map (same result).
+    splitting="refinement" (with mesh_n, the hex mesh's intervals per side) coarsens by geometric
+    refinement, halving the mesh per level while it stays even."""
     A = sp.csr_matrix(A)
     A.sort_indices()
     G = sp.csr_matrix(G)
@@ -531,8 +666,10 @@ def setup(A, G, coarse_size=100, max_levels=20, interp="local", p_max=128, ring=
         levels.append(L)
         if n <= coarse_size or len(levels) == max_levels:
             break
+        if splitting == "refinement" and (mesh_n is None or mesh_n % 2 or mesh_n < 4):
+            break
         cz = coarsen(A, G, interp=interp, p_max=p_max, ring=ring, strength=strength, theta=theta,
-                     pmap=pmap, nchunks=nchunks)
+                     pmap=pmap, nchunks=nchunks, splitting=splitting, mesh_n=mesh_n)
         L["coarsening"] = cz
         nc = len(cz["edges"])
         if nc == 0 or nc > stall_ratio * n:
@@ -541,6 +678,8 @@ def setup(A, G, coarse_size=100, max_levels=20, interp="local", p_max=128, ring=
         L["P"] = cz["P"]
         A = galerkin(A, cz["P"])
         G = cz["Gc"]
+        if splitting == "refinement":
+            mesh_n //= 2
     last = levels[-1]
     last["chol"] = sla.cho_factor(last["A"].toarray(), lower=True)
     return levels

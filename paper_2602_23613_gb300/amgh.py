@@ -15,7 +15,8 @@ from . import build as _build
 AMGH_OK, AMGH_ERR_INVALID_ARG, AMGH_ERR_NOT_SPD, AMGH_ERR_NOT_CONVERGED = 0, 1, 2, 3
 AMGH_ERR_CUDA, AMGH_ERR_OOM, AMGH_ERR_TIMEOUT, AMGH_ERR_SETUP_STALL, AMGH_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 AMGH_F64, AMGH_F32, AMGH_BF16 = 0, 1, 2
-AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED = 0, 1
+AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED, AMGH_INTERP_GEOMETRIC = 0, 1, 2
+AMGH_COARSEN_ALGEBRAIC, AMGH_COARSEN_REFINEMENT = 0, 1
 KIND = {"schwarz": 0, "l1": 1, "residual": 2, "restrict": 3, "prolong": 4, "coarse": 5, "spmv": 6, "rr": 7}
 
 
@@ -30,7 +31,7 @@ class amgh_params(ctypes.Structure):
                 ("interp", ctypes.c_int), ("ring", ctypes.c_int), ("p_max", ctypes.c_int),
                 ("theta", ctypes.c_double), ("stall_ratio", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("dense_tail", ctypes.c_int), ("mlp", ctypes.c_void_p), ("rho_ref", ctypes.c_double),
-                ("fuse_restrict", ctypes.c_int)]
+                ("fuse_restrict", ctypes.c_int), ("coarsening", ctypes.c_int), ("mesh_n", ctypes.c_int)]
 
 
 class amgh_hier_info(ctypes.Structure):

@@ -1688,8 +1688,14 @@ static void check_params(const amgh_params& prm) {
         prm.p_max > 256 || prm.precision < 0 || prm.precision > 2 || !(prm.theta >= 0.0 && prm.theta <= 1.0) ||
         !(prm.stall_ratio > 0.0) || prm.dense_tail < 0 || prm.dense_tail > 16384)
         throw StatusError{AMGH_ERR_INVALID_ARG, "parameter out of range"};
-    if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED)
+    if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED && prm.interp != AMGH_INTERP_GEOMETRIC)
         throw StatusError{AMGH_ERR_INVALID_ARG, "unknown interpolation mode"};
+    if (prm.coarsening != AMGH_COARSEN_ALGEBRAIC && prm.coarsening != AMGH_COARSEN_REFINEMENT)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "unknown coarsening mode"};
+    if (prm.coarsening == AMGH_COARSEN_REFINEMENT && (prm.mesh_n < 4 || prm.mesh_n % 2))
+        throw StatusError{AMGH_ERR_INVALID_ARG, "refinement coarsening needs mesh_n even and at least 4"};
+    if (prm.interp == AMGH_INTERP_GEOMETRIC && prm.coarsening != AMGH_COARSEN_REFINEMENT)
+        throw StatusError{AMGH_ERR_INVALID_ARG, "the geometric interpolation needs refinement coarsening"};
     if (prm.interp == AMGH_INTERP_LEARNED && !prm.mlp)
         throw StatusError{AMGH_ERR_INVALID_ARG, "learned interpolation needs a network (params.mlp)"};
 }
@@ -1730,8 +1736,13 @@ static void host_structure_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr
     LevelHost& cur = h->hl.back();
     cur.A = std::move(A);
     cur.G = std::move(G);
-    std::string msg = coarsen_level(cur.A, cur.G, graph_params(h->prm), cur.cz, host_threads());
-    if (!msg.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, msg};
+    std::string msg = h->prm.coarsening == AMGH_COARSEN_REFINEMENT
+                          ? coarsen_level_refinement(cur.A, cur.G, h->prm.mesh_n,
+                                                     h->prm.interp == AMGH_INTERP_GEOMETRIC, graph_params(h->prm),
+                                                     cur.cz, host_threads())
+                          : coarsen_level(cur.A, cur.G, graph_params(h->prm), cur.cz, host_threads());
+    if (!msg.empty())
+        throw StatusError{h->prm.coarsening == AMGH_COARSEN_REFINEMENT ? AMGH_ERR_INVALID_ARG : AMGH_ERR_SETUP_STALL, msg};
     if (cur.cz.edges.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, "the finest level produced no coarse edge"};
     msg = build_stars(cur.A, cur.G, cur.stars);
     if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
@@ -1791,6 +1802,8 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         const char* ov = std::getenv("AMGH_ENGINE_OVERLAP");
         if (!(ov && std::string(ov) == "0")) worker.reset(new EngineWorker(h, e, (int)cap));
     }
+    const bool refine = prm.coarsening == AMGH_COARSEN_REFINEMENT;
+    int mesh_n = prm.mesh_n;
     for (int l = 0;; ++l) {
         h->hl.emplace_back();
         LevelHost& cur = h->hl.back();
@@ -1800,9 +1813,14 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         const int n = cur.A.nrows;
         bool coarsest = n <= prm.coarse_size || l + 1 >= prm.max_levels;
         double t0 = now_ms();
+        // refinement coarsening halves the mesh per level while it stays even
+        if (refine && (mesh_n % 2 || mesh_n < 4)) coarsest = true;
         if (!coarsest) {
-            std::string msg = coarsen_level(cur.A, cur.G, gp, cur.cz, nthreads);
-            if (!msg.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, msg};
+            std::string msg = refine ? coarsen_level_refinement(cur.A, cur.G, mesh_n,
+                                                                prm.interp == AMGH_INTERP_GEOMETRIC, gp, cur.cz,
+                                                                nthreads)
+                                     : coarsen_level(cur.A, cur.G, gp, cur.cz, nthreads);
+            if (!msg.empty()) throw StatusError{l == 0 && refine ? AMGH_ERR_INVALID_ARG : AMGH_ERR_SETUP_STALL, msg};
             const int nc = (int)cur.cz.edges.size();
             if (nc == 0 || (double)nc > prm.stall_ratio * n) {
                 if (l == 0) throw StatusError{AMGH_ERR_SETUP_STALL, "the finest level produced no usable coarse level"};
@@ -1867,7 +1885,24 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             }
             bool solved = false;
             auto* net = static_cast<amgh_mlp_ctx*>(prm.mlp);
-            if (l == 0 && prm.interp == AMGH_INTERP_LEARNED && net && maxp <= MLP_SLOTS) {
+            if (!cz.geo_ptr.empty()) {
+                // the geometric interpolation: its weights are set, not solved for
+                std::vector<double> pv(cz.P.nnz(), 0.0), ptv(cz.PT.nnz(), 0.0);
+                for (int c = 0; c < nc; ++c) {
+                    pv[cz.ext_pos_P[2 * (size_t)c]] = cz.edges[c].s1;
+                    pv[cz.ext_pos_P[2 * (size_t)c + 1]] = cz.edges[c].s2;
+                    ptv[cz.ext_pos_PT[2 * (size_t)c]] = cz.edges[c].s1;
+                    ptv[cz.ext_pos_PT[2 * (size_t)c + 1]] = cz.edges[c].s2;
+                }
+                for (size_t q = 0; q < cz.geo_val.size(); ++q) {
+                    pv[cz.patch_pos_P[q]] = cz.geo_val[q];
+                    ptv[cz.patch_pos_PT[q]] = cz.geo_val[q];
+                }
+                AMGH_CUDA(cudaMemcpyAsync(P.val.p, pv.data(), sizeof(double) * pv.size(), cudaMemcpyHostToDevice, s));
+                AMGH_CUDA(cudaMemcpyAsync(PT.val.p, ptv.data(), sizeof(double) * ptv.size(), cudaMemcpyHostToDevice, s));
+                AMGH_CUDA(cudaStreamSynchronize(s));
+                h->interp_used = AMGH_INTERP_GEOMETRIC;
+            } else if (l == 0 && prm.interp == AMGH_INTERP_LEARNED && net && maxp <= MLP_SLOTS) {
                 // the network predicts the interior values of every column of P on its patch
                 DevArray<float> X, Y;
                 X.alloc((size_t)nc * MLP_DIN);
@@ -1937,6 +1972,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         AMGH_CUDA(cudaMemcpyAsync(An.val.data(), Ac.val.p, sizeof(double) * Ac.nnz, cudaMemcpyDeviceToHost, s));
         AMGH_CUDA(cudaStreamSynchronize(s));
         if (worker) worker->hand_over(l, s);   // level l's P, P^T and stars are final
+        if (refine) mesh_n /= 2;
         h->dev_ms += std::max(0.0, now_ms() - t0 - t_stars);
         ph.mark(s, "Galerkin + download", l);
         A = std::move(An);
@@ -2640,6 +2676,8 @@ void amgh_default_params(amgh_params* p) {
     p->mlp = nullptr;
     p->rho_ref = 0.0;
     p->fuse_restrict = 0;
+    p->coarsening = AMGH_COARSEN_ALGEBRAIC;
+    p->mesh_n = 0;
 }
 
 amgh_status amgh_batch_setup(int nsys, const amgh_csr* A, const amgh_csr* G, const amgh_params* params,

@@ -567,9 +567,11 @@ static void match(const HostCSR& Gt, const HostCSR& GtT, const HostCSR& N, const
     }
 }
 
+static std::string finish_coarsening(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
+                                     int nthreads, PhaseClock& clk);
+
 std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
                           int nthreads) {
-    const int n = A.nrows;
     PhaseClock clk;
     int nB = 0;
     HostCSR Gt = augment(G, nB, nthreads);
@@ -585,16 +587,129 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     out.edges.clear();
     match(Gt, GtT, N, Minc, out.state, G.ncols, out.edges);
     clk.mark("matching");
-    const int nc = (int)out.edges.size();
-    if (nc == 0) return "";
+    if (out.edges.empty()) return "";
     for (const auto& e : out.edges)
         if (e.d1 < 0 || e.d2 < 0) return "internal: matching found no edge for a path";
+    out.geo_ptr.clear();
+    out.geo_idx.clear();
+    out.geo_val.clear();
+    return finish_coarsening(A, G, prm, out, nthreads, clk);
+}
 
-    // Eq. Gc: rows e_j - e_i (or -e_i when j is artificial); keep the nonzero columns
+// -------------------------------------------------------------------------------------------
+// Section 3's refinement-based coarse variables on the structured hex mesh of the unit cube with
+// mesh_n intervals per side (interior edges numbered x, y, z, each lexicographic by start node,
+// +axis; interior nodes lexicographic).  Every interior edge of the coarse (mesh_n/2)^3 mesh, in
+// the coarse mesh's own numbering, pairs its two fine halves with signs (+1, +1): the orthogonal
+// complement of the middle node's gradient column, both halves oriented like the coarse edge.
+// With `geometric`, the interior support of a column is the 16 fine edges parallel to it one fine
+// step across (the support of the geometric Nedelec interpolation), with the hat-product weights
+// 1/2 (one transverse step) and 1/4 (two), in the scaling whose rows on the halves are R^T.
+// -------------------------------------------------------------------------------------------
+namespace {
+struct HexIds {
+    int n, m;
+    int64_t nx;
+    explicit HexIds(int nn) : n(nn), m(nn - 1), nx((int64_t)nn * (nn - 1) * (nn - 1)) {}
+    int32_t edge(int d, int i, int j, int k) const {
+        if (d == 0) return (i >= 0 && i < n && j >= 1 && j <= m && k >= 1 && k <= m)
+                               ? (int32_t)(i + (int64_t)n * ((j - 1) + (int64_t)m * (k - 1))) : -1;
+        if (d == 1) return (i >= 1 && i <= m && j >= 0 && j < n && k >= 1 && k <= m)
+                               ? (int32_t)(nx + (i - 1) + (int64_t)m * (j + (int64_t)n * (k - 1))) : -1;
+        return (i >= 1 && i <= m && j >= 1 && j <= m && k >= 0 && k < n)
+                   ? (int32_t)(2 * nx + (i - 1) + (int64_t)m * ((j - 1) + (int64_t)m * k)) : -1;
+    }
+    int32_t node(int i, int j, int k) const {
+        return (i >= 1 && i <= m && j >= 1 && j <= m && k >= 1 && k <= m)
+                   ? (int32_t)((i - 1) + (int64_t)m * ((j - 1) + (int64_t)m * (k - 1))) : -1;
+    }
+    int64_t nedges() const { return 3 * nx; }
+};
+}  // namespace
+
+std::string coarsen_level_refinement(const HostCSR& A, const HostCSR& G, int mesh_n, bool geometric,
+                                     const Params& prm, Coarsening& out, int nthreads) {
+    PhaseClock clk;
+    if (mesh_n < 4 || mesh_n % 2) return "refinement coarsening needs an even mesh size of at least 4";
+    const HexIds fine(mesh_n), coarse(mesh_n / 2);
+    if (A.nrows != fine.nedges() || G.nrows != A.nrows || G.ncols != (int64_t)fine.m * fine.m * fine.m)
+        return "A and G do not match a hex mesh of " + std::to_string(mesh_n) + " intervals per side";
+    const int N = mesh_n / 2;
+    const int nc = (int)coarse.nedges();
+    out.edges.assign(nc, CoarseEdge{-1, 0, -1, 0, -1, -1, -1});
+    out.m = G.ncols;
+    out.nB = 0;
+    out.state.assign(G.ncols, 2);
+    const int step[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int d = 0; d < 3; ++d)
+        for (int K = 0; K <= N; ++K)
+            for (int J = 0; J <= N; ++J)
+                for (int I = 0; I <= N; ++I) {
+                    const int32_t c = coarse.edge(d, I, J, K);
+                    if (c < 0) continue;
+                    const int x = 2 * I, y = 2 * J, z = 2 * K, a = step[d][0], b = step[d][1], e = step[d][2];
+                    CoarseEdge& ce = out.edges[c];
+                    ce.d1 = fine.edge(d, x, y, z);
+                    ce.d2 = fine.edge(d, x + a, y + b, z + e);
+                    ce.s1 = ce.s2 = 1;
+                    ce.i = fine.node(x, y, z);
+                    ce.k = fine.node(x + a, y + b, z + e);
+                    ce.j = fine.node(x + 2 * a, y + 2 * b, z + 2 * e);
+                    if (ce.d1 < 0 || ce.d2 < 0 || ce.k < 0) return "internal: a coarse edge's half is not interior";
+                    if (ce.i >= 0) out.state[ce.i] = 1;
+                    if (ce.j >= 0) out.state[ce.j] = 1;
+                }
+    clk.mark("refinement pairs");
+    out.geo_ptr.clear();
+    out.geo_idx.clear();
+    out.geo_val.clear();
+    if (!geometric) return finish_coarsening(A, G, prm, out, nthreads, clk);
+    // geometric interpolation: the supports and weights of Sec. 5's comparison interpolation
+    out.geo_ptr.assign(nc + 1, 0);
+    out.geo_idx.clear();
+    out.geo_val.clear();
+    for (int d = 0; d < 3; ++d)
+        for (int K = 0; K <= N; ++K)
+            for (int J = 0; J <= N; ++J)
+                for (int I = 0; I <= N; ++I) {
+                    const int32_t c = coarse.edge(d, I, J, K);
+                    if (c < 0) continue;
+                    const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+                    std::vector<std::pair<int32_t, double>> col;
+                    for (int half = 0; half < 2; ++half)
+                        for (int o1 = -1; o1 <= 1; ++o1)
+                            for (int o2 = -1; o2 <= 1; ++o2) {
+                                if (o1 == 0 && o2 == 0) continue;   // the halves: R^T
+                                int q[3] = {2 * I + half * step[d][0], 2 * J + half * step[d][1],
+                                            2 * K + half * step[d][2]};
+                                q[t1] += o1;
+                                q[t2] += o2;
+                                const int32_t f = fine.edge(d, q[0], q[1], q[2]);
+                                if (f >= 0) col.push_back({f, (o1 ? 0.5 : 1.0) * (o2 ? 0.5 : 1.0)});
+                            }
+                    std::sort(col.begin(), col.end());
+                    for (const auto& pv : col) {
+                        out.geo_idx.push_back(pv.first);
+                        out.geo_val.push_back(pv.second);
+                    }
+                    out.geo_ptr[c + 1] = (int32_t)col.size();
+                }
+    for (int c = 0; c < nc; ++c) out.geo_ptr[c + 1] += out.geo_ptr[c];
+    // the columns were appended in the loop order, which is the coarse numbering's order
+    clk.mark("geometric interpolation");
+    return finish_coarsening(A, G, prm, out, nthreads, clk);
+}
+
+static std::string finish_coarsening(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
+                                     int nthreads, PhaseClock& clk) {
+    const int n = A.nrows;
+    const int nc = (int)out.edges.size();
+    // Eq. Gc: rows e_j - e_i over the ends that are columns of G (an artificial or eliminated
+    // end contributes nothing); keep the nonzero columns
     std::vector<char> keep(G.ncols, 0);
     for (const auto& e : out.edges) {
-        keep[e.i] = 1;
-        if (e.j < G.ncols) keep[e.j] = 1;
+        if (e.i >= 0 && e.i < G.ncols) keep[e.i] = 1;
+        if (e.j >= 0 && e.j < G.ncols) keep[e.j] = 1;
     }
     std::vector<int32_t> newid(G.ncols, -1);
     out.coarse_nodes.clear();
@@ -611,135 +726,145 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
     Gc.val.clear();
     for (int c = 0; c < nc; ++c) {
         const auto& e = out.edges[c];
-        // i < j always; new ids keep the order
-        Gc.idx.push_back(newid[e.i]);
-        Gc.val.push_back(-1.0);
-        if (e.j < G.ncols) {
+        // new ids keep the order of the fine columns, so the row stays sorted when i < j
+        const bool hi = e.i >= 0 && e.i < G.ncols, hj = e.j >= 0 && e.j < G.ncols;
+        if (hi && hj && e.j < e.i) return "internal: a coarse edge's ends are out of order";
+        if (hi) {
+            Gc.idx.push_back(newid[e.i]);
+            Gc.val.push_back(-1.0);
+        }
+        if (hj) {
             Gc.idx.push_back(newid[e.j]);
             Gc.val.push_back(1.0);
         }
         Gc.ptr[c + 1] = (int32_t)Gc.idx.size();
     }
 
-    // ---- Eq. sparseP patches: components of graph(A_II) if small enough, else rings ----------
-    std::vector<char> ext(n, 0);
-    for (const auto& e : out.edges) ext[e.d1] = ext[e.d2] = 1;
-    // connected components of graph(A_II) by a concurrent union-find: a root is only ever linked
-    // below a smaller root (compare-and-swap), so every component ends with its smallest member as
-    // root whatever the order of the unions; finds halve paths with relaxed stores, which keep
-    // every node's parent an ancestor
-    std::vector<int32_t> parent(n);
-    std::iota(parent.begin(), parent.end(), 0);
-    int32_t* par = parent.data();
-    auto find = [par](int32_t x) {
-        for (;;) {
-            const int32_t p = __atomic_load_n(&par[x], __ATOMIC_RELAXED);
-            if (p == x) return x;
-            const int32_t gp = __atomic_load_n(&par[p], __ATOMIC_RELAXED);
-            if (gp != p) __atomic_store_n(&par[x], gp, __ATOMIC_RELAXED);
-            x = gp;
-        }
-    };
-#pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
-    for (int r = 0; r < n; ++r) {
-        if (ext[r]) continue;
-        for (int32_t t = A.ptr[r]; t < A.ptr[r + 1]; ++t) {
-            const int32_t c = A.idx[t];
-            if (c <= r || ext[c]) continue;
-            int32_t x = r, y = c;
+    if (!out.geo_ptr.empty()) {
+        // the geometric interpolation's supports stand in for the patches (their values are set,
+        // not solved for)
+        out.patch_ptr = out.geo_ptr;
+        out.patch_idx = out.geo_idx;
+    } else {
+        // ---- Eq. sparseP patches: components of graph(A_II) if small enough, else rings ----------
+        std::vector<char> ext(n, 0);
+        for (const auto& e : out.edges) ext[e.d1] = ext[e.d2] = 1;
+        // connected components of graph(A_II) by a concurrent union-find: a root is only ever linked
+        // below a smaller root (compare-and-swap), so every component ends with its smallest member as
+        // root whatever the order of the unions; finds halve paths with relaxed stores, which keep
+        // every node's parent an ancestor
+        std::vector<int32_t> parent(n);
+        std::iota(parent.begin(), parent.end(), 0);
+        int32_t* par = parent.data();
+        auto find = [par](int32_t x) {
             for (;;) {
-                x = find(x);
-                y = find(y);
-                if (x == y) break;
-                if (x < y) std::swap(x, y);   // link the larger root below the smaller one
-                int32_t expect = x;
-                if (__atomic_compare_exchange_n(&par[x], &expect, y, false, __ATOMIC_ACQ_REL, __ATOMIC_RELAXED)) break;
+                const int32_t p = __atomic_load_n(&par[x], __ATOMIC_RELAXED);
+                if (p == x) return x;
+                const int32_t gp = __atomic_load_n(&par[p], __ATOMIC_RELAXED);
+                if (gp != p) __atomic_store_n(&par[x], gp, __ATOMIC_RELAXED);
+                x = gp;
             }
-        }
-    }
-    std::vector<int32_t> comp(n, -1), csize;
-    {
-        std::vector<int32_t> label(n, -1);
-        for (int r = 0; r < n; ++r)
-            if (!ext[r]) {
-                int32_t root = find(r);
-                if (label[root] < 0) { label[root] = (int32_t)csize.size(); csize.push_back(0); }
-                comp[r] = label[root];
-                csize[comp[r]]++;
-            }
-    }
-    std::vector<int32_t> cptr(csize.size() + 1, 0), cmem(n);
-    for (size_t c = 0; c < csize.size(); ++c) cptr[c + 1] = cptr[c] + csize[c];
-    {
-        std::vector<int32_t> cur(cptr.begin(), cptr.end() - 1);
-        for (int r = 0; r < n; ++r)
-            if (comp[r] >= 0) cmem[cur[comp[r]]++] = r;   // ascending within a component
-    }
-    clk.mark("G_c + components");
-    // each thread keeps its scratch lists across coarse edges and appends the patches it builds
-    // to its own flat buffer; a patch is found through (thread, offset, length)
-    std::vector<std::vector<int32_t>> pbuf(nthreads);
-    std::vector<int32_t> pthread(nc), poff(nc), plen(nc);
-#pragma omp parallel num_threads(nthreads)
-    {
-        const int tid = thread_id();
-        auto& buf = pbuf[tid];
-        std::vector<int32_t> seeds, comps, order, level, seen, nxt, merged;
-#pragma omp for schedule(dynamic, 64)
-        for (int c = 0; c < nc; ++c) {
-            const auto& e = out.edges[c];
-            seeds.clear();
-            for (int32_t d : {e.d1, e.d2})
-                for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t)
-                    if (!ext[A.idx[t]]) seeds.push_back(A.idx[t]);
-            std::sort(seeds.begin(), seeds.end());
-            seeds.erase(std::unique(seeds.begin(), seeds.end()), seeds.end());
-            comps.clear();
-            for (int32_t sd : seeds) comps.push_back(comp[sd]);
-            std::sort(comps.begin(), comps.end());
-            comps.erase(std::unique(comps.begin(), comps.end()), comps.end());
-            int64_t tot = 0;
-            for (int32_t q : comps) tot += csize[q];
-            const size_t b = buf.size();
-            if (tot <= prm.p_max) {
-                for (int32_t q : comps) buf.insert(buf.end(), cmem.begin() + cptr[q], cmem.begin() + cptr[q + 1]);
-            } else {
-                order = seeds;
-                level = seeds;
-                seen = seeds;   // sorted
-                for (int r = 1; r < prm.ring && (int)order.size() < prm.p_max; ++r) {
-                    nxt.clear();
-                    for (int32_t d : level)
-                        for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t) {
-                            int32_t x = A.idx[t];
-                            if (!ext[x] && !std::binary_search(seen.begin(), seen.end(), x)) nxt.push_back(x);
-                        }
-                    std::sort(nxt.begin(), nxt.end());
-                    nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
-                    order.insert(order.end(), nxt.begin(), nxt.end());
-                    merged.clear();
-                    std::merge(seen.begin(), seen.end(), nxt.begin(), nxt.end(), std::back_inserter(merged));
-                    seen.swap(merged);
-                    level.swap(nxt);
+        };
+    #pragma omp parallel for schedule(dynamic, 4096) num_threads(nthreads)
+        for (int r = 0; r < n; ++r) {
+            if (ext[r]) continue;
+            for (int32_t t = A.ptr[r]; t < A.ptr[r + 1]; ++t) {
+                const int32_t c = A.idx[t];
+                if (c <= r || ext[c]) continue;
+                int32_t x = r, y = c;
+                for (;;) {
+                    x = find(x);
+                    y = find(y);
+                    if (x == y) break;
+                    if (x < y) std::swap(x, y);   // link the larger root below the smaller one
+                    int32_t expect = x;
+                    if (__atomic_compare_exchange_n(&par[x], &expect, y, false, __ATOMIC_ACQ_REL, __ATOMIC_RELAXED)) break;
                 }
-                if ((int)order.size() > prm.p_max) order.resize(prm.p_max);
-                buf.insert(buf.end(), order.begin(), order.end());
             }
-            std::sort(buf.begin() + (std::ptrdiff_t)b, buf.end());
-            pthread[c] = tid;
-            poff[c] = (int32_t)b;
-            plen[c] = (int32_t)(buf.size() - b);
+        }
+        std::vector<int32_t> comp(n, -1), csize;
+        {
+            std::vector<int32_t> label(n, -1);
+            for (int r = 0; r < n; ++r)
+                if (!ext[r]) {
+                    int32_t root = find(r);
+                    if (label[root] < 0) { label[root] = (int32_t)csize.size(); csize.push_back(0); }
+                    comp[r] = label[root];
+                    csize[comp[r]]++;
+                }
+        }
+        std::vector<int32_t> cptr(csize.size() + 1, 0), cmem(n);
+        for (size_t c = 0; c < csize.size(); ++c) cptr[c + 1] = cptr[c] + csize[c];
+        {
+            std::vector<int32_t> cur(cptr.begin(), cptr.end() - 1);
+            for (int r = 0; r < n; ++r)
+                if (comp[r] >= 0) cmem[cur[comp[r]]++] = r;   // ascending within a component
+        }
+        clk.mark("G_c + components");
+        // each thread keeps its scratch lists across coarse edges and appends the patches it builds
+        // to its own flat buffer; a patch is found through (thread, offset, length)
+        std::vector<std::vector<int32_t>> pbuf(nthreads);
+        std::vector<int32_t> pthread(nc), poff(nc), plen(nc);
+    #pragma omp parallel num_threads(nthreads)
+        {
+            const int tid = thread_id();
+            auto& buf = pbuf[tid];
+            std::vector<int32_t> seeds, comps, order, level, seen, nxt, merged;
+    #pragma omp for schedule(dynamic, 64)
+            for (int c = 0; c < nc; ++c) {
+                const auto& e = out.edges[c];
+                seeds.clear();
+                for (int32_t d : {e.d1, e.d2})
+                    for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t)
+                        if (!ext[A.idx[t]]) seeds.push_back(A.idx[t]);
+                std::sort(seeds.begin(), seeds.end());
+                seeds.erase(std::unique(seeds.begin(), seeds.end()), seeds.end());
+                comps.clear();
+                for (int32_t sd : seeds) comps.push_back(comp[sd]);
+                std::sort(comps.begin(), comps.end());
+                comps.erase(std::unique(comps.begin(), comps.end()), comps.end());
+                int64_t tot = 0;
+                for (int32_t q : comps) tot += csize[q];
+                const size_t b = buf.size();
+                if (tot <= prm.p_max) {
+                    for (int32_t q : comps) buf.insert(buf.end(), cmem.begin() + cptr[q], cmem.begin() + cptr[q + 1]);
+                } else {
+                    order = seeds;
+                    level = seeds;
+                    seen = seeds;   // sorted
+                    for (int r = 1; r < prm.ring && (int)order.size() < prm.p_max; ++r) {
+                        nxt.clear();
+                        for (int32_t d : level)
+                            for (int32_t t = A.ptr[d]; t < A.ptr[d + 1]; ++t) {
+                                int32_t x = A.idx[t];
+                                if (!ext[x] && !std::binary_search(seen.begin(), seen.end(), x)) nxt.push_back(x);
+                            }
+                        std::sort(nxt.begin(), nxt.end());
+                        nxt.erase(std::unique(nxt.begin(), nxt.end()), nxt.end());
+                        order.insert(order.end(), nxt.begin(), nxt.end());
+                        merged.clear();
+                        std::merge(seen.begin(), seen.end(), nxt.begin(), nxt.end(), std::back_inserter(merged));
+                        seen.swap(merged);
+                        level.swap(nxt);
+                    }
+                    if ((int)order.size() > prm.p_max) order.resize(prm.p_max);
+                    buf.insert(buf.end(), order.begin(), order.end());
+                }
+                std::sort(buf.begin() + (std::ptrdiff_t)b, buf.end());
+                pthread[c] = tid;
+                poff[c] = (int32_t)b;
+                plen[c] = (int32_t)(buf.size() - b);
+            }
+        }
+        out.patch_ptr.assign(nc + 1, 0);
+        for (int c = 0; c < nc; ++c) out.patch_ptr[c + 1] = out.patch_ptr[c] + plen[c];
+        out.patch_idx.resize(out.patch_ptr[nc]);
+    #pragma omp parallel for schedule(static) num_threads(nthreads)
+        for (int c = 0; c < nc; ++c) {
+            const int32_t* src = pbuf[pthread[c]].data() + poff[c];
+            std::copy(src, src + plen[c], out.patch_idx.begin() + out.patch_ptr[c]);
         }
     }
-    out.patch_ptr.assign(nc + 1, 0);
-    for (int c = 0; c < nc; ++c) out.patch_ptr[c + 1] = out.patch_ptr[c] + plen[c];
-    out.patch_idx.resize(out.patch_ptr[nc]);
-#pragma omp parallel for schedule(static) num_threads(nthreads)
-    for (int c = 0; c < nc; ++c) {
-        const int32_t* src = pbuf[pthread[c]].data() + poff[c];
-        std::copy(src, src + plen[c], out.patch_idx.begin() + out.patch_ptr[c]);
-    }
-
     clk.mark("patches");
     // ---- patterns of P^T (row c: the patch and the two exterior DoFs, ascending) and of P (its
     // transpose), with the positions of every computed entry in both -------------------------

@@ -39,6 +39,10 @@ struct Coarsening {
     std::vector<int64_t> ext_pos_P, ext_pos_PT;   // 2 per coarse edge: (d1, c), (d2, c)
     HostCSR AP;                          // symbolic pattern of A P
     HostCSR Ac;                          // symbolic pattern of P^T A P
+    // geometric interpolation only: per coarse edge its interior support (sorted) and weights,
+    // which then also are the patches
+    std::vector<int32_t> geo_ptr, geo_idx;
+    std::vector<double> geo_val;
 };
 
 struct Params {
@@ -59,6 +63,13 @@ std::string check_csr(const HostCSR& M, bool square);
 // A must carry values (strength test).  Returns "" or an error message.
 std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm, Coarsening& out,
                           int nthreads);
+
+// Section 3's refinement-based pairs on the structured hex mesh with mesh_n intervals per side
+// (coarse edges in the (mesh_n/2)^3 mesh's numbering), then the same patches, G_c and patterns;
+// with `geometric`, the geometric Nedelec interpolation's supports and weights (geo_*) instead of
+// the patches.  Returns "" or an error message.
+std::string coarsen_level_refinement(const HostCSR& A, const HostCSR& G, int mesh_n, bool geometric,
+                                     const Params& prm, Coarsening& out, int nthreads);
 
 // Smoother structure (node stars of G and their colouring) -------------------------------------
 struct StarLayout {

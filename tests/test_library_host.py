@@ -163,3 +163,38 @@ def test_host_structure_matches_oracle_golden_at_bench_size(amgh):
     assert digest(s["patch_ptr"], "i4") == d["patch_ptr"]
     assert digest(s["patch_idx"], "i4") == d["patch_idx"]
     assert digest(s["colour"], "i4") == d["colour"]
+
+
+@pytest.mark.parametrize("n,geometric", [(8, False), (8, True), (16, False), (16, True)])
+def test_refinement_structure_matches_oracle(amgh, n, geometric):
+    """Section 3's refinement pairs ("Ref") and the geometric interpolation's supports ("Geo")
+    from the library's host code against the oracle's: coarse edges with signs and end nodes,
+    coarse nodes, patches (Geo: its supports), colours and the P pattern, bit for bit."""
+    p = W.make_config("hex16_checker") if n == 16 else W.hex_problem(8, W.fields.checkerboard(8, 4), 1e-2)
+    kw = dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=n)
+    if geometric:
+        kw["interp"] = amgh.AMGH_INTERP_GEOMETRIC
+    h = amgh.amgh_setup_host_structure(p["A"], p["G"], **kw)
+    s = amgh.amgh_level_structure(h, 0)
+    cz = O.coarsen(p["A"], p["G"], splitting="refinement", mesh_n=n, interp="geometric" if geometric else "local")
+    edges = np.array([[e[0], int(e[1]), e[2], int(e[3]), e[4], e[5], e[6]] for e in cz["edges"]], np.int64)
+    np.testing.assert_array_equal(s["edges"].astype(np.int64), edges)
+    np.testing.assert_array_equal(s["coarse_nodes"], cz["coarse_nodes"])
+    np.testing.assert_array_equal(s["patch_idx"], np.concatenate(cz["patches"]))
+    np.testing.assert_array_equal(s["colour"], O.colour_stars(p["A"], p["G"]))
+    P = amgh.amgh_level_matrix(h, 0, 1)
+    np.testing.assert_array_equal(P.indptr, cz["P"].indptr)
+    np.testing.assert_array_equal(P.indices, cz["P"].indices)
+
+
+def test_refinement_rejects_bad_meshes(amgh):
+    p = W.hex_problem(8, 1.0, 1.0)
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_setup_host_structure(p["A"], p["G"], coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=7)
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_setup_host_structure(p["A"], p["G"], coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=10)
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_setup_host_structure(p["A"], p["G"], interp=amgh.AMGH_INTERP_GEOMETRIC)
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
