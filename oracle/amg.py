@@ -36,6 +36,19 @@ Readings of points the paper leaves open (each is repeated where it is used):
   R8 (Eq. Gc) I_C keeps the nonzero columns of R G, in ascending order.
   R9 (Sec. 5) coarsening stops when n <= coarse_size, at max_levels, when a level yields no
      coarse edge, or when n_c > 0.9 n.
+  R10 (Eq. commuting; interp="constrained", the 3-D localisation the paper leaves open) the
+     nodal interpolation P_n maps the columns of G~ to the coarse nodes: a coarse node (a column
+     kept by I_C) is injected; the middle node k of a pair (i, k, j) takes half of each of its
+     two ends (an end that is not a coarse node, i.e. a boundary node, counts as zero); every
+     other node outside B, in breadth-first layers of the incidence graph from those nodes, takes
+     the mean over its neighbours in the previous layer and in the boundary nodes B (zero).
+     On the refinement of a hex mesh this is trilinear interpolation.
+  R11 (Eq. sparseP with Eq. commuting; interp="constrained") with R's rows (+-1, +-1) the
+     exterior rows R^T satisfy P G_c = 2 G P_n (a half edge carries half of its coarse edge's
+     difference); every interior row p_i of the local extension (R1) is replaced by the nearest
+     row on the same pattern S_i (Euclidean norm) that satisfies row i of that relation, in the
+     least-squares sense where none on S_i does: p_i + (t_i - p_i C_i) C_i^+, with C_i the rows
+     S_i of G_c and t_i row i of 2 G P_n.
 """
 import heapq
 
@@ -394,6 +407,83 @@ def interpolation_global(A, edges, ndof):
     return sp.csr_matrix(P)
 
 
+# ----------------------------------------------------------------------------------------------
+# Eq. commuting: the local extension corrected to commute with a nodal interpolation (R10, R11)
+# ----------------------------------------------------------------------------------------------
+
+
+def nodal_interpolation(Gt, B, edges, coarse_nodes):
+    """R10: P_n (columns of G~ x coarse nodes).  Layer 0 holds the coarse nodes (injected) and
+    the middle nodes of the pairs (half of each coarse end); layer d + 1 holds the nodes outside B
+    first reached from layer d in the incidence graph, each the mean of its neighbours in layer d
+    and in B (the boundary nodes, zero).  Nodes never reached keep zero rows."""
+    Gt = sp.csr_matrix(Gt)
+    nn = Gt.shape[1]
+    nc = len(coarse_nodes)
+    col = np.full(nn, -1, dtype=np.int64)
+    col[coarse_nodes] = np.arange(nc)
+    layer = np.full(nn, -1, dtype=np.int64)
+    layer[coarse_nodes] = 0
+    rows, cols, vals = list(coarse_nodes), list(range(nc)), [1.0] * nc
+    for e in edges:
+        i, k, j = e[4], e[5], e[6]
+        if k < 0:
+            continue
+        layer[k] = 0
+        for end in (i, j):
+            if end >= 0 and col[end] >= 0:
+                rows.append(k)
+                cols.append(col[end])
+                vals.append(0.5)
+    Pn = sp.csr_matrix((vals, (rows, cols)), shape=(nn, nc))
+    nbr = incidence_graph(Gt)
+    Adj = sp.csr_matrix((np.ones(sum(len(a) for a in nbr)), np.concatenate(nbr) if nn else np.zeros(0, int),
+                         np.concatenate([[0], np.cumsum([len(a) for a in nbr])])), shape=(nn, nn))
+    isB = np.zeros(nn, dtype=bool)
+    isB[B] = True
+    d = 0
+    while True:
+        reached = Adj @ ((layer == d) & ~isB).astype(np.float64)
+        nxt = np.flatnonzero((reached > 0) & (layer < 0) & ~isB)
+        if len(nxt) == 0:
+            break
+        d += 1
+        layer[nxt] = d
+        eligible = ((layer == d - 1) | isB).astype(np.float64)
+        Wn = sp.csr_matrix(Adj[nxt] @ sp.diags(eligible))
+        Wn = sp.csr_matrix(sp.diags(1.0 / np.asarray(Wn.sum(axis=1)).ravel()) @ Wn)
+        place = sp.csr_matrix((np.ones(len(nxt)), (nxt, np.arange(len(nxt)))), shape=(nn, len(nxt)))
+        Pn = sp.csr_matrix(Pn + place @ (Wn @ Pn))
+    Pn.sort_indices()
+    return Pn
+
+
+def interpolation_constrained(P, G, Gc, Pn, edges):
+    """R11: every interior row of P moved, on its own pattern, to the nearest row satisfying
+    row i of P G_c = 2 G P_n (least squares where it cannot); exterior rows kept."""
+    P = sp.csr_matrix(P, copy=True)
+    P.sort_indices()
+    G = sp.csr_matrix(G)
+    m = G.shape[1]
+    T = sp.csr_matrix(2.0 * (G @ sp.csr_matrix(Pn)[:m]))
+    Gc = sp.csr_matrix(Gc)
+    ext = np.zeros(P.shape[0], dtype=bool)
+    for e in edges:
+        ext[e[0]] = ext[e[2]] = True
+    data = P.data.copy()
+    for i in np.flatnonzero(~ext):
+        a, b = P.indptr[i], P.indptr[i + 1]
+        if a == b:
+            continue
+        C = Gc[P.indices[a:b]]
+        nodes = np.union1d(C.indices, T.indices[T.indptr[i]:T.indptr[i + 1]])
+        Cd = C[:, nodes].toarray()
+        t = T[i][:, nodes].toarray().ravel()
+        p0 = P.data[a:b]
+        data[a:b] = p0 + (t - p0 @ Cd) @ np.linalg.pinv(Cd)
+    return sp.csr_matrix((data, P.indices.copy(), P.indptr.copy()), shape=P.shape)
+
+
 def galerkin(A, P):
     """A_c = P^T A P (Eq. tl) on the symbolic pattern (R3)."""
     Pt = sp.csr_matrix(P.T)
@@ -600,8 +690,9 @@ def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta
     """One application of the two-level setup.  splitting="algebraic" (Sec. 4): augment G
     (Alg. 1), split the nodal dual operator (Alg. 2), pair edges (Alg. 3).  splitting="refinement"
     (Sec. 3): the pairs of the geometric refinement of the mesh_n^3 hex mesh.  Then interpolate
-    (Eq. sparseP; interp="geometric": the geometric Nedelec interpolation instead) and form G_c
-    (Eq. Gc)."""
+    (Eq. sparseP; interp="geometric": the geometric Nedelec interpolation instead;
+    interp="constrained": Eq. sparseP's local extension corrected to commute, R10-R11) and form
+    G_c (Eq. Gc)."""
     A = sp.csr_matrix(A)
     G = sp.csr_matrix(G)
     ndof = A.shape[0]
@@ -633,6 +724,11 @@ def coarsen(A, G, interp="local", p_max=128, ring=1, strength="classical", theta
     else:
         patches = interior_patches(A, edges, ndof, p_max=p_max, ring=ring)
         P = interpolation_local(A, edges, patches, ndof, pmap=pmap, nchunks=nchunks)
+    if interp == "constrained":
+        Gn, Bn = (out["Gt"], out["B"]) if splitting != "refinement" else augment_G(G)
+        Pn = nodal_interpolation(Gn, Bn, edges, keep)
+        out["Pn"] = Pn
+        P = interpolation_constrained(P, G, Gc, Pn, edges)
     out.update(R=R, Gc=Gc, coarse_nodes=keep, patches=patches, P=P)
     return out
 
