@@ -38,6 +38,9 @@ def parse():
                     help="rows at or below which the V-cycle tail is one dense operator (library default if unset)")
     ap.add_argument("--fuse-restrict", type=int, default=None, choices=[-1, 0, 1],
                     help="fused residual + restriction: -1 tuned per level, 0 off, 1 on (library default if unset)")
+    ap.add_argument("--interp", default="local", choices=["local", "constrained"],
+                    help="interior extension: the paper's local harmonic extension, or the same corrected to "
+                         "commute with a nodal interpolation")
     ap.add_argument("--variants", default="hex128_spheres",
                     help="workload of the FP64 / FP32 / BF16 comparison reported in the line ('none' to skip)")
     ap.add_argument("--variant-steps", type=int, default=1)
@@ -419,6 +422,8 @@ def run_gpu(args, rank, world, local_rank):
     extra = {} if args.dense_tail is None else {"dense_tail": args.dense_tail}
     if args.fuse_restrict is not None:
         extra["fuse_restrict"] = args.fuse_restrict
+    if args.interp == "constrained":
+        extra["interp"] = amgh.AMGH_INTERP_CONSTRAINED
 
     if args.profile_setup:
         h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)
@@ -525,15 +530,24 @@ def run_gpu(args, rank, world, local_rank):
     traffic = traffic_for("schwarz", args.workload, modes.get(res[-1]["info"]["fused"][0]))
     last = res[-1]
 
-    # end to end through the same API with host buffers (copies inside the timed region)
-    fh = np.ascontiguousarray(f)
-    xh = np.zeros(n)
+    # end to end through the same API with host buffers in page-locked memory (copies inside the
+    # timed region)
+    def pinned(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+    def pinned_csr(M):
+        return (pinned(M.indptr.astype(np.int32)), pinned(M.indices.astype(np.int32)),
+                pinned(M.data.astype(np.float64)), M.shape)
+
+    Ah, Gh = pinned_csr(A), pinned_csr(G)
+    fh = pinned(np.asarray(f, dtype=np.float64))
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        h = amgh.amgh_setup(A, G, precision=prec, **extra)
-        xh[:] = 0.0
+        h = amgh.amgh_setup(Ah, Gh, precision=prec, **extra)
+        xh.zero_()
         amgh.amgh_pcg_solve(h, fh, xh, 1e-8, 2000)
         amgh.amgh_destroy(h)
     barrier()
@@ -548,14 +562,16 @@ def run_gpu(args, rank, world, local_rank):
     amgh.amgh_destroy(hl)
     # the paper's three interpolations on this workload (Sec. 5's comparison): the algebraic one
     # timed above ("Alg"), the refinement-based one ("Ref") and geometric Nedelec ("Geo")
+    # and the local extension corrected to commute (P G_c = 2 G P_n), with either coarse variables
     comparison = None
     if world == 1 and W.CONFIGS[args.workload]["n"] % 4 == 0:
         mesh_n = W.CONFIGS[args.workload]["n"]
         din = (Ad, Gd, fd)
         comparison = {}
-        for label, kw in (("Ref", dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=mesh_n)),
-                          ("Geo", dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=mesh_n,
-                                       interp=amgh.AMGH_INTERP_GEOMETRIC))):
+        ref = dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=mesh_n)
+        for label, kw in (("Ref", ref), ("Geo", dict(ref, interp=amgh.AMGH_INTERP_GEOMETRIC)),
+                          ("Alg+C", dict(interp=amgh.AMGH_INTERP_CONSTRAINED)),
+                          ("Ref+C", dict(ref, interp=amgh.AMGH_INTERP_CONSTRAINED))):
             v = time_variant(amgh, prob, din, args.precision, 3, 1, **kw)
             comparison[label] = {k: v[k] for k in ("s_per_step", "setup_s", "solve_s", "pcg_iters", "relres",
                                                    "converged", "levels", "op_complexity")}
@@ -581,7 +597,7 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": 1000 * t_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "desc": W.describe(args.workload)[0], "n_dofs": n, "nnz": int(A.nnz),
-                   "precision": args.precision, "tol": 1e-8,
+                   "precision": args.precision, "tol": 1e-8, "interp": args.interp,
                    "l2": "inputs larger than L2 (A alone %.0f MB > 129 MB)" % (12 * A.nnz / 1e6),
                    "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
                    "level_precision": [{0: "f64", 1: "f32", 2: "bf16"}[q] for q in info["precision"]],

@@ -73,7 +73,7 @@ enum { AMGH_F64 = 0, AMGH_F32 = 1, AMGH_BF16 = 2 };
  * V-cycles on A x = 0 (x0 ~ U(-1,1), SplitMix64 stream 8, seed 0) and falls back to the exact
  * local solves when rho exceeds 1.1 times the exact solves' factor (params.rho_ref, or measured
  * on an exact setup); amgh_info reports which interpolation was kept. */
-enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1, AMGH_INTERP_GEOMETRIC = 2 };
+enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1, AMGH_INTERP_GEOMETRIC = 2, AMGH_INTERP_CONSTRAINED = 3 };
 
 /* coarse variables: ALGEBRAIC (Section 4: Alg. 1-3 on the nodal dual operator, the default) or
  * REFINEMENT (Section 3, "Ref"): A and G must be the lowest-order Nedelec system of the structured
@@ -85,7 +85,18 @@ enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1, AMGH_INTERP_GEOMETRIC = 2
  * REFINEMENT, interp may also be AMGH_INTERP_GEOMETRIC ("Geo", the comparison of Section 5): the
  * geometric Nedelec interpolation of the coarse mesh, scaled so that its rows on the halves are
  * R^T (a fine edge parallel to its coarse edge one fine step across takes 1/2, two steps 1/4),
- * in place of the local harmonic extensions. */
+ * in place of the local harmonic extensions.
+ *
+ * AMGH_INTERP_CONSTRAINED (either coarsening) corrects the local extensions to satisfy the
+ * commuting relation of Section 2 (Eq. commuting), P G_c = 2 G P_n, which the exact P_app keeps up
+ * to O(beta) (Thm. 3.3) and local patches in 3-D lose; the paper leaves a 3-D localisation open, so
+ * this is an extension beyond it.  P_n is a nodal interpolation built from the splitting: coarse
+ * nodes injected, the middle node of each pair half of each coarse end, every other node the mean
+ * of its neighbours in the previous breadth-first layer and of its boundary edges (zero); on a hex
+ * refinement that is trilinear interpolation.  The exterior rows R^T satisfy the relation as they
+ * are; every interior row of P moves, on its own pattern, to the nearest row (Euclidean) that
+ * satisfies its row of the relation, in least squares where none does.  The pattern of P, and so
+ * the cost of a V-cycle, is unchanged. */
 enum { AMGH_COARSEN_ALGEBRAIC = 0, AMGH_COARSEN_REFINEMENT = 1 };
 
 typedef struct {
@@ -95,7 +106,8 @@ typedef struct {
                              keeps FP64 unless kappa * u <= 1/4 for the largest 1-norm condition
                              estimate kappa of its smoother blocks and the unit roundoff u of the
                              reduced format (BF16 falls back to FP32 first)                     */
-    int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED | AMGH_INTERP_GEOMETRIC     */
+    int interp;           /* AMGH_INTERP_LOCAL | AMGH_INTERP_LEARNED | AMGH_INTERP_GEOMETRIC |
+                             AMGH_INTERP_CONSTRAINED                                            */
     int ring;             /* rings of interior A-neighbours in a truncated patch (>= 1)        */
     int p_max;            /* largest patch of one local harmonic extension (<= 256)            */
     double theta;         /* strength-of-connection threshold of the nodal C/F split (0.25)    */
@@ -267,7 +279,8 @@ typedef struct {
                                (coarsest level: of its matrix); estimated only when a reduced
                                precision is requested, else 0 (coarsest level: always)          */
     int dense_tail;       /* level whose sub-cycle is applied as a dense operator, or -1       */
-    int interp_used;      /* AMGH_INTERP_LOCAL or AMGH_INTERP_LEARNED (after the fallback test) */
+    int interp_used;      /* the interpolation the hierarchy holds (LEARNED only if it passed
+                             the fallback test)                                                 */
     double rho;           /* measured convergence factor of the kept hierarchy (learned setups)  */
     double rho_exact;     /* the exact local solves' factor it was compared with               */
     double interp_ms;     /* wall time of filling the finest level's P values (solves or network) */

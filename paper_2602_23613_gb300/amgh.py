@@ -15,7 +15,7 @@ from . import build as _build
 AMGH_OK, AMGH_ERR_INVALID_ARG, AMGH_ERR_NOT_SPD, AMGH_ERR_NOT_CONVERGED = 0, 1, 2, 3
 AMGH_ERR_CUDA, AMGH_ERR_OOM, AMGH_ERR_TIMEOUT, AMGH_ERR_SETUP_STALL, AMGH_ERR_UNSUPPORTED = 4, 5, 6, 7, 8
 AMGH_F64, AMGH_F32, AMGH_BF16 = 0, 1, 2
-AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED, AMGH_INTERP_GEOMETRIC = 0, 1, 2
+AMGH_INTERP_LOCAL, AMGH_INTERP_LEARNED, AMGH_INTERP_GEOMETRIC, AMGH_INTERP_CONSTRAINED = 0, 1, 2, 3
 AMGH_COARSEN_ALGEBRAIC, AMGH_COARSEN_REFINEMENT = 0, 1
 KIND = {"schwarz": 0, "l1": 1, "residual": 2, "restrict": 3, "prolong": 4, "coarse": 5, "spmv": 6, "rr": 7}
 

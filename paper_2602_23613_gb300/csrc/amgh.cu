@@ -1647,12 +1647,16 @@ static void check_flag(amgh_ctx* h, const char* what) {
     if (flag) throw StatusError{AMGH_ERR_NOT_SPD, std::string("non-positive pivot in ") + what};
 }
 
-static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false) {
+static void check_csr_args(const amgh_csr* M) {
     if (!M || !M->row_ptr || (M->nnz > 0 && (!M->col || !M->val)))
         throw StatusError{AMGH_ERR_INVALID_ARG, "null CSR pointer"};
     if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0 || M->nrows >= INT32_MAX || M->ncols >= INT32_MAX ||
         M->nnz >= INT32_MAX)
         throw StatusError{AMGH_ERR_INVALID_ARG, "CSR dimensions out of range"};
+}
+
+static HostCSR to_host(const amgh_csr* M, cudaStream_t s, bool host_only = false) {
+    check_csr_args(M);
     HostCSR h;
     h.nrows = (int)M->nrows;
     h.ncols = (int)M->ncols;
@@ -1688,7 +1692,8 @@ static void check_params(const amgh_params& prm) {
         prm.p_max > 256 || prm.precision < 0 || prm.precision > 2 || !(prm.theta >= 0.0 && prm.theta <= 1.0) ||
         !(prm.stall_ratio > 0.0) || prm.dense_tail < 0 || prm.dense_tail > 16384)
         throw StatusError{AMGH_ERR_INVALID_ARG, "parameter out of range"};
-    if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED && prm.interp != AMGH_INTERP_GEOMETRIC)
+    if (prm.interp != AMGH_INTERP_LOCAL && prm.interp != AMGH_INTERP_LEARNED && prm.interp != AMGH_INTERP_GEOMETRIC &&
+        prm.interp != AMGH_INTERP_CONSTRAINED)
         throw StatusError{AMGH_ERR_INVALID_ARG, "unknown interpolation mode"};
     if (prm.coarsening != AMGH_COARSEN_ALGEBRAIC && prm.coarsening != AMGH_COARSEN_REFINEMENT)
         throw StatusError{AMGH_ERR_INVALID_ARG, "unknown coarsening mode"};
@@ -1753,6 +1758,24 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
     cudaStream_t s = h->s;
     const auto& prm = h->prm;
     check_params(prm);
+    // A goes to the device straight from the caller's arrays, before the host copy: from
+    // page-locked arrays the transfer then runs while the host copies them
+    check_csr_args(Ain);
+    DevCSR dA;
+    dA.nrows = (int)Ain->nrows;
+    dA.ncols = (int)Ain->ncols;
+    dA.nnz = Ain->nnz;
+    dA.ptr.alloc(dA.nrows + 1);
+    dA.idx.alloc(std::max<int64_t>(1, dA.nnz));
+    dA.val.alloc(std::max<int64_t>(1, dA.nnz));
+    {
+        const cudaMemcpyKind k = Ain->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        AMGH_CUDA(cudaMemcpyAsync(dA.ptr.p, Ain->row_ptr, sizeof(int32_t) * (dA.nrows + 1), k, s));
+        if (dA.nnz) {
+            AMGH_CUDA(cudaMemcpyAsync(dA.idx.p, Ain->col, sizeof(int32_t) * dA.nnz, k, s));
+            AMGH_CUDA(cudaMemcpyAsync(dA.val.p, Ain->val, sizeof(double) * dA.nnz, k, s));
+        }
+    }
     HostCSR A = to_host(Ain, s);
     HostCSR G = to_host(Gin, s);
     ph.mark(s, "inputs to host");
@@ -1770,21 +1793,6 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         int dev = 0;
         AMGH_CUDA(cudaGetDevice(&dev));
         AMGH_CUDA(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
-    }
-    DevCSR dA;
-    if (Ain->on_device) {
-        // the caller's device copy is copied on the device, not sent back from the host
-        dA.nrows = A.nrows;
-        dA.ncols = A.ncols;
-        dA.nnz = A.nnz();
-        dA.ptr.alloc(A.nrows + 1);
-        dA.idx.alloc(std::max<int64_t>(1, dA.nnz));
-        dA.val.alloc(std::max<int64_t>(1, dA.nnz));
-        AMGH_CUDA(cudaMemcpyAsync(dA.ptr.p, Ain->row_ptr, sizeof(int32_t) * (A.nrows + 1), cudaMemcpyDeviceToDevice, s));
-        AMGH_CUDA(cudaMemcpyAsync(dA.idx.p, Ain->col, sizeof(int32_t) * dA.nnz, cudaMemcpyDeviceToDevice, s));
-        AMGH_CUDA(cudaMemcpyAsync(dA.val.p, Ain->val, sizeof(double) * dA.nnz, cudaMemcpyDeviceToDevice, s));
-    } else {
-        upload_csr(A, dA, s, true);
     }
     // level arrays keep their addresses while the engine worker reads finished levels
     const size_t cap = (size_t)prm.max_levels + 1;
@@ -1832,7 +1840,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         ph.mark(s, "host graph steps", l);
         if (coarsest) break;
         t0 = now_ms();
-        double t_stars = 0.0;
+        double t_stars = 0.0, t_comm = 0.0;
         Coarsening& cz = cur.cz;
         const int nc = (int)cz.edges.size();
         h->P64.emplace_back();
@@ -1885,6 +1893,12 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             }
             bool solved = false;
             auto* net = static_cast<amgh_mlp_ctx*>(prm.mlp);
+            // per-row data of the commuting correction (interp CONSTRAINED), alive until the
+            // flag check below has waited for its kernel
+            CommutingRows crow;
+            DevArray<int32_t> dcr_order, dcr_rows, dcr_nptr, dcr_comp, dcr_ptpos;
+            DevArray<int16_t> dcr_ea, dcr_eb;
+            DevArray<double> dcr_t;
             if (!cz.geo_ptr.empty()) {
                 // the geometric interpolation: its weights are set, not solved for
                 std::vector<double> pv(cz.P.nnz(), 0.0), ptv(cz.PT.nnz(), 0.0);
@@ -1918,6 +1932,45 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
                                    h->errflag.p, s);
                 solved = true;
+                if (prm.interp == AMGH_INTERP_CONSTRAINED) {
+                    // Eq. commuting: the host builds the nodal interpolation and every interior
+                    // row's constraint while the solves run; the device then corrects the rows
+                    const double tc = now_ms();
+                    std::string msg = commuting_rows(cur.G, cz, crow, nthreads);
+                    if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+                    // rows grouped by the size class of their local node count
+                    int sizes[8];
+                    const int ncls = commute_size_classes(sizes);
+                    if (crow.max_nodes > sizes[ncls - 1])
+                        throw StatusError{AMGH_ERR_UNSUPPORTED, "a row of the commuting correction touches " +
+                                                                    std::to_string(crow.max_nodes) +
+                                                                    " coarse nodes (at most " +
+                                                                    std::to_string(sizes[ncls - 1]) + ")"};
+                    std::vector<int32_t> order;
+                    order.reserve(crow.rows.size());
+                    int32_t cls_ptr[9] = {0};
+                    for (int c = 0; c < ncls; ++c) {
+                        const int lo = c ? sizes[c - 1] : -1;
+                        for (size_t r = 0; r < crow.rows.size(); ++r) {
+                            const int mr = crow.node_ptr[r + 1] - crow.node_ptr[r];
+                            if (mr > lo && mr <= sizes[c]) order.push_back((int32_t)r);
+                        }
+                        cls_ptr[c + 1] = (int32_t)order.size();
+                    }
+                    t_comm = now_ms() - tc;
+                    h->host_ms += t_comm;
+                    dcr_order.upload(order, s);
+                    dcr_rows.upload(crow.rows, s);
+                    dcr_nptr.upload(crow.node_ptr, s);
+                    dcr_comp.upload(crow.comp, s);
+                    dcr_ptpos.upload(crow.pt_pos, s);
+                    dcr_ea.upload(crow.ea, s);
+                    dcr_eb.upload(crow.eb, s);
+                    dcr_t.upload(crow.t, s);
+                    launch_commute_rows(cls_ptr, dcr_order.p, dcr_rows.p, P.ptr.p, P.val.p, PT.val.p, dcr_ptpos.p,
+                                        dcr_ea.p, dcr_eb.p, dcr_nptr.p, dcr_t.p, dcr_comp.p, h->errflag.p, s);
+                    h->interp_used = AMGH_INTERP_CONSTRAINED;
+                }
             }
             if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             // the smoother's node stars and colouring are host work: built while the solves run
@@ -1928,7 +1981,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 t_stars = now_ms() - ts;
                 h->host_ms += t_stars;
             }
-            if (solved) check_flag(h, "a local harmonic-extension solve");
+            if (solved) check_flag(h, "a local harmonic-extension solve or the commuting correction");
             if (l == 0) {
                 float ms = 0.f;
                 AMGH_CUDA(cudaEventSynchronize(fe.e1));
@@ -1973,7 +2026,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
         AMGH_CUDA(cudaStreamSynchronize(s));
         if (worker) worker->hand_over(l, s);   // level l's P, P^T and stars are final
         if (refine) mesh_n /= 2;
-        h->dev_ms += std::max(0.0, now_ms() - t0 - t_stars);
+        h->dev_ms += std::max(0.0, now_ms() - t0 - t_stars - t_comm);
         ph.mark(s, "Galerkin + download", l);
         A = std::move(An);
         G = cz.Gc;

@@ -1037,4 +1037,243 @@ std::string build_stars(const HostCSR& A, const HostCSR& G, StarLayout& L) {
     return "";
 }
 
+// ---- Eq. commuting: nodal interpolation and the per-row data of the least-distance correction ----
+std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows& out, int nthreads) {
+    PhaseClock clk;
+    const int n = G.nrows, m = G.ncols;
+    const HostCSR& P = cz.P;
+    const HostCSR& PT = cz.PT;
+    const HostCSR& Gc = cz.Gc;
+    const int nc = (int)cz.edges.size();
+    const int ncn = Gc.ncols;
+    if (P.nrows != n || PT.nrows != nc || Gc.nrows != nc || (int)G.val.size() != (int)G.nnz())
+        return "internal: commuting rows need G with values and the patterns of P, P^T and G_c";
+    std::vector<int32_t> col(m, -1);
+    for (size_t q = 0; q < cz.coarse_nodes.size(); ++q) col[cz.coarse_nodes[q]] = (int32_t)q;
+    typedef std::pair<int32_t, double> Entry;
+
+    // P_n: rows in a pool (row v at pool[off[v] .. off[v] + len[v]), ascending coarse node),
+    // appended layer by layer
+    std::vector<int64_t> off(m, 0);
+    std::vector<int32_t> len(m, 0), layer(m, -1);
+    std::vector<Entry> pool;
+    pool.reserve((size_t)8 * m);
+    for (int v = 0; v < m; ++v)
+        if (col[v] >= 0) {
+            layer[v] = 0;
+            off[v] = (int64_t)pool.size();
+            len[v] = 1;
+            pool.emplace_back(col[v], 1.0);
+        }
+    for (const auto& e : cz.edges) {
+        if (e.k < 0 || e.k >= m) continue;
+        if (layer[e.k] == 0) return "internal: a middle node is a coarse node or the middle of two pairs";
+        layer[e.k] = 0;
+        Entry row[2];
+        int nr = 0;
+        for (int32_t end : {e.i, e.j})
+            if (end >= 0 && end < m && col[end] >= 0) row[nr++] = Entry(col[end], 0.5);
+        if (nr == 2 && row[0].first == row[1].first) {
+            row[0].second = 1.0;
+            nr = 1;
+        }
+        if (nr == 2 && row[1].first < row[0].first) std::swap(row[0], row[1]);
+        off[e.k] = (int64_t)pool.size();
+        len[e.k] = nr;
+        for (int t = 0; t < nr; ++t) pool.push_back(row[t]);
+    }
+    HostCSR GT = transpose_pattern(G, false, nthreads);   // node -> its rows of G
+    auto other_end = [&](int32_t row, int32_t v) -> int32_t {
+        const int32_t a = G.ptr[row], b = G.ptr[row + 1];
+        if (b - a != 2) return -1;   // a boundary edge: its other end is artificial (zero)
+        return G.idx[a] == v ? G.idx[a + 1] : G.idx[a];
+    };
+    std::vector<int32_t> front;
+    for (int v = 0; v < m; ++v)
+        if (layer[v] == 0) front.push_back(v);
+    const int nth = std::max(1, nthreads);
+    std::vector<std::vector<Entry>> tbuf(nth);
+    for (int d = 1; !front.empty(); ++d) {
+        std::vector<int32_t> next;
+        for (int32_t v : front)
+            for (int32_t q = GT.ptr[v]; q < GT.ptr[v + 1]; ++q) {
+                const int32_t w = other_end(GT.idx[q], v);
+                if (w >= 0 && layer[w] < 0) {
+                    layer[w] = d;
+                    next.push_back(w);
+                }
+            }
+        std::sort(next.begin(), next.end());
+        // each new row: the mean over the previous layer's neighbours and the boundary edges,
+        // built per thread, then appended to the pool
+        std::vector<int32_t> bthread(next.size());
+        std::vector<int64_t> boff(next.size());
+        for (auto& b : tbuf) b.clear();
+#pragma omp parallel num_threads(nth)
+        {
+            const int tid = thread_id();
+            std::vector<Entry>& buf = tbuf[tid];
+            std::vector<Entry> acc;
+#pragma omp for schedule(dynamic, 512)
+            for (size_t a = 0; a < next.size(); ++a) {
+                const int32_t u = next[a];
+                acc.clear();
+                int cnt = 0;
+                for (int32_t q = GT.ptr[u]; q < GT.ptr[u + 1]; ++q) {
+                    const int32_t w = other_end(GT.idx[q], u);
+                    if (w < 0) {
+                        ++cnt;
+                    } else if (layer[w] == d - 1) {
+                        ++cnt;
+                        for (int64_t t = off[w]; t < off[w] + len[w]; ++t) acc.push_back(pool[t]);
+                    }
+                }
+                std::sort(acc.begin(), acc.end(),
+                          [](const Entry& x, const Entry& y) { return x.first < y.first; });
+                bthread[a] = tid;
+                boff[a] = (int64_t)buf.size();
+                size_t k = 0;
+                while (k < acc.size()) {
+                    double sum = 0.0;
+                    const int32_t c = acc[k].first;
+                    for (; k < acc.size() && acc[k].first == c; ++k) sum += acc[k].second;
+                    buf.emplace_back(c, sum / cnt);
+                }
+                len[u] = (int32_t)(buf.size() - boff[a]);
+            }
+        }
+        for (size_t a = 0; a < next.size(); ++a) {
+            const int32_t u = next[a];
+            const Entry* src = tbuf[bthread[a]].data() + boff[a];
+            off[u] = (int64_t)pool.size();
+            pool.insert(pool.end(), src, src + len[u]);
+        }
+        front = std::move(next);
+    }
+    {
+        HostCSR& Pn = out.Pn;
+        Pn.nrows = m;
+        Pn.ncols = ncn;
+        Pn.ptr.assign(m + 1, 0);
+        for (int v = 0; v < m; ++v) Pn.ptr[v + 1] = Pn.ptr[v] + len[v];
+        Pn.idx.resize(Pn.ptr[m]);
+        Pn.val.resize(Pn.ptr[m]);
+#pragma omp parallel for schedule(static) num_threads(nth)
+        for (int v = 0; v < m; ++v)
+            for (int32_t t = 0; t < len[v]; ++t) {
+                Pn.idx[Pn.ptr[v] + t] = pool[off[v] + t].first;
+                Pn.val[Pn.ptr[v] + t] = pool[off[v] + t].second;
+            }
+    }
+    clk.mark("commuting: nodal interp.");
+    const HostCSR& Pn = out.Pn;
+
+    // positions in P^T of every entry of P (rows of P sorted by column)
+    out.pt_pos.assign(P.nnz(), -1);
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nth)
+    for (int c = 0; c < nc; ++c)
+        for (int32_t t = PT.ptr[c]; t < PT.ptr[c + 1]; ++t) {
+            const int32_t i = PT.idx[t];
+            const int32_t* b = P.idx.data() + P.ptr[i];
+            const int32_t* e = P.idx.data() + P.ptr[i + 1];
+            out.pt_pos[std::lower_bound(b, e, c) - P.idx.data()] = t;
+        }
+    std::vector<char> ext(n, 0);
+    for (const auto& e : cz.edges) ext[e.d1] = ext[e.d2] = 1;
+    out.rows.clear();
+    for (int i = 0; i < n; ++i)
+        if (!ext[i] && P.ptr[i + 1] > P.ptr[i]) out.rows.push_back(i);
+    const size_t nr = out.rows.size();
+    clk.mark("commuting: P^T positions");
+
+    // local nodes of a row: the coarse nodes its pattern's G_c rows touch, ascending; first into
+    // slots of 2 per entry, then compacted
+    std::vector<int64_t> slot(nr + 1, 0);
+    for (size_t r = 0; r < nr; ++r) slot[r + 1] = slot[r] + 2 * (P.ptr[out.rows[r] + 1] - P.ptr[out.rows[r]]);
+    std::vector<int32_t> wide(slot[nr]);
+    out.node_ptr.assign(nr + 1, 0);
+    clk.mark("commuting: slots");
+#pragma omp parallel for schedule(dynamic, 1024) num_threads(nth)
+    for (size_t r = 0; r < nr; ++r) {
+        const int32_t i = out.rows[r];
+        int32_t* nodes = wide.data() + slot[r];
+        int k = 0;
+        for (int32_t q = P.ptr[i]; q < P.ptr[i + 1]; ++q)
+            for (int32_t t = Gc.ptr[P.idx[q]]; t < Gc.ptr[P.idx[q] + 1]; ++t) nodes[k++] = Gc.idx[t];
+        std::sort(nodes, nodes + k);
+        out.node_ptr[r + 1] = (int32_t)(std::unique(nodes, nodes + k) - nodes);
+    }
+    int mx = 0;
+    for (size_t r = 0; r < nr; ++r) {
+        mx = std::max(mx, out.node_ptr[r + 1]);
+        out.node_ptr[r + 1] += out.node_ptr[r];
+    }
+    out.max_nodes = mx;
+    clk.mark("commuting: sorted nodes");
+    if (mx > 32000) return "a row of the commuting correction touches too many coarse nodes";
+    out.t.assign(out.node_ptr[nr], 0.0);
+    out.comp.assign(out.node_ptr[nr], -1);
+    out.ea.assign(P.nnz(), 0);
+    out.eb.assign(P.nnz(), 0);
+    clk.mark("commuting: node lists");
+#pragma omp parallel num_threads(nth)
+    {
+        std::vector<int32_t> parent;
+        std::vector<char> grounded;
+#pragma omp for schedule(dynamic, 1024)
+        for (size_t r = 0; r < nr; ++r) {
+            const int32_t i = out.rows[r];
+            const int32_t* nodes = wide.data() + slot[r];
+            const int nl = out.node_ptr[r + 1] - out.node_ptr[r];
+            auto loc = [&](int32_t u) { return (int32_t)(std::lower_bound(nodes, nodes + nl, u) - nodes); };
+            // t = row i of 2 G P_n on the local nodes
+            double* t = out.t.data() + out.node_ptr[r];
+            for (int32_t q = G.ptr[i]; q < G.ptr[i + 1]; ++q) {
+                const int32_t v = G.idx[q];
+                const double g = G.val[q];
+                for (int32_t e = Pn.ptr[v]; e < Pn.ptr[v + 1]; ++e) {
+                    const int32_t l = loc(Pn.idx[e]);
+                    if (l < nl && nodes[l] == Pn.idx[e]) t[l] += 2.0 * g * Pn.val[e];
+                }
+            }
+            // the signed local ends of every entry, and the components of the local graph
+            parent.resize(nl);
+            std::iota(parent.begin(), parent.end(), 0);
+            grounded.assign(nl, 0);
+            auto find = [&](int32_t x) {
+                while (parent[x] != x) x = parent[x] = parent[parent[x]];
+                return x;
+            };
+            for (int32_t q = P.ptr[i]; q < P.ptr[i + 1]; ++q) {
+                const int32_t c = P.idx[q];
+                int32_t ends[2] = {-1, -1};
+                int ne = 0;
+                for (int32_t t2 = Gc.ptr[c]; t2 < Gc.ptr[c + 1] && ne < 2; ++t2) {
+                    const int32_t l = loc(Gc.idx[t2]);
+                    const int sg = Gc.val[t2] > 0 ? 1 : -1;
+                    (ne == 0 ? out.ea[q] : out.eb[q]) = (int16_t)(sg * (l + 1));
+                    ends[ne++] = l;
+                }
+                if (ne == 2) {
+                    int32_t x = find(ends[0]), y = find(ends[1]);
+                    if (x != y) {
+                        if (x > y) std::swap(x, y);
+                        parent[y] = x;   // the smaller root stays: a root is its component's first node
+                        grounded[x] = grounded[x] | grounded[y];
+                    }
+                } else if (ne == 1) {
+                    grounded[find(ends[0])] = 1;
+                }
+            }
+            int32_t* comp = out.comp.data() + out.node_ptr[r];
+            for (int u = 0; u < nl; ++u) {
+                const int32_t root = find(u);
+                comp[u] = grounded[root] ? -1 : root;
+            }
+        }
+    }
+    clk.mark("commuting: row data");
+    return "";
+}
+
 }  // namespace amgh

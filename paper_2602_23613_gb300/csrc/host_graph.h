@@ -71,6 +71,35 @@ std::string coarsen_level(const HostCSR& A, const HostCSR& G, const Params& prm,
 std::string coarsen_level_refinement(const HostCSR& A, const HostCSR& G, int mesh_n, bool geometric,
                                      const Params& prm, Coarsening& out, int nthreads);
 
+// Eq. commuting: the local extension corrected to commute --------------------------------------
+// The nodal interpolation P_n maps the nodes (columns of G) to the coarse nodes: a coarse node is
+// injected; the middle node k of a pair (i, k, j) takes half of each end that is a coarse node;
+// every other node, in breadth-first layers of the incidence graph from those nodes, takes the
+// mean over its neighbours in the previous layer and its boundary edges (one-entry rows of G,
+// whose artificial ends carry zero).  With R's rows (+-1, +-1) the exterior rows R^T of P satisfy
+// P G_c = 2 G P_n; every interior row of P is moved, on its own pattern, to the nearest row that
+// satisfies row i of it (least squares where none does).  Per interior row this holds what the
+// device needs for that least-distance problem: its local nodes (the coarse nodes its pattern's
+// G_c rows touch, ascending), the target t = row i of 2 G P_n on them, and which local nodes form
+// components that no one-ended G_c row of the pattern grounds (their residual is matched only up
+// to its mean there, and their first node is left out of the solve).
+struct CommutingRows {
+    int max_nodes = 0;
+    std::vector<int32_t> rows;       // interior rows of P with a nonempty pattern, ascending
+    std::vector<int32_t> node_ptr;   // rows.size() + 1: local nodes of each row
+    std::vector<double> t;           // per local node: row i of 2 G P_n there
+    std::vector<int32_t> comp;       // per local node: first local node of its component when
+                                     // nothing grounds the component, else -1
+    std::vector<int16_t> ea, eb;     // per entry of P: the local ends of the entry's G_c row as
+                                     // (local index + 1) * sign, 0 for none
+    std::vector<int32_t> pt_pos;     // per entry of P: its position in P^T
+    HostCSR Pn;                      // the nodal interpolation (columns of G x coarse nodes)
+};
+
+// needs cz's edges, coarse nodes, G_c and the patterns of P and P^T (from coarsen_level or
+// coarsen_level_refinement); returns "" or an error message
+std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows& out, int nthreads);
+
 // Smoother structure (node stars of G and their colouring) -------------------------------------
 struct StarLayout {
     int nstars = 0, ncolours = 0, max_block = 0;

@@ -16,6 +16,18 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
                         const int32_t* patch_idx, const int64_t* pos_P, const int64_t* pos_PT,
                         double* Pval, double* PTval, int max_patch, int* err_flag, cudaStream_t s);
 
+// Eq. commuting: each listed interior row of P (values after the local solves) moved on its own
+// pattern to the nearest row satisfying row i of P G_c = 2 G P_n, from the host-built per-row data
+// (see CommutingRows); P^T's copy follows.  Rows go by size class: order[class_ptr[c] ..
+// class_ptr[c+1]) lists the rows (indices into rows) with at most sizes[c] local nodes, sizes from
+// commute_size_classes (ascending; returns their number, 4).  A non-positive pivot, or a row
+// larger than its class, sets *err_flag.  class_ptr is a host array.
+int commute_size_classes(int* sizes);
+void launch_commute_rows(const int32_t* class_ptr, const int32_t* order, const int32_t* rows, const int32_t* Pptr,
+                         double* Pval, double* PTval, const int32_t* pt_pos, const int16_t* ea, const int16_t* eb,
+                         const int32_t* node_ptr, const double* t, const int32_t* comp, int* err_flag,
+                         cudaStream_t s);
+
 // Galerkin product A_c = P^T (A P) on given symbolic patterns (Eq. tl), FP64, deterministic order.
 // symbolic Z = X Y on the device (sorted columns per row); false when a row overflows the
 // kernel's shared-memory set (the caller then computes the pattern on the host)

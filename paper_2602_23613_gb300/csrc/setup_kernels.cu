@@ -404,6 +404,146 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
     }
 }
 
+// Eq. commuting: every interior row p of P (the local extension) moved, on its own pattern, to
+// the nearest row satisfying p C = t, C the pattern's rows of G_c on the row's local nodes and t
+// row i of 2 G P_n (host-built).  The least-distance change is C y with C^T C y = r, r = t - p C
+// taken to the range of C^T C: its mean is removed on every component of the local graph that no
+// one-ended row grounds, whose first node is then left out (y = 0 there); C^T C (small integer
+// entries) is factored by Cholesky.  One thread per row, its packed matrix and vector in its own
+// slice of shared memory; rows come grouped by their number of local nodes, one launch per size
+// class M, with as many threads per CTA as M's slices fit in about 140 KB.
+namespace {
+
+constexpr int COMMUTE_SIZES[4] = {16, 32, 64, 128};
+
+__host__ __device__ constexpr int commute_slice(int M) { return M * (M + 1) / 2 + M; }
+__host__ __device__ constexpr int commute_threads(int M) { return M <= 16 ? 64 : (M <= 32 ? 32 : (M <= 64 ? 8 : 2)); }
+
+template <int M>
+__global__ void __launch_bounds__(commute_threads(M)) commute_rows_kernel(
+    int count, const int32_t* __restrict__ order, const int32_t* __restrict__ rows, const int32_t* __restrict__ Pptr,
+    double* __restrict__ Pval, double* __restrict__ PTval, const int32_t* __restrict__ pt_pos,
+    const int16_t* __restrict__ ea, const int16_t* __restrict__ eb, const int32_t* __restrict__ node_ptr,
+    const double* __restrict__ tt, const int32_t* __restrict__ comp, int* err_flag) {
+    extern __shared__ double commute_shm[];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int r = order[k];
+    const int i = rows[r];
+    const int q0 = Pptr[i], q1 = Pptr[i + 1];
+    const int n0 = node_ptr[r], m = node_ptr[r + 1] - n0;
+    if (m > M) {   // the host groups rows by size; anything else is an internal error
+        atomicExch(err_flag, 1);
+        return;
+    }
+    const int32_t* cp = comp + n0;
+    double* L = commute_shm + (size_t)threadIdx.x * commute_slice(M);
+    double* y = L + M * (M + 1) / 2;
+    for (int u = 0; u < m; ++u) y[u] = tt[n0 + u];
+    for (int q = q0; q < q1; ++q) {
+        const double p = Pval[q];
+        const int a = ea[q], b = eb[q];
+        if (a) y[(a > 0 ? a : -a) - 1] -= a > 0 ? p : -p;
+        if (b) y[(b > 0 ? b : -b) - 1] -= b > 0 ? p : -p;
+    }
+    for (int u = 0; u < m; ++u) {
+        if (cp[u] != u) continue;   // not the first node of an ungrounded component
+        double sum = 0.0;
+        int cnt = 0;
+        for (int v = u; v < m; ++v)
+            if (cp[v] == u) {
+                sum += y[v];
+                ++cnt;
+            }
+        const double mean = sum / cnt;
+        for (int v = u; v < m; ++v)
+            if (cp[v] == u) y[v] -= mean;
+    }
+    auto at = [](int a, int b) { return a >= b ? a * (a + 1) / 2 + b : b * (b + 1) / 2 + a; };
+    for (int t = 0; t < m * (m + 1) / 2; ++t) L[t] = 0.0;
+    for (int q = q0; q < q1; ++q) {
+        const int a = ea[q], b = eb[q];
+        const int la = a ? (a > 0 ? a : -a) - 1 : -1, lb = b ? (b > 0 ? b : -b) - 1 : -1;
+        const bool ua = la >= 0 && cp[la] != la, ub = lb >= 0 && cp[lb] != lb;   // in the solve
+        if (ua) L[at(la, la)] += 1.0;
+        if (ub) L[at(lb, lb)] += 1.0;
+        if (ua && ub) L[at(la, lb)] += (a > 0) == (b > 0) ? 1.0 : -1.0;
+    }
+    for (int u = 0; u < m; ++u)
+        if (cp[u] == u) {
+            L[at(u, u)] = 1.0;
+            y[u] = 0.0;
+        }
+    // Cholesky L = F F^T in place, then F F^T y = r
+    for (int j = 0; j < m; ++j) {
+        double d = L[at(j, j)];
+        for (int t = 0; t < j; ++t) d -= L[at(j, t)] * L[at(j, t)];
+        if (!(d > 0.0)) {
+            atomicExch(err_flag, 1);
+            return;
+        }
+        const double f = sqrt(d);
+        L[at(j, j)] = f;
+        for (int a = j + 1; a < m; ++a) {
+            double v = L[at(a, j)];
+            for (int t = 0; t < j; ++t) v -= L[at(a, t)] * L[at(j, t)];
+            L[at(a, j)] = v / f;
+        }
+    }
+    for (int a = 0; a < m; ++a) {
+        double v = y[a];
+        for (int t = 0; t < a; ++t) v -= L[at(a, t)] * y[t];
+        y[a] = v / L[at(a, a)];
+    }
+    for (int a = m - 1; a >= 0; --a) {
+        double v = y[a];
+        for (int t = a + 1; t < m; ++t) v -= L[at(t, a)] * y[t];
+        y[a] = v / L[at(a, a)];
+    }
+    for (int q = q0; q < q1; ++q) {
+        const int a = ea[q], b = eb[q];
+        double p = Pval[q];
+        if (a) p += a > 0 ? y[a - 1] : -y[-a - 1];
+        if (b) p += b > 0 ? y[b - 1] : -y[-b - 1];
+        Pval[q] = p;
+        PTval[pt_pos[q]] = p;
+    }
+}
+
+template <int M>
+void commute_launch(int count, const int32_t* order, const int32_t* rows, const int32_t* Pptr, double* Pval,
+                    double* PTval, const int32_t* pt_pos, const int16_t* ea, const int16_t* eb,
+                    const int32_t* node_ptr, const double* t, const int32_t* comp, int* err_flag, cudaStream_t s) {
+    if (count == 0) return;
+    constexpr int T = commute_threads(M);
+    const size_t shm = sizeof(double) * (size_t)T * commute_slice(M);
+    AMGH_CUDA(cudaFuncSetAttribute(commute_rows_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    commute_rows_kernel<M><<<(count + T - 1) / T, T, shm, s>>>(count, order, rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                                                               node_ptr, t, comp, err_flag);
+    AMGH_LAUNCHED();
+}
+
+}  // namespace
+
+int commute_size_classes(int* sizes) {
+    for (int c = 0; c < 4; ++c) sizes[c] = COMMUTE_SIZES[c];
+    return 4;
+}
+
+void launch_commute_rows(const int32_t* class_ptr, const int32_t* order, const int32_t* rows, const int32_t* Pptr,
+                         double* Pval, double* PTval, const int32_t* pt_pos, const int16_t* ea, const int16_t* eb,
+                         const int32_t* node_ptr, const double* t, const int32_t* comp, int* err_flag,
+                         cudaStream_t s) {
+    commute_launch<16>(class_ptr[1] - class_ptr[0], order + class_ptr[0], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                       node_ptr, t, comp, err_flag, s);
+    commute_launch<32>(class_ptr[2] - class_ptr[1], order + class_ptr[1], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                       node_ptr, t, comp, err_flag, s);
+    commute_launch<64>(class_ptr[3] - class_ptr[2], order + class_ptr[2], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                       node_ptr, t, comp, err_flag, s);
+    commute_launch<128>(class_ptr[4] - class_ptr[3], order + class_ptr[3], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                        node_ptr, t, comp, err_flag, s);
+}
+
 // Symbolic sparse product Z = X Y, one CTA per row of Z: the candidate columns (Y's rows selected
 // by the row of X) go into a shared-memory hash set; the count pass writes each row's number of
 // distinct columns, the fill pass writes them in ascending order (each key's rank is the number of
