@@ -1932,55 +1932,74 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 launch_patch_solve(h->A64[l], nc, de4.p, dpp.p, dpi.p, dpos.p, dpost.p, P.val.p, PT.val.p, maxp,
                                    h->errflag.p, s);
                 solved = true;
-                if (prm.interp == AMGH_INTERP_CONSTRAINED) {
-                    // Eq. commuting: the host builds the nodal interpolation and every interior
-                    // row's constraint while the solves run; the device then corrects the rows
-                    const double tc = now_ms();
-                    std::string msg = commuting_rows(cur.G, cz, crow, nthreads);
-                    if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
-                    // rows grouped by the size class of their local node count
-                    int sizes[8];
-                    const int ncls = commute_size_classes(sizes);
-                    if (crow.max_nodes > sizes[ncls - 1])
-                        throw StatusError{AMGH_ERR_UNSUPPORTED, "a row of the commuting correction touches " +
-                                                                    std::to_string(crow.max_nodes) +
-                                                                    " coarse nodes (at most " +
-                                                                    std::to_string(sizes[ncls - 1]) + ")"};
-                    std::vector<int32_t> order;
-                    order.reserve(crow.rows.size());
-                    int32_t cls_ptr[9] = {0};
-                    for (int c = 0; c < ncls; ++c) {
-                        const int lo = c ? sizes[c - 1] : -1;
-                        for (size_t r = 0; r < crow.rows.size(); ++r) {
-                            const int mr = crow.node_ptr[r + 1] - crow.node_ptr[r];
-                            if (mr > lo && mr <= sizes[c]) order.push_back((int32_t)r);
-                        }
-                        cls_ptr[c + 1] = (int32_t)order.size();
-                    }
-                    t_comm = now_ms() - tc;
-                    h->host_ms += t_comm;
-                    dcr_order.upload(order, s);
-                    dcr_rows.upload(crow.rows, s);
-                    dcr_nptr.upload(crow.node_ptr, s);
-                    dcr_comp.upload(crow.comp, s);
-                    dcr_ptpos.upload(crow.pt_pos, s);
-                    dcr_ea.upload(crow.ea, s);
-                    dcr_eb.upload(crow.eb, s);
-                    dcr_t.upload(crow.t, s);
-                    launch_commute_rows(cls_ptr, dcr_order.p, dcr_rows.p, P.ptr.p, P.val.p, PT.val.p, dcr_ptpos.p,
-                                        dcr_ea.p, dcr_eb.p, dcr_nptr.p, dcr_t.p, dcr_comp.p, h->errflag.p, s);
-                    h->interp_used = AMGH_INTERP_CONSTRAINED;
-                }
             }
-            if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
+            // Eq. commuting (interp CONSTRAINED): the nodal interpolation and every interior row's
+            // constraint are built on a helper thread while this one builds the smoother's stars
+            // and the solves run; the device then corrects the rows
+            const bool commute = solved && prm.interp == AMGH_INTERP_CONSTRAINED;
+            std::string comm_msg;
+            std::vector<int32_t> order;
+            int32_t cls_ptr[9] = {0};
+            int sizes[8];
+            const int ncls = commute_size_classes(sizes);
+            struct Joiner {
+                std::thread t;
+                ~Joiner() {
+                    if (t.joinable()) t.join();
+                }
+            } comm;
+            if (commute)
+                comm.t = std::thread([&] {
+                    try {
+                        comm_msg = commuting_rows(cur.G, cz, crow, nthreads);
+                        if (comm_msg.empty() && crow.max_nodes > sizes[ncls - 1])
+                            comm_msg = "a row of the commuting correction touches " + std::to_string(crow.max_nodes) +
+                                       " coarse nodes (at most " + std::to_string(sizes[ncls - 1]) + ")";
+                        if (!comm_msg.empty()) return;
+                        // rows grouped by the size class of their local node count
+                        order.reserve(crow.rows.size());
+                        for (int c = 0; c < ncls; ++c) {
+                            const int lo = c ? sizes[c - 1] : -1;
+                            for (size_t r = 0; r < crow.rows.size(); ++r) {
+                                const int mr = crow.node_ptr[r + 1] - crow.node_ptr[r];
+                                if (mr > lo && mr <= sizes[c]) order.push_back((int32_t)r);
+                            }
+                            cls_ptr[c + 1] = (int32_t)order.size();
+                        }
+                    } catch (const std::exception& e) {
+                        comm_msg = std::string("commuting correction: ") + e.what();
+                    }
+                });
             // the smoother's node stars and colouring are host work: built while the solves run
             {
                 const double ts = now_ms();
                 std::string msg = build_stars(cur.A, cur.G, cur.stars);
-                if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
                 t_stars = now_ms() - ts;
                 h->host_ms += t_stars;
+                if (!msg.empty()) {
+                    if (comm.t.joinable()) comm.t.join();
+                    throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+                }
             }
+            if (commute) {
+                const double tc = now_ms();
+                comm.t.join();
+                if (!comm_msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, comm_msg};
+                t_comm = now_ms() - tc;   // what the helper thread took beyond the stars
+                h->host_ms += t_comm;
+                dcr_order.upload(order, s);
+                dcr_rows.upload(crow.rows, s);
+                dcr_nptr.upload(crow.node_ptr, s);
+                dcr_comp.upload(crow.comp, s);
+                dcr_ptpos.upload(crow.pt_pos, s);
+                dcr_ea.upload(crow.ea, s);
+                dcr_eb.upload(crow.eb, s);
+                dcr_t.upload(crow.t, s);
+                launch_commute_rows(cls_ptr, dcr_order.p, dcr_rows.p, P.ptr.p, P.val.p, PT.val.p, dcr_ptpos.p,
+                                    dcr_ea.p, dcr_eb.p, dcr_nptr.p, dcr_t.p, dcr_comp.p, h->errflag.p, s);
+                h->interp_used = AMGH_INTERP_CONSTRAINED;
+            }
+            if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             if (solved) check_flag(h, "a local harmonic-extension solve or the commuting correction");
             if (l == 0) {
                 float ms = 0.f;

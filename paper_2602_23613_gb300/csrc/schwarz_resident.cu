@@ -107,7 +107,8 @@ __device__ __forceinline__ int2 rs_id(const int2* __restrict__ items, int i, int
 // Grid-wide barrier of the pipelined sweep: each CTA adds one to a counter (zeroed before the
 // launch) with release semantics and thread 0 polls it with acquire loads until all CTAs of
 // barrier `round` have arrived.  The wait is bounded: after SPIN_LIMIT polls it raises the abort
-// word and the error flag; a CTA that sees the abort word gives up too.  False when it gave up.
+// word and the error flag; a CTA that sees the abort word (read every 16th poll) gives up too.
+// False when it gave up.
 constexpr long long RS_SPIN_LIMIT = 1ll << 20;
 
 __device__ __forceinline__ unsigned rs_ld_acquire(const unsigned* p) {
@@ -125,7 +126,8 @@ __device__ __forceinline__ bool rs_grid_sync(const GridBarrier& b, unsigned roun
         const unsigned target = round * gridDim.x;
         long long it = 0;
         while (rs_ld_acquire(b.count) < target) {
-            if (rs_ld_acquire(b.abort) != 0u || ++it > RS_SPIN_LIMIT) {
+            // the abort word is read on every 16th poll only, so the poll loop issues one load
+            if ((++it & 15) == 0 && (rs_ld_acquire(b.abort) != 0u || it > RS_SPIN_LIMIT)) {
                 atomicExch(b.abort, 1u);
                 atomicExch(b.err, 1);
                 good = 0;
