@@ -480,7 +480,10 @@ def interpolation_constrained(P, G, Gc, Pn, edges):
         Cd = C[:, nodes].toarray()
         t = T[i][:, nodes].toarray().ravel()
         p0 = P.data[a:b]
-        data[a:b] = p0 + (t - p0 @ Cd) @ np.linalg.pinv(Cd)
+        # C_i is a +-1 incidence block whose rank is structural: its nonzero singular values are
+        # at least 1/k for k nodes, its zero ones come out of the SVD as rounding noise (up to
+        # ~1e-13 sigma_max), so the pseudo-inverse cuts at 1e-8 sigma_max
+        data[a:b] = p0 + (t - p0 @ Cd) @ np.linalg.pinv(Cd, rcond=1e-8)
     return sp.csr_matrix((data, P.indices.copy(), P.indptr.copy()), shape=P.shape)
 
 

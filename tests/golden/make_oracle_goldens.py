@@ -16,6 +16,9 @@ PCG solve of the workload's right-hand side to 1e-8 (iterations, residual histor
 sampled entries of x).
 
 Usage: python tests/golden/make_oracle_goldens.py hex64_checker   (about an hour on one core)
+       python tests/golden/make_oracle_goldens.py hex64_checker constrained
+           (the local extension corrected to commute, readings R10-R11; written to
+           tests/golden/hex64_checker_constrained.json)
 """
 import hashlib
 import json
@@ -77,12 +80,12 @@ def max_cond(A, blocks):
     return worst
 
 
-def main(name, out_path=None):
+def main(name, interp="local", out_path=None):
     t0 = time.time()
     p = W.make_config(name)
     print("inputs %.1f s" % (time.time() - t0), flush=True)
     t = time.time()
-    H = O.setup(p["A"], p["G"])
+    H = O.setup(p["A"], p["G"], interp=interp)
     t_setup = time.time() - t
     print("oracle setup %.1f s, levels %s" % (t_setup, [L["A"].shape[0] for L in H]), flush=True)
     rng = np.random.default_rng(20260101)
@@ -119,10 +122,10 @@ def main(name, out_path=None):
                energy=float(p["f"] @ x), inf_norm=float(np.abs(x).max()),
                idx=[int(i) for i in idx[:1024]], values=[float(x[i]) for i in idx[:1024]])
     out = dict(workload=name, description=W.describe(name)[0], generator="tests/golden/make_oracle_goldens.py",
-               params=dict(coarse_size=100, p_max=128, ring=1, strength="classical", theta=0.25),
+               params=dict(coarse_size=100, p_max=128, ring=1, strength="classical", theta=0.25, interp=interp),
                oracle_seconds=dict(setup=t_setup, vcycle=t_vc, pcg=t_pcg),
                levels=levels, vcycle=vcyc, pcg=pcg)
-    out_path = out_path or os.path.join(HERE, name + ".json")
+    out_path = out_path or os.path.join(HERE, name + ("" if interp == "local" else "_" + interp) + ".json")
     with open(out_path, "w") as fh:
         json.dump(out, fh, indent=None, separators=(",", ":"))
         fh.write("\n")
@@ -130,4 +133,5 @@ def main(name, out_path=None):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "hex64_checker", sys.argv[2] if len(sys.argv) > 2 else None)
+    main(sys.argv[1] if len(sys.argv) > 1 else "hex64_checker", sys.argv[2] if len(sys.argv) > 2 else "local",
+         sys.argv[3] if len(sys.argv) > 3 else None)

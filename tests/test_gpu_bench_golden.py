@@ -1,7 +1,9 @@
 """Parity on the benchmark's own workload (64^3 checkerboard, 762,048 DoFs), against the oracle's
 values stored by tests/golden/make_oracle_goldens.py (the oracle needs most of an hour for this
 size, so its results are stored, not recomputed).  The library is set up exactly as bench.py sets
-it up (default parameters).
+it up (default parameters), and once more with the commuting correction of the local extension
+(interp CONSTRAINED, bench.py --interp constrained) against that form's golden; its P values may
+differ by twice the local solves' tolerance plus 1e-13 (see test_gpu_constrained.py).
 
   * structure: SHA-256 digests of every level's C/F state, coarse edges with signs, coarse nodes,
     patches, star colours and the patterns of A_l and P_l, bit-exact;
@@ -25,7 +27,8 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-GOLDEN = os.path.join(HERE, "golden", "hex64_checker.json")
+GOLDENS = {"local": os.path.join(HERE, "golden", "hex64_checker.json"),
+           "constrained": os.path.join(HERE, "golden", "hex64_checker_constrained.json")}
 TOL = 1e-12
 EPS = np.finfo(np.float64).eps
 
@@ -35,9 +38,14 @@ def digest(arr, dtype):
                           .tobytes()).hexdigest()
 
 
+@pytest.fixture(scope="module", params=list(GOLDENS))
+def form(request):
+    return request.param
+
+
 @pytest.fixture(scope="module")
-def gold():
-    return json.load(open(GOLDEN))
+def gold(form):
+    return json.load(open(GOLDENS[form]))
 
 
 @pytest.fixture(scope="module")
@@ -52,17 +60,25 @@ def amgh():
 
 
 @pytest.fixture(scope="module")
-def bench_handle(amgh):
-    p = W.make_config("hex64_checker")
-    h = amgh.amgh_setup(p["A"], p["G"])
-    return p, h
+def problem():
+    return W.make_config("hex64_checker")
+
+
+@pytest.fixture(scope="module")
+def bench_handle(amgh, problem, form):
+    kw = {} if form == "local" else dict(interp=amgh.AMGH_INTERP_CONSTRAINED)
+    h = amgh.amgh_setup(problem["A"], problem["G"], **kw)
+    return problem, h
 
 
 def level_tols(gold):
+    constrained = gold["params"].get("interp", "local") == "constrained"
     out, prev_p = [], TOL
     for l, g in enumerate(gold["levels"]):
-        t = dict(smooth=max(TOL, 8 * EPS * g["kappa_star"]), P=max(TOL, 8 * EPS * g.get("kappa_patch", 1.0)),
-                 A=max(TOL, 2 * prev_p))
+        tp = max(TOL, 8 * EPS * g.get("kappa_patch", 1.0))
+        if constrained:
+            tp = 2 * tp + 1e-13
+        t = dict(smooth=max(TOL, 8 * EPS * g["kappa_star"]), P=tp, A=max(TOL, 2 * prev_p))
         out.append(t)
         prev_p = t["P"] if l == 0 else max(t["P"], t["A"])
     return out

@@ -92,7 +92,7 @@ def test_each_row_is_the_nearest_on_its_pattern(pair):
         t = T[i].toarray().ravel()
         k, m = C.shape
         K = np.block([[np.eye(k), C], [C.T, np.zeros((m, m))]])
-        sol = np.linalg.lstsq(K, np.concatenate([Pl[i, S].toarray().ravel(), t]), rcond=None)[0]
+        sol = np.linalg.lstsq(K, np.concatenate([Pl[i, S].toarray().ravel(), t]), rcond=1e-10)[0]
         assert np.allclose(sol[:k] @ C, t, rtol=0, atol=1e-12), (name, i)
         np.testing.assert_allclose(Pc[i, S].toarray().ravel(), sol[:k], rtol=0, atol=1e-12)
 
@@ -133,3 +133,43 @@ def test_three_dimensional_convergence():
     print("16^3 checkerboard PCG iterations:", its)
     assert its["constrained"] <= its["local"] - 3
     assert its["ref constrained"] <= its["local"] - 3
+
+
+def test_rank_of_the_row_block_is_structural():
+    """A row whose block C (an incidence block of 27 coarse edges on 27 coarse nodes: one
+    ungrounded component plus a node only the target touches, so two exact zero singular values,
+    one of which the SVD returns as ~2e-14) met on the 64^3 checkerboard's third level: the
+    correction must equal the structural least-squares solution (mean of the residual removed on
+    the component, the untouched node dropped, one node pinned, the graph Laplacian solved) and
+    stay bounded, where a default pseudo-inverse cutoff keeps the noise and returns 1e13."""
+    ends = [(1, 11), (2, 14), (3, 15), (4, 16), (5, 9), (6, 10), (7, 11), (8, 9), (9, 10), (9, 14), (9, 21),
+            (10, 11), (10, 15), (10, 22), (11, 12), (11, 16), (11, 23), (13, 14), (14, 15), (14, 18), (14, 24),
+            (15, 16), (15, 19), (15, 25), (16, 17), (16, 20), (16, 26)]
+    p0 = np.array([0.0667232, 1.55595e-05, 0.374158, 0.125761, 1.87685e-06, 5.10011e-06, 6.86364e-06,
+                   -3.27861e-07, -2.50915e-06, 0.00329235, 0.0013778, -0.0103606, -0.00638136, 0.0146981,
+                   -1.55354e-06, 0.000105693, 0.0131414, 1.40856e-07, -0.0493808, -0.00309791, -0.00103133,
+                   -0.0174202, 0.0164795, 0.0221993, -2.25032e-06, 0.00330395, 0.00683052])
+    k, m = len(ends), 27
+    C = np.zeros((k, m))
+    for e, (u, v) in enumerate(ends):
+        C[e, u], C[e, v] = -1.0, 1.0
+    Gc = sp.csr_matrix(C)
+    # fine row 0 (interior) with all 27 coarse edges in its pattern; fine row 1 holds the pairs
+    P = sp.csr_matrix((p0, (np.zeros(k, int), np.arange(k))), shape=(2, k))
+    G = sp.csr_matrix(np.array([[-1.0, 1.0], [0.0, 1.0]]))
+    Pn = sp.csr_matrix(np.array([[0.25 if c in (0, 3) else 0.0 for c in range(m)],
+                                 [0.25 if c in (10, 15) else 0.0 for c in range(m)]]))
+    edges = [(1, 1.0, 1, 1.0, -1, -1, -1)]
+    t = 2.0 * (G @ Pn).toarray()[0]
+    out = O.interpolation_constrained(P, G, Gc, Pn, edges).toarray()[0]
+    # structural solution: nodes 1..26 form one ungrounded component, node 0 is untouched
+    r = t - p0 @ C
+    comp = np.arange(1, m)
+    r_c = r[comp] - r[comp].mean()
+    act = comp[1:]                        # node 1 pinned
+    L = C.T @ C
+    y = np.zeros(m)
+    y[act] = np.linalg.solve(L[np.ix_(act, act)], r_c[1:])
+    want = p0 + C @ y
+    assert np.abs(out).max() < 10.0
+    np.testing.assert_allclose(out, want, rtol=0, atol=1e-12)
