@@ -170,7 +170,8 @@ amgh_status amgh_setup(const amgh_csr* A, const amgh_csr* G, const amgh_params* 
  * the smoother stars and colouring of level 0 on the host and makes no CUDA call (A and G must be
  * host CSR).  On the returned handle only amgh_level_structure(h, 0, ...), amgh_level_matrix(h,
  * 0, which) (which = 1 returns P's pattern with the exterior +-1 and zeros elsewhere; which = 3
- * returns the symbolic pattern of P^T A P with zero values), amgh_last_error and amgh_destroy are
+ * returns the symbolic pattern of P^T A P with zero values; which = 4 the nodal interpolation of
+ * the commuting correction when interp is CONSTRAINED), amgh_last_error and amgh_destroy are
  * valid; every other call returns INVALID_ARG.  Errors as amgh_setup. */
 amgh_status amgh_setup_host_structure(const amgh_csr* A, const amgh_csr* G, const amgh_params* params,
                                       amgh_handle* out);
@@ -309,7 +310,10 @@ amgh_status amgh_level_structure(amgh_handle h, int l, int64_t* n_nodes_aug, int
 
 /* Copy a level matrix to host CSR arrays (FP64 values as computed on the device).
  * which = 0: A_l (n_l x n_l); 1: P_l (n_l x n_{l+1}); 2: G_l (n_l x m_l); 3: the symbolic pattern
- * of P_l^T A_l P_l with the device values of A_{l+1} (zeros on a structure-only handle).
+ * of P_l^T A_l P_l with the device values of A_{l+1} (zeros on a structure-only handle); 4: the
+ * nodal interpolation P_n of Eq. commuting that the commuting correction used on level l (m_l x
+ * coarse nodes, host-computed; interp CONSTRAINED only, on a structure-only handle too, else
+ * INVALID_ARG).
  * Query form: pass row_ptr = col = val = NULL to receive nrows, ncols, nnz only. */
 amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, int64_t* ncols,
                               int64_t* nnz, int32_t* row_ptr, int32_t* col, double* val);

@@ -337,7 +337,8 @@ def amgh_level_structure(h, l):
 
 
 def amgh_level_matrix(h, l, which):
-    """Level matrix as scipy CSR: which = 0 A_l, 1 P_l, 2 G_l, 3 P_l^T A_l P_l (symbolic pattern)."""
+    """Level matrix as scipy CSR: which = 0 A_l, 1 P_l, 2 G_l, 3 P_l^T A_l P_l (symbolic pattern),
+    4 the nodal interpolation of the commuting correction (interp CONSTRAINED)."""
     import scipy.sparse as sp
     Lb = load()
     nr, nc, nz = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)

@@ -1751,6 +1751,12 @@ static void host_structure_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr
     if (cur.cz.edges.empty()) throw StatusError{AMGH_ERR_SETUP_STALL, "the finest level produced no coarse edge"};
     msg = build_stars(cur.A, cur.G, cur.stars);
     if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+    if (h->prm.interp == AMGH_INTERP_CONSTRAINED) {
+        CommutingRows crow;
+        msg = commuting_rows(cur.G, cur.cz, crow, host_threads());
+        if (!msg.empty()) throw StatusError{AMGH_ERR_UNSUPPORTED, msg};
+        cur.Pn = std::move(crow.Pn);
+    }
 }
 
 static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
@@ -1998,6 +2004,7 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                 launch_commute_rows(cls_ptr, dcr_order.p, dcr_rows.p, P.ptr.p, P.val.p, PT.val.p, dcr_ptpos.p,
                                     dcr_ea.p, dcr_eb.p, dcr_nptr.p, dcr_t.p, dcr_comp.p, h->errflag.p, s);
                 h->interp_used = AMGH_INTERP_CONSTRAINED;
+                cur.Pn = std::move(crow.Pn);
             }
             if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             if (solved) check_flag(h, "a local harmonic-extension solve or the commuting correction");
@@ -3123,14 +3130,16 @@ amgh_status amgh_level_structure(amgh_handle h, int l, int64_t* n_nodes_aug, int
 
 amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, int64_t* ncols, int64_t* nnz,
                               int32_t* row_ptr, int32_t* col, double* val) {
-    if (!h || l < 0 || l >= (int)h->hl.size() || which < 0 || which > 3) return AMGH_ERR_INVALID_ARG;
+    if (!h || l < 0 || l >= (int)h->hl.size() || which < 0 || which > 4) return AMGH_ERR_INVALID_ARG;
     const bool has_coarse = h->structure_only || l + 1 < (int)h->hl.size();
     if ((which == 1 || which == 3) && !has_coarse) return AMGH_ERR_INVALID_ARG;
+    if (which == 4 && h->hl[l].Pn.ptr.empty()) return AMGH_ERR_INVALID_ARG;
     return guarded(h, [&] {
         const auto& L = h->hl[l];
         const HostCSR& M = which == 0 ? L.A
                            : which == 1 ? L.cz.P
                            : which == 2 ? L.G
+                           : which == 4 ? L.Pn
                            : (h->structure_only ? L.cz.Ac : h->hl[l + 1].A);
         if (nrows) *nrows = M.nrows;
         if (ncols) *ncols = M.ncols;
@@ -3138,7 +3147,7 @@ amgh_status amgh_level_matrix(amgh_handle h, int l, int which, int64_t* nrows, i
         if (row_ptr) std::memcpy(row_ptr, M.ptr.data(), M.ptr.size() * 4);
         if (col) std::memcpy(col, M.idx.data(), M.idx.size() * 4);
         if (val) {
-            if (which == 2 || (h->structure_only && which != 3)) {
+            if (which == 2 || which == 4 || (h->structure_only && which != 3)) {
                 std::memcpy(val, M.val.data(), M.val.size() * 8);
             } else if (h->structure_only) {
                 std::memset(val, 0, sizeof(double) * M.nnz());

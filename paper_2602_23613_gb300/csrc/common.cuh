@@ -106,6 +106,7 @@ struct LevelHost {
     HostCSR G;
     Coarsening cz;        // empty on the coarsest level
     StarLayout stars;
+    HostCSR Pn;           // nodal interpolation of the commuting correction (interp CONSTRAINED)
 };
 
 }  // namespace amgh

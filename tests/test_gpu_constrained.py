@@ -87,8 +87,15 @@ def test_hierarchy_matches_oracle(amgh, con):
         np.testing.assert_array_equal(P.indptr, cz["P"].indptr)
         np.testing.assert_array_equal(P.indices, cz["P"].indices)
         assert rel(P.data, cz["P"].data, "constrained %s P_%d" % (name, l)) < tols[l]["P"]
-        # the library's own P satisfies the relation (with the oracle's P_n: the structure is equal)
+        # the library's nodal interpolation is the oracle's
         G = sp.csr_matrix(H[l]["G"])
+        Pn = amgh.amgh_level_matrix(h, l, 4)
+        want = sp.csr_matrix(cz["Pn"][:G.shape[1]])
+        want.eliminate_zeros()
+        np.testing.assert_array_equal(Pn.indptr, want.indptr)
+        np.testing.assert_array_equal(Pn.indices, want.indices)
+        np.testing.assert_allclose(Pn.data, want.data, rtol=1e-15, atol=0)
+        # the library's own P satisfies the relation (with the oracle's P_n: the structure is equal)
         d = abs(sp.csr_matrix(P) @ cz["Gc"] - 2.0 * (G @ cz["Pn"][:G.shape[1]])).max()
         print("constrained %s level %d: max |P G_c - 2 G P_n| = %.2e" % (name, l, d))
         assert d <= 1e-12 + 4 * tols[l]["P"] * abs(cz["P"]).max()

@@ -198,3 +198,40 @@ def test_refinement_rejects_bad_meshes(amgh):
     with pytest.raises(amgh.AmghError) as e:
         amgh.amgh_setup_host_structure(p["A"], p["G"], interp=amgh.AMGH_INTERP_GEOMETRIC)
     assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("case", ["hex8_unit", "hex12_lognormal", "tri16", "hex8_ref", "hex16_checker"])
+def test_commuting_nodal_interpolation_matches_oracle(amgh, case):
+    """The nodal interpolation P_n of the commuting correction (reading R10) from the library's
+    host code against the oracle's: pattern bit for bit, values to 1e-15 (the library sums a
+    layer's neighbours, then divides; the oracle scales, then sums); on the hex refinement it is
+    the trilinear interpolation the oracle's pin fixes."""
+    kw, okw = {}, {}
+    if case == "hex8_unit":
+        p = W.make_config("hex8_unit")
+    elif case == "hex12_lognormal":
+        p = W.hex_problem(12, W.fields.log_uniform(12, 3, lo=-2, hi=2), 0.1)
+    elif case == "tri16":
+        p = W.tri_problem(16, 1.0, 0.01)
+    elif case == "hex8_ref":
+        p = W.hex_problem(8, 1.0, 1.0)
+        kw = dict(coarsening=amgh.AMGH_COARSEN_REFINEMENT, mesh_n=8)
+        okw = dict(splitting="refinement", mesh_n=8)
+    else:
+        p = W.make_config("hex16_checker")
+    h = amgh.amgh_setup_host_structure(p["A"], p["G"], interp=amgh.AMGH_INTERP_CONSTRAINED, **kw)
+    Pn = amgh.amgh_level_matrix(h, 0, 4)
+    cz = O.coarsen(p["A"], p["G"], interp="constrained", **okw)
+    m = p["G"].shape[1]
+    want = sp.csr_matrix(cz["Pn"][:m])
+    want.sort_indices()
+    want.eliminate_zeros()
+    assert Pn.shape == want.shape
+    np.testing.assert_array_equal(Pn.indptr, want.indptr)
+    np.testing.assert_array_equal(Pn.indices, want.indices)
+    np.testing.assert_allclose(Pn.data, want.data, rtol=1e-15, atol=0)
+    # without the correction there is no P_n to read
+    h0 = amgh.amgh_setup_host_structure(p["A"], p["G"], **kw)
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_level_matrix(h0, 0, 4)
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
