@@ -1052,12 +1052,13 @@ std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows
     for (size_t q = 0; q < cz.coarse_nodes.size(); ++q) col[cz.coarse_nodes[q]] = (int32_t)q;
     typedef std::pair<int32_t, double> Entry;
 
-    // P_n: rows in a pool (row v at pool[off[v] .. off[v] + len[v]), ascending coarse node),
-    // appended layer by layer
-    std::vector<int64_t> off(m, 0);
+    // P_n row by row (ascending coarse node): row v at rowp[v], len[v] entries; layer 0 in `pool`,
+    // every later layer in its own per-thread buffers
     std::vector<int32_t> len(m, 0), layer(m, -1);
+    std::vector<const Entry*> rowp(m, nullptr);
+    std::vector<int64_t> off(m, 0);
     std::vector<Entry> pool;
-    pool.reserve((size_t)8 * m);
+    pool.reserve((size_t)m + 2 * cz.edges.size());
     for (int v = 0; v < m; ++v)
         if (col[v] >= 0) {
             layer[v] = 0;
@@ -1082,33 +1083,44 @@ std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows
         len[e.k] = nr;
         for (int t = 0; t < nr; ++t) pool.push_back(row[t]);
     }
+    for (int v = 0; v < m; ++v)
+        if (layer[v] == 0) rowp[v] = pool.data() + off[v];
     HostCSR GT = transpose_pattern(G, false, nthreads);   // node -> its rows of G
     auto other_end = [&](int32_t row, int32_t v) -> int32_t {
         const int32_t a = G.ptr[row], b = G.ptr[row + 1];
         if (b - a != 2) return -1;   // a boundary edge: its other end is artificial (zero)
         return G.idx[a] == v ? G.idx[a + 1] : G.idx[a];
     };
-    std::vector<int32_t> front;
-    for (int v = 0; v < m; ++v)
-        if (layer[v] == 0) front.push_back(v);
     const int nth = std::max(1, nthreads);
-    std::vector<std::vector<Entry>> tbuf(nth);
-    for (int d = 1; !front.empty(); ++d) {
-        std::vector<int32_t> next;
-        for (int32_t v : front)
-            for (int32_t q = GT.ptr[v]; q < GT.ptr[v + 1]; ++q) {
-                const int32_t w = other_end(GT.idx[q], v);
-                if (w >= 0 && layer[w] < 0) {
-                    layer[w] = d;
-                    next.push_back(w);
+    std::vector<std::vector<std::vector<Entry>>> layer_bufs;
+    for (int d = 1;; ++d) {
+        // layer d: the unassigned nodes next to layer d - 1, found by a scan in node order (each
+        // thread a contiguous range, so the concatenation is ascending)
+        std::vector<std::vector<int32_t>> found(nth);
+#pragma omp parallel num_threads(nth)
+        {
+            const int tid = thread_id();
+            const int64_t lo = (int64_t)m * tid / nth, hi = (int64_t)m * (tid + 1) / nth;
+            for (int64_t u = lo; u < hi; ++u) {
+                if (layer[u] >= 0) continue;
+                for (int32_t q = GT.ptr[u]; q < GT.ptr[u + 1]; ++q) {
+                    const int32_t w = other_end(GT.idx[q], (int32_t)u);
+                    if (w >= 0 && layer[w] == d - 1) {
+                        found[tid].push_back((int32_t)u);
+                        break;
+                    }
                 }
             }
-        std::sort(next.begin(), next.end());
-        // each new row: the mean over the previous layer's neighbours and the boundary edges,
-        // built per thread, then appended to the pool
+        }
+        std::vector<int32_t> next;
+        for (const auto& f : found) next.insert(next.end(), f.begin(), f.end());
+        if (next.empty()) break;
+        for (int32_t w : next) layer[w] = d;
+        // each new row: the mean over the previous layer's neighbours and the boundary edges
+        layer_bufs.emplace_back(nth);
+        auto& tbuf = layer_bufs.back();
         std::vector<int32_t> bthread(next.size());
         std::vector<int64_t> boff(next.size());
-        for (auto& b : tbuf) b.clear();
 #pragma omp parallel num_threads(nth)
         {
             const int tid = thread_id();
@@ -1125,7 +1137,7 @@ std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows
                         ++cnt;
                     } else if (layer[w] == d - 1) {
                         ++cnt;
-                        for (int64_t t = off[w]; t < off[w] + len[w]; ++t) acc.push_back(pool[t]);
+                        acc.insert(acc.end(), rowp[w], rowp[w] + len[w]);
                     }
                 }
                 std::sort(acc.begin(), acc.end(),
@@ -1142,13 +1154,8 @@ std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows
                 len[u] = (int32_t)(buf.size() - boff[a]);
             }
         }
-        for (size_t a = 0; a < next.size(); ++a) {
-            const int32_t u = next[a];
-            const Entry* src = tbuf[bthread[a]].data() + boff[a];
-            off[u] = (int64_t)pool.size();
-            pool.insert(pool.end(), src, src + len[u]);
-        }
-        front = std::move(next);
+        // the buffers are complete: their rows' addresses stay fixed from here on
+        for (size_t a = 0; a < next.size(); ++a) rowp[next[a]] = tbuf[bthread[a]].data() + boff[a];
     }
     {
         HostCSR& Pn = out.Pn;
@@ -1161,8 +1168,8 @@ std::string commuting_rows(const HostCSR& G, const Coarsening& cz, CommutingRows
 #pragma omp parallel for schedule(static) num_threads(nth)
         for (int v = 0; v < m; ++v)
             for (int32_t t = 0; t < len[v]; ++t) {
-                Pn.idx[Pn.ptr[v] + t] = pool[off[v] + t].first;
-                Pn.val[Pn.ptr[v] + t] = pool[off[v] + t].second;
+                Pn.idx[Pn.ptr[v] + t] = rowp[v][t].first;
+                Pn.val[Pn.ptr[v] + t] = rowp[v][t].second;
             }
     }
     clk.mark("commuting: nodal interp.");

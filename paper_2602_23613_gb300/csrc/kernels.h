@@ -20,7 +20,7 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
 // pattern to the nearest row satisfying row i of P G_c = 2 G P_n, from the host-built per-row data
 // (see CommutingRows); P^T's copy follows.  Rows go by size class: order[class_ptr[c] ..
 // class_ptr[c+1]) lists the rows (indices into rows) with at most sizes[c] local nodes, sizes from
-// commute_size_classes (ascending; returns their number, 4).  A non-positive pivot, or a row
+// commute_size_classes (ascending; returns their number, 5).  A non-positive pivot, or a row
 // larger than its class, sets *err_flag.  class_ptr is a host array.
 int commute_size_classes(int* sizes);
 void launch_commute_rows(const int32_t* class_ptr, const int32_t* order, const int32_t* rows, const int32_t* Pptr,

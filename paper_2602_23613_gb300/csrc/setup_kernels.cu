@@ -411,13 +411,16 @@ void launch_patch_solve(const DevCSR& A, int nc, const int32_t* edges4, const in
 // one-ended row grounds, whose first node is then left out (y = 0 there); C^T C (small integer
 // entries) is factored by Cholesky.  One thread per row, its packed matrix and vector in its own
 // slice of shared memory; rows come grouped by their number of local nodes, one launch per size
-// class M, with as many threads per CTA as M's slices fit in about 140 KB.
+// class M (8 to 128), with as many threads per CTA as keep one or two CTAs per SM.
 namespace {
 
-constexpr int COMMUTE_SIZES[4] = {16, 32, 64, 128};
+constexpr int COMMUTE_SIZES[5] = {8, 16, 32, 64, 128};
 
 __host__ __device__ constexpr int commute_slice(int M) { return M * (M + 1) / 2 + M; }
-__host__ __device__ constexpr int commute_threads(int M) { return M <= 16 ? 64 : (M <= 32 ? 32 : (M <= 64 ? 8 : 2)); }
+// threads per CTA: two CTAs' slices (about 70-140 KB each) per SM where they fit
+__host__ __device__ constexpr int commute_threads(int M) {
+    return M <= 8 ? 256 : (M <= 16 ? 64 : (M <= 32 ? 24 : (M <= 64 ? 8 : 2)));
+}
 
 template <int M>
 __global__ void __launch_bounds__(commute_threads(M)) commute_rows_kernel(
@@ -526,21 +529,23 @@ void commute_launch(int count, const int32_t* order, const int32_t* rows, const 
 }  // namespace
 
 int commute_size_classes(int* sizes) {
-    for (int c = 0; c < 4; ++c) sizes[c] = COMMUTE_SIZES[c];
-    return 4;
+    for (int c = 0; c < 5; ++c) sizes[c] = COMMUTE_SIZES[c];
+    return 5;
 }
 
 void launch_commute_rows(const int32_t* class_ptr, const int32_t* order, const int32_t* rows, const int32_t* Pptr,
                          double* Pval, double* PTval, const int32_t* pt_pos, const int16_t* ea, const int16_t* eb,
                          const int32_t* node_ptr, const double* t, const int32_t* comp, int* err_flag,
                          cudaStream_t s) {
-    commute_launch<16>(class_ptr[1] - class_ptr[0], order + class_ptr[0], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+    commute_launch<8>(class_ptr[1] - class_ptr[0], order + class_ptr[0], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+                      node_ptr, t, comp, err_flag, s);
+    commute_launch<16>(class_ptr[2] - class_ptr[1], order + class_ptr[1], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
                        node_ptr, t, comp, err_flag, s);
-    commute_launch<32>(class_ptr[2] - class_ptr[1], order + class_ptr[1], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+    commute_launch<32>(class_ptr[3] - class_ptr[2], order + class_ptr[2], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
                        node_ptr, t, comp, err_flag, s);
-    commute_launch<64>(class_ptr[3] - class_ptr[2], order + class_ptr[2], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+    commute_launch<64>(class_ptr[4] - class_ptr[3], order + class_ptr[3], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
                        node_ptr, t, comp, err_flag, s);
-    commute_launch<128>(class_ptr[4] - class_ptr[3], order + class_ptr[3], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
+    commute_launch<128>(class_ptr[5] - class_ptr[4], order + class_ptr[4], rows, Pptr, Pval, PTval, pt_pos, ea, eb,
                         node_ptr, t, comp, err_flag, s);
 }
 
