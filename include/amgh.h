@@ -341,13 +341,21 @@ amgh_status amgh_kernel_stats(amgh_handle h, int64_t* launches, double* total_ms
  * replay counts every kernel it runs); the handle argument may be NULL. */
 int64_t amgh_launch_count(amgh_handle h);
 
-/* ---- learned interpolation weights (a 3-layer perceptron, width 64, FP32, trained on the GPU) ----
+/* ---- learned interpolation weights (a 3-layer perceptron, width 64, FP32 or BF16 storage,
+ * trained on the GPU) ----
  * Input per finest-level coarse edge: 3 features per patch slot (64 slots) plus 2, from A alone
  * (signed log magnitudes, normalised by A[DoF1, DoF1], of the slot's diagonal, of the local
  * right-hand side of Eq. sparseP and of its coupling inside the patch); output: the patch values
  * of the edge's column of P.  Training target: the exact local solves; loss: masked mean squared
  * error; optimiser: Adam. */
 amgh_status amgh_mlp_create(uint64_t seed, amgh_mlp* out);   /* Glorot-uniform init, stream 7   */
+/* storage of the network's products: AMGH_F32 (the default) or AMGH_BF16, where the inputs, the
+ * weight matrices and the hidden activations are held as bfloat16 (nearest, ties to even) and
+ * every product accumulates in FP32; biases, outputs, gradients, the Adam state and the master
+ * weights (what amgh_mlp_params reads and writes) stay FP32.  Applies to every later prediction,
+ * gradient and training step, and to setups that use the network.  INVALID_ARG for any other
+ * value. */
+amgh_status amgh_mlp_set_precision(amgh_mlp m, int precision);
 /* append the finest-level samples (features, exact patch values) of a hierarchy built with exact
  * local solves (patches of at most 64 DoFs) to the network's device-resident training set */
 amgh_status amgh_mlp_add_samples(amgh_mlp m, amgh_handle h);

@@ -16,6 +16,11 @@ Definitions (the library implements the same ones independently):
   * Network: h1 = relu(X W1 + b1), h2 = relu(h1 W2 + b2), y = h2 W3 + b3 (width 64).
   * Loss: sum over the batch of sum_q mask (y - t)^2, divided by the number of used slots.
   * Adam (Kingma and Ba, 2015) with beta1 = 0.9, beta2 = 0.999, eps = 1e-8, bias-corrected.
+  * BF16 storage (precision="bf16"): the network's inputs, the weight matrices W1, W2, W3 and the
+    hidden activations h1, h2 are held as bfloat16 (each the float32 value rounded to the nearest
+    bfloat16, ties to even); biases, pre-activations, outputs, gradients and the Adam state stay at
+    full precision, and the gradients are taken with the stored (rounded) operands.  The FP32
+    master weights are what Adam updates.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -75,25 +80,45 @@ def init_params(u01, d_in=D_IN, width=WIDTH, d_out=M_IN):
     return params
 
 
-def forward(params, X):
+def to_bf16(x):
+    """The nearest bfloat16 (ties to even) of x's float32 rounding, as a float64 array: a bfloat16
+    is the upper 16 bits of a float32, so the float32 bit pattern is rounded at bit 16."""
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _storage(precision):
+    if precision == "fp32":
+        return lambda v: v
+    if precision == "bf16":
+        return to_bf16
+    raise ValueError("precision must be 'fp32' or 'bf16'")
+
+
+def forward(params, X, precision="fp32"):
+    """y and the stored intermediates (X, z1, h1, z2, h2, W1, W2, W3 as the products used them)."""
+    q = _storage(precision)
     W1, b1, W2, b2, W3, b3 = params
+    X, W1, W2, W3 = q(X), q(W1), q(W2), q(W3)
     z1 = X @ W1 + b1
-    h1 = np.maximum(z1, 0.0)
+    h1 = q(np.maximum(z1, 0.0))
     z2 = h1 @ W2 + b2
-    h2 = np.maximum(z2, 0.0)
+    h2 = q(np.maximum(z2, 0.0))
     y = h2 @ W3 + b3
-    return y, (X, z1, h1, z2, h2)
+    return y, (X, z1, h1, z2, h2, W1, W2, W3)
 
 
-def loss(params, X, T, M):
-    y, _ = forward(params, X)
+def loss(params, X, T, M, precision="fp32"):
+    y, _ = forward(params, X, precision)
     return float(((y - T) ** 2 * M).sum() / max(M.sum(), 1.0))
 
 
-def backward(params, X, T, M):
-    """Loss and the gradients of every parameter (the chain rule written out by hand)."""
-    W1, b1, W2, b2, W3, b3 = params
-    y, (X, z1, h1, z2, h2) = forward(params, X)
+def backward(params, X, T, M, precision="fp32"):
+    """Loss and the gradients of every parameter (the chain rule written out by hand), taken with
+    the operands as stored."""
+    y, (X, z1, h1, z2, h2, W1, W2, W3) = forward(params, X, precision)
     nrm = max(M.sum(), 1.0)
     L = float(((y - T) ** 2 * M).sum() / nrm)
     dy = 2.0 * (y - T) * M / nrm

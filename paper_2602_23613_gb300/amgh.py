@@ -52,7 +52,7 @@ EXPORTS = ["amgh_default_params", "amgh_setup", "amgh_batch_setup", "amgh_setup_
            "amgh_amg_solve", "amgh_info",
            "amgh_level_structure", "amgh_level_matrix", "amgh_level_apply", "amgh_profile", "amgh_kernel_stats",
            "amgh_launch_count", "amgh_last_error", "amgh_destroy",
-           "amgh_mlp_create", "amgh_mlp_add_samples", "amgh_mlp_num_samples", "amgh_mlp_train", "amgh_mlp_params",
+           "amgh_mlp_create", "amgh_mlp_set_precision", "amgh_mlp_add_samples", "amgh_mlp_num_samples", "amgh_mlp_train", "amgh_mlp_params",
            "amgh_mlp_loss_grad", "amgh_mlp_predict", "amgh_mlp_features", "amgh_mlp_last_error", "amgh_mlp_destroy",
            "amgh_selftest_wait_timeout"]
 _NOT_STATUS = ("amgh_default_params", "amgh_launch_count", "amgh_last_error", "amgh_destroy", "amgh_mlp_num_samples",
@@ -101,6 +101,7 @@ def load():
     L.amgh_destroy.restype = None
     U64 = ctypes.c_uint64
     L.amgh_mlp_create.argtypes = [U64, ctypes.POINTER(P)]
+    L.amgh_mlp_set_precision.argtypes = [P, I]
     L.amgh_mlp_add_samples.argtypes = [P, P]
     L.amgh_mlp_num_samples.argtypes = [P]
     L.amgh_mlp_num_samples.restype = I64
@@ -418,6 +419,11 @@ def amgh_mlp_create(seed=0):
     out = ctypes.c_void_p()
     _mcheck(load().amgh_mlp_create(seed, ctypes.byref(out)), None)
     return Mlp(out.value)
+
+
+def amgh_mlp_set_precision(m, precision):
+    """AMGH_F32 or AMGH_BF16 storage of the network's products (see include/amgh.h)."""
+    _mcheck(load().amgh_mlp_set_precision(m.ptr, precision), m)
 
 
 def amgh_mlp_add_samples(m, h):

@@ -3273,6 +3273,14 @@ amgh_status amgh_mlp_train(amgh_mlp m, int epochs, int batch, double lr, uint64_
     });
 }
 
+amgh_status amgh_mlp_set_precision(amgh_mlp m, int precision) {
+    if (!m || (precision != AMGH_F32 && precision != AMGH_BF16)) return AMGH_ERR_INVALID_ARG;
+    return mlp_guarded(m, [&] {
+        m->net.bf16 = precision == AMGH_BF16;
+        return AMGH_OK;
+    });
+}
+
 amgh_status amgh_mlp_params(amgh_mlp m, float* out, float* in, int64_t* count) {
     if (!m) return AMGH_ERR_INVALID_ARG;
     return mlp_guarded(m, [&] {

@@ -1,7 +1,7 @@
 // Learned interpolation weights: features of a coarse edge's local problem, a 3-layer perceptron
-// (FP32, width 64) with hand-written forward/backward/Adam kernels, and the scatter of predicted
-// patch values into P.  The layers are small dense products (batch x 194 x 64): plain tiled FP32
-// kernels, deterministic summation order.
+// (width 64; FP32, or BF16 storage with FP32 accumulation) with hand-written forward/backward/Adam
+// kernels, and the scatter of predicted patch values into P.  The layers are small dense products
+// (batch x 194 x 64): plain tiled kernels with FP32 accumulation, deterministic summation order.
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -23,11 +23,22 @@ __global__ void init_layer_kernel(float* W, int fi, int fo, uint64_t seed, uint6
     W[t] = (float)((2.0 * draw01(seed, off + (uint64_t)t) - 1.0) * lim);
 }
 
-// C (Mr x N, row-major) = A B (+ bias[col]) (relu), A(i,k) = A[i a_rs + k a_cs], B(k,j) = B[k b_rs + j b_cs]
-template <bool RELU>
-__global__ void gemm_kernel(int Mr, int N, int K, const float* __restrict__ A, int64_t a_rs, int64_t a_cs,
-                            const float* __restrict__ B, int64_t b_rs, int64_t b_cs, const float* __restrict__ bias,
-                            float* __restrict__ Zout, float* __restrict__ C) {
+__device__ __forceinline__ float ldf(const float* p, int64_t i) { return p[i]; }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void stf(float* p, int64_t i, float v) { p[i] = v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, int64_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+
+__global__ void to_bf16_kernel(int64_t n, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = __float2bfloat16_rn(in[t]);
+}
+
+// C (Mr x N, row-major) = A B (+ bias[col]) (relu), A(i,k) = A[i a_rs + k a_cs], B(k,j) = B[k b_rs + j b_cs];
+// operands FP32 or BF16, FP32 accumulation, C stored in its type (BF16: rounded to nearest even)
+template <class TA, class TB, class TC, bool RELU>
+__global__ void gemm_kernel(int Mr, int N, int K, const TA* __restrict__ A, int64_t a_rs, int64_t a_cs,
+                            const TB* __restrict__ B, int64_t b_rs, int64_t b_cs, const float* __restrict__ bias,
+                            float* __restrict__ Zout, TC* __restrict__ C) {
     __shared__ float As[16][17];
     __shared__ float Bs[16][17];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -35,8 +46,8 @@ __global__ void gemm_kernel(int Mr, int N, int K, const float* __restrict__ A, i
     float acc = 0.f;
     for (int k0 = 0; k0 < K; k0 += 16) {
         const int ka = k0 + tx, kb = k0 + ty;
-        As[ty][tx] = (row < Mr && ka < K) ? A[row * a_rs + ka * a_cs] : 0.f;
-        Bs[ty][tx] = (kb < K && col < N) ? B[kb * b_rs + col * b_cs] : 0.f;
+        As[ty][tx] = (row < Mr && ka < K) ? ldf(A, row * a_rs + ka * a_cs) : 0.f;
+        Bs[ty][tx] = (kb < K && col < N) ? ldf(B, kb * b_rs + col * b_cs) : 0.f;
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
@@ -45,7 +56,7 @@ __global__ void gemm_kernel(int Mr, int N, int K, const float* __restrict__ A, i
     if (row < Mr && col < N) {
         const float z = acc + (bias ? bias[col] : 0.f);
         if (Zout) Zout[(int64_t)row * N + col] = z;
-        C[(int64_t)row * N + col] = RELU ? fmaxf(z, 0.f) : z;
+        stf(C, (int64_t)row * N + col, RELU ? fmaxf(z, 0.f) : z);
     }
 }
 
@@ -179,12 +190,25 @@ __global__ void scatter_kernel(int c0, int nc, const int32_t* __restrict__ pptr,
     }
 }
 
-template <bool RELU>
-void gemm(int Mr, int N, int K, const float* A, int64_t a_rs, int64_t a_cs, const float* B, int64_t b_rs,
-          int64_t b_cs, const float* bias, float* Zout, float* C, cudaStream_t s) {
+template <bool RELU, class TA, class TB, class TC>
+void gemm(int Mr, int N, int K, const TA* A, int64_t a_rs, int64_t a_cs, const TB* B, int64_t b_rs, int64_t b_cs,
+          const float* bias, float* Zout, TC* C, cudaStream_t s) {
     dim3 blk(16, 16), grd((N + 15) / 16, (Mr + 15) / 16);
-    gemm_kernel<RELU><<<grd, blk, 0, s>>>(Mr, N, K, A, a_rs, a_cs, B, b_rs, b_cs, bias, Zout, C);
+    gemm_kernel<TA, TB, TC, RELU><<<grd, blk, 0, s>>>(Mr, N, K, A, a_rs, a_cs, B, b_rs, b_cs, bias, Zout, C);
     AMGH_LAUNCHED();
+}
+
+void to_bf16(const float* in, __nv_bfloat16* out, int64_t n, cudaStream_t s) {
+    if (n == 0) return;
+    to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out);
+    AMGH_LAUNCHED();
+}
+
+// the BF16 copies of the parameters, from the FP32 masters
+void refresh_wq(MlpNet& net, cudaStream_t s) {
+    if (!net.bf16) return;
+    if ((int64_t)net.wq.n < net.count()) net.wq.alloc(net.count());
+    to_bf16(net.params.p, net.wq.p, net.count(), s);
 }
 
 void ensure_batch(MlpNet& net, int nb) {
@@ -202,6 +226,9 @@ void ensure_batch(MlpNet& net, int nb) {
     net.dy.alloc((size_t)nb * net.d_out);
     net.dh.alloc((size_t)nb * w);
     net.dz.alloc((size_t)nb * w);
+    net.xq.alloc((size_t)nb * net.d_in);
+    net.h1q.alloc((size_t)nb * net.width);
+    net.h2q.alloc((size_t)nb * net.width);
     net.lossbuf.alloc(1);
 }
 
@@ -246,8 +273,20 @@ void mlp_reserve(MlpNet& net, int64_t rows, cudaStream_t s) {
     net.capacity = cap;
 }
 
+// (BF16: the parameters' copies must be current, see refresh_wq)
 static void forward_batch(MlpNet& net, const float* X, int nb, float* Y, cudaStream_t s) {
     const float* P = net.params.p;
+    if (net.bf16) {
+        const __nv_bfloat16* Q = net.wq.p;
+        to_bf16(X, net.xq.p, (int64_t)nb * net.d_in, s);
+        gemm<true>(nb, net.width, net.d_in, net.xq.p, net.d_in, 1, Q + net.off_W1(), net.width, 1, P + net.off_b1(),
+                   net.z1.p, net.h1q.p, s);
+        gemm<true>(nb, net.width, net.width, net.h1q.p, net.width, 1, Q + net.off_W2(), net.width, 1,
+                   P + net.off_b2(), net.z2.p, net.h2q.p, s);
+        gemm<false>(nb, net.d_out, net.width, net.h2q.p, net.width, 1, Q + net.off_W3(), net.d_out, 1,
+                    P + net.off_b3(), nullptr, Y, s);
+        return;
+    }
     gemm<true>(nb, net.width, net.d_in, X, net.d_in, 1, P + net.off_W1(), net.width, 1, P + net.off_b1(), net.z1.p,
                net.h1.p, s);
     gemm<true>(nb, net.width, net.width, net.h1.p, net.width, 1, P + net.off_W2(), net.width, 1, P + net.off_b2(),
@@ -259,6 +298,7 @@ static void forward_batch(MlpNet& net, const float* X, int nb, float* Y, cudaStr
 void mlp_forward(MlpNet& net, const float* X, int64_t n, float* Y, cudaStream_t s) {
     const int chunk = 4096;
     ensure_batch(net, chunk);
+    refresh_wq(net, s);
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int nb = (int)std::min<int64_t>(chunk, n - r0);
         forward_batch(net, X + r0 * net.d_in, nb, Y + r0 * net.d_out, s);
@@ -267,6 +307,7 @@ void mlp_forward(MlpNet& net, const float* X, int64_t n, float* Y, cudaStream_t 
 
 double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M, int nb, cudaStream_t s) {
     ensure_batch(net, nb);
+    refresh_wq(net, s);
     forward_batch(net, X, nb, net.y.p, s);
     const int64_t ny = (int64_t)nb * net.d_out;
     loss_kernel<<<1, 256, 0, s>>>(ny, net.y.p, T, M, net.dy.p, net.lossbuf.p);
@@ -274,6 +315,30 @@ double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M
     float* G = net.grads.p;
     const float* P = net.params.p;
     const int w = net.width;
+    if (net.bf16) {
+        // the same chain with the operands as the forward pass stored them
+        const __nv_bfloat16* Q = net.wq.p;
+        gemm<false>(w, net.d_out, nb, net.h2q.p, 1, w, net.dy.p, net.d_out, 1, nullptr, nullptr, G + net.off_W3(), s);
+        colsum_kernel<<<(net.d_out + 127) / 128, 128, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());
+        AMGH_LAUNCHED();
+        gemm<false>(nb, w, net.d_out, net.dy.p, net.d_out, 1, Q + net.off_W3(), 1, net.d_out, nullptr, nullptr,
+                    net.dh.p, s);
+        relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z2.p, net.dh.p);
+        AMGH_LAUNCHED();
+        gemm<false>(w, w, nb, net.h1q.p, 1, w, net.dh.p, w, 1, nullptr, nullptr, G + net.off_W2(), s);
+        colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dh.p, G + net.off_b2());
+        AMGH_LAUNCHED();
+        gemm<false>(nb, w, w, net.dh.p, w, 1, Q + net.off_W2(), 1, w, nullptr, nullptr, net.dz.p, s);
+        relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z1.p, net.dz.p);
+        AMGH_LAUNCHED();
+        gemm<false>(net.d_in, w, nb, net.xq.p, 1, net.d_in, net.dz.p, w, 1, nullptr, nullptr, G + net.off_W1(), s);
+        colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dz.p, G + net.off_b1());
+        AMGH_LAUNCHED();
+        double L = 0.0;
+        AMGH_CUDA(cudaMemcpyAsync(&L, net.lossbuf.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+        return L;
+    }
     // layer 3: dW3 = h2^T dy, db3 = colsum(dy), dh2 = dy W3^T
     gemm<false>(w, net.d_out, nb, net.h2.p, 1, w, net.dy.p, net.d_out, 1, nullptr, nullptr, G + net.off_W3(), s);
     colsum_kernel<<<(net.d_out + 127) / 128, 128, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());

@@ -1,7 +1,10 @@
-// Learned interpolation weights: a 3-layer perceptron (width 64, FP32) that maps a finest-level
-// coarse edge's local problem to the values of its column of P on the patch (the interior part of
-// Eq. sparseP), with our own forward, backward and Adam kernels.
+// Learned interpolation weights: a 3-layer perceptron (width 64, FP32, or BF16 storage of inputs,
+// weights and hidden activations with FP32 accumulation) that maps a finest-level coarse edge's
+// local problem to the values of its column of P on the patch (the interior part of Eq. sparseP),
+// with our own forward, backward and Adam kernels.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace amgh {
@@ -18,6 +21,11 @@ struct MlpNet {
     int64_t nsamples = 0, capacity = 0;
     DevArray<float> bx, bt, bm, z1, h1, z2, h2, y, dy, dh, dz;   // batch buffers
     int batch_cap = 0;
+    // BF16 storage: the products read bfloat16 copies of the inputs (xq), of the parameters (wq,
+    // refreshed from the FP32 masters before every pass) and of the hidden activations (h1q,
+    // h2q); accumulation, biases, outputs, gradients and Adam stay FP32
+    bool bf16 = false;
+    DevArray<__nv_bfloat16> wq, xq, h1q, h2q;
     DevArray<double> lossbuf;
     int64_t off_W1() const { return 0; }
     int64_t off_b1() const { return (int64_t)d_in * width; }

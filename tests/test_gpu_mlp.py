@@ -191,3 +191,68 @@ def test_trained_network_gains(amgh):
     assert info["interp_used"] == amgh.AMGH_INTERP_LEARNED
     assert info["rho"] <= 1.1 * info["rho_exact"]
     assert info["rho"] < ui["rho"]
+
+
+def test_bf16_storage_matches_oracle(amgh, logu12):
+    """BF16 storage (inputs, weight matrices and hidden activations bfloat16, FP32 accumulation)
+    against the oracle's definition on the same FP32 master weights.  The products accumulate in
+    FP32 on the GPU and in FP64 in the oracle, so a hidden activation that lies within that
+    difference of a bfloat16 rounding boundary may round the other way: one bfloat16 unit (2^-8
+    relative) in that activation.  Those rare flips bound the largest difference (1e-2 of max|y|);
+    the median difference stays at the FP32 level (1e-4), and the result differs from FP32 storage
+    by more than that (the mode is in effect)."""
+    _, _, X, T, Mk = logu12
+    m = amgh.amgh_mlp_create(9)
+    params = unflat(amgh.amgh_mlp_params(m), oracle_params(9))
+    X32, T32, M32 = X.astype(np.float32), T.astype(np.float32), Mk.astype(np.float32)
+    Xd, Td, Md = (a.astype(np.float64) for a in (X32, T32, M32))
+    y32 = amgh.amgh_mlp_predict(m, X32)
+    amgh.amgh_mlp_set_precision(m, amgh.AMGH_BF16)
+    y = amgh.amgh_mlp_predict(m, X32)
+    y_ref, _ = M.forward(params, Xd, "bf16")
+    scale = max(1.0, np.abs(y_ref).max())
+    err = np.abs(y - y_ref)
+    print("BF16 forward: max |y - y_oracle| %.3e, median %.3e, max |y - y_fp32| %.3e (scale %.3e)"
+          % (err.max(), np.median(err), np.abs(y - y32).max(), scale))
+    assert err.max() <= 1e-2 * scale
+    assert np.median(err) <= 1e-4 * scale
+    assert np.abs(y - y32).max() >= 1e-4 * scale
+    nb = 200
+    L, g = amgh.amgh_mlp_loss_grad(m, X32[:nb], T32[:nb], M32[:nb])
+    L_ref, g_ref = M.backward(params, Xd[:nb], Td[:nb], Md[:nb], "bf16")
+    g_ref = flat(g_ref)
+    print("BF16 loss gpu %.8e oracle %.8e; max gradient error %.3e of max %.3e"
+          % (L, L_ref, np.abs(g - g_ref).max(), np.abs(g_ref).max()))
+    assert abs(L - L_ref) <= 1e-2 * L_ref
+    assert np.abs(g - g_ref).max() <= 2e-2 * np.abs(g_ref).max()
+    # the masters are untouched; other precisions are refused
+    np.testing.assert_array_equal(amgh.amgh_mlp_params(m), flat(params).astype(np.float32))
+    with pytest.raises(amgh.AmghError) as e:
+        amgh.amgh_mlp_set_precision(m, amgh.AMGH_F64)
+    assert e.value.status == amgh.AMGH_ERR_INVALID_ARG
+
+
+def test_bf16_training_and_learned_setup(amgh, logu12):
+    """Training with BF16 storage lowers the loss about as far as FP32 storage does, and a setup
+    with the BF16 network runs its fallback test and solves."""
+    import torch
+    p, _, X, T, Mk = logu12
+    h = amgh.amgh_setup(p["A"], p["G"])
+    final = {}
+    for label, prec in (("fp32", amgh.AMGH_F32), ("bf16", amgh.AMGH_BF16)):
+        m = amgh.amgh_mlp_create(4)
+        amgh.amgh_mlp_set_precision(m, prec)
+        amgh.amgh_mlp_add_samples(m, h)
+        losses = [amgh.amgh_mlp_train(m, 1, 256, 1e-3, 100 * e) for e in range(20)]
+        final[label] = losses[-1]
+        print("%s storage: epoch loss %.5f -> %.5f" % (label, losses[0], losses[-1]))
+        assert losses[-1] < 0.9 * losses[0]
+    assert final["bf16"] <= 1.25 * final["fp32"]
+    hl = amgh.amgh_setup(p["A"], p["G"], interp=amgh.AMGH_INTERP_LEARNED, mlp=m)
+    info = amgh.amgh_info(hl)
+    f = torch.tensor(fields.rhs(p["ndof"], 1), device="cuda")
+    x = torch.zeros_like(f)
+    it, rel, ok = amgh.amgh_pcg_solve(hl, f, x, 1e-8, 500)
+    print("BF16 network setup: kept %s, rho %.4f (exact %.4f), PCG %d"
+          % (info["interp_used"] == amgh.AMGH_INTERP_LEARNED, info["rho"], info["rho_exact"], it))
+    assert ok and rel <= 1e-8

@@ -130,3 +130,40 @@ def test_probe_factor_obeys_the_energy_bound():
     assert f <= rho * (lam[-1] / lam[0]) ** (0.5 / k) * (1 + 1e-12)
     ek = np.linalg.matrix_power(E, k) @ x0
     assert abs(f - (np.linalg.norm(A @ ek) / np.linalg.norm(A @ x0)) ** (1.0 / k)) < 1e-9
+
+
+def test_bf16_rounding_is_nearest_even_of_the_float32_value():
+    """to_bf16 against hand-placed ties and against torch's own float32 -> bfloat16 conversion
+    (round to nearest, ties to even) on random values."""
+    torch = __import__("pytest").importorskip("torch")
+    u = 2.0 ** -8                      # half a bfloat16 unit at 1 (8 significant bits)
+    vals = np.array([1.0, 1 + u, 1 + 3 * u, 1 + u + 2.0 ** -20, -(1 + 3 * u), 3.0, 0.0, 2.0 ** -130])
+    want = np.array([1.0, 1.0, 1 + 4 * u, 1 + 2 * u, -(1 + 4 * u), 3.0, 0.0, 2.0 ** -130])
+    np.testing.assert_array_equal(M.to_bf16(vals), want)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(20000) * 10.0 ** rng.uniform(-6, 6, 20000)
+    ref = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(M.to_bf16(x), ref)
+
+
+def test_bf16_storage_changes_only_what_it_rounds():
+    """With inputs, weights and every hidden activation already bfloat16 values (small integers and
+    halves), BF16 storage gives exactly the FP32 forward pass and gradients; with general values
+    the forward pass differs, by about the bfloat16 unit."""
+    rng = np.random.default_rng(2)
+    d_in, width, d_out, nb = 6, 5, 4, 3
+    ints = lambda shape: rng.integers(-3, 4, shape).astype(float) / 2.0
+    params = [ints((d_in, width)), ints(width), ints((width, width)), ints(width), ints((width, d_out)), ints(d_out)]
+    X, T, Mk = ints((nb, d_in)), ints((nb, d_out)), np.ones((nb, d_out))
+    y32, _ = M.forward(params, X)
+    y16, _ = M.forward(params, X, "bf16")
+    np.testing.assert_array_equal(y16, y32)
+    L32, g32 = M.backward(params, X, T, Mk)
+    L16, g16 = M.backward(params, X, T, Mk, "bf16")
+    assert L16 == L32 and all(np.array_equal(a, b) for a, b in zip(g16, g32))
+    params = M.init_params(_u01(3), d_in, width, d_out)
+    X = rng.standard_normal((nb, d_in))
+    y32, _ = M.forward(params, X)
+    y16, _ = M.forward(params, X, "bf16")
+    d = np.abs(y16 - y32).max() / np.abs(y32).max()
+    assert 1e-5 < d < 5e-2
