@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--variants", default="hex128_spheres",
                     help="workload of the FP64 / FP32 / BF16 comparison reported in the line ('none' to skip)")
     ap.add_argument("--variant-steps", type=int, default=1)
+    ap.add_argument("--learned-meshes", type=int, default=40,
+                    help="training meshes of the learned-interpolation comparison reported in the line (0 to skip)")
     ap.add_argument("--profile-setup", action="store_true",
                     help="set up once, then once more between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
@@ -212,7 +214,55 @@ def time_variant(amgh, prob, dev_inputs, precision, steps, warmup, **kw):
             "converged": res[-1][5], "true_relres": true_rel,
             "level_precision": [names[q] for q in info["precision"]],
             "block_kappa": info["block_kappa"], "levels": info["n"], "op_complexity": round(info["op_complexity"], 4),
+            "interp_used": info["interp_used"], "rho": info["rho"], "rho_exact": info["rho_exact"],
             "steps": steps, "warmup": warmup}
+
+
+def learned_comparison(amgh, prob, dev_inputs, meshes, epochs=8):
+    """The learned interpolation on this workload: a network trained on the exact local solves of
+    `meshes` seeded 24^3 meshes with alpha = 10^U(-4,4) per element (FP32 and BF16 storage), its
+    setup with the convergence-factor test (the exact factor measured once, then passed as the
+    stored reference), against the exact local solves; whole steps (setup + CG to 1e-8)."""
+    import workloads as W
+    from workloads import fields
+    t0 = time.perf_counter()
+    nets = {"fp32": amgh.amgh_mlp_create(0), "bf16": amgh.amgh_mlp_create(0)}
+    amgh.amgh_mlp_set_precision(nets["bf16"], amgh.AMGH_BF16)
+    old = os.environ.get("AMGH_TUNE")
+    os.environ["AMGH_TUNE"] = "0"   # the samples need the finest P only
+    try:
+        for s in range(meshes):
+            pt = W.hex_problem(24, fields.log_uniform(24, 700 + s), 1.0)
+            h = amgh.amgh_setup(pt["A"], pt["G"])
+            for m in nets.values():
+                amgh.amgh_mlp_add_samples(m, h)
+            amgh.amgh_destroy(h)
+    finally:
+        if old is None:
+            del os.environ["AMGH_TUNE"]
+        else:
+            os.environ["AMGH_TUNE"] = old
+    t_data = time.perf_counter() - t0
+    out = {"train": {"meshes": meshes, "mesh": "24^3, alpha = 10^U(-4,4) per element, beta = 1",
+                     "samples": amgh.amgh_mlp_num_samples(nets["fp32"]), "data_s": t_data, "epochs": epochs}}
+    for label, m in nets.items():
+        t0 = time.perf_counter()
+        losses = [amgh.amgh_mlp_train(m, 1, 512, 1e-3, 20000 + e) for e in range(epochs)]
+        out["train"][label] = {"train_s": time.perf_counter() - t0, "loss_first": losses[0], "loss_last": losses[-1]}
+    Ad, Gd, fd = dev_inputs
+    h = amgh.amgh_setup(Ad, Gd, interp=amgh.AMGH_INTERP_LEARNED, mlp=nets["fp32"])
+    rho_ref = amgh.amgh_info(h)["rho_exact"]
+    amgh.amgh_destroy(h)
+    keys = ("s_per_step", "setup_s", "solve_s", "pcg_iters", "converged", "levels", "interp_used", "rho", "rho_exact")
+    ex = time_variant(amgh, prob, dev_inputs, "f64", 2, 1)
+    out["exact"] = {k: ex[k] for k in keys if k not in ("interp_used", "rho", "rho_exact")}
+    out["rho_exact"] = rho_ref
+    for label, m in nets.items():
+        v = time_variant(amgh, prob, dev_inputs, "f64", 2, 1, interp=amgh.AMGH_INTERP_LEARNED, mlp=m, rho_ref=rho_ref)
+        v = {k: v[k] for k in keys}
+        v["kept"] = v.pop("interp_used") == amgh.AMGH_INTERP_LEARNED
+        out[label] = v
+    return out
 
 
 def last_colour(res):
@@ -587,6 +637,10 @@ def run_gpu(args, rank, world, local_rank):
         for v in variants:
             v["speedup_vs_f64"] = base / v["s_per_step"]
 
+    learned = None
+    if args.learned_meshes > 0 and world == 1:
+        learned = learned_comparison(amgh, prob, (Ad, Gd, fd), args.learned_meshes)
+
     if rank != 0:
         return 0
     cpu = oracle_sample(workload=args.workload)
@@ -626,6 +680,8 @@ def run_gpu(args, rank, world, local_rank):
         line["comparison"] = comparison
     if variants is not None:
         line["variants"] = variants
+    if learned is not None:
+        line["learned"] = learned
     print(json.dumps(line), flush=True)
     return 0
 
