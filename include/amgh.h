@@ -96,9 +96,9 @@ enum { AMGH_INTERP_LOCAL = 0, AMGH_INTERP_LEARNED = 1, AMGH_INTERP_GEOMETRIC = 2
  * refinement that is trilinear interpolation.  The exterior rows R^T satisfy the relation as they
  * are; every interior row of P moves, on its own pattern, to the nearest row (Euclidean) that
  * satisfies its row of the relation, in least squares where none does.  The pattern of P, and so
- * the cost of a V-cycle, is unchanged.  It pays where the gradients are the troublesome modes
- * (a small mass coefficient under a few jumps); under coefficients that jump over many decades
- * it can take more iterations than the plain extension. */
+ * the cost of a V-cycle, is unchanged.  It pays for smooth or piecewise-constant coefficients;
+ * where the curl coefficient varies over many decades from element to element it can take more
+ * iterations than the plain extension. */
 enum { AMGH_COARSEN_ALGEBRAIC = 0, AMGH_COARSEN_REFINEMENT = 1 };
 
 typedef struct {
