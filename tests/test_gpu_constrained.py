@@ -132,3 +132,36 @@ def test_fewer_iterations_than_the_plain_local_extension(amgh):
         assert ok
     print("24^3 checkerboard PCG iterations:", its, "nnz per level:", nnz)
     assert its["constrained"] <= its["local"] // 2
+
+
+def test_with_reduced_precision_and_batched_setup(amgh):
+    """The corrected hierarchy under the other setup options: FP32 storage requested (flexible CG
+    to the same FP64 residual, iterations close to the FP64 ones), and a batched setup of several
+    systems, each equal to its own single setup."""
+    import torch
+    p = W.hex_problem(12, 1.0, 1.0)          # star blocks well enough conditioned for FP32 levels
+    f = cuda(W.fields.rhs(p["ndof"], 0))
+    h64 = amgh.amgh_setup(p["A"], p["G"], interp=amgh.AMGH_INTERP_CONSTRAINED, dense_tail=0)
+    h32 = amgh.amgh_setup(p["A"], p["G"], interp=amgh.AMGH_INTERP_CONSTRAINED, precision=amgh.AMGH_F32,
+                          dense_tail=0)
+    assert amgh.AMGH_F32 in amgh.amgh_info(h32)["precision"]
+    its = []
+    for h in (h64, h32):
+        x = torch.zeros(p["ndof"], dtype=torch.float64, device="cuda")
+        it, rel, ok = amgh.amgh_pcg_solve(h, f, x, 1e-8, 500)
+        assert ok and rel <= 1e-8
+        its.append(it)
+    print("constrained 12^3 unit coefficients: FP64 %d, FP32 storage %d iterations (levels %s)"
+          % (its[0], its[1], amgh.amgh_info(h32)["precision"]))
+    assert its[1] <= its[0] + 2
+    probs = [W.make_config("hex8_unit"), W.make_config("hex16_checker"),
+             W.hex_problem(12, W.fields.log_uniform(12, 3, lo=-2, hi=2), 0.1)]
+    hs = amgh.amgh_batch_setup([q["A"] for q in probs], [q["G"] for q in probs],
+                               interp=amgh.AMGH_INTERP_CONSTRAINED)
+    for q, hb in zip(probs, hs):
+        hs1 = amgh.amgh_setup(q["A"], q["G"], interp=amgh.AMGH_INTERP_CONSTRAINED)
+        assert amgh.amgh_info(hb)["interp_used"] == amgh.AMGH_INTERP_CONSTRAINED
+        for l in range(len(amgh.amgh_info(hb)["n"]) - 1):
+            Pb, Ps = amgh.amgh_level_matrix(hb, l, 1), amgh.amgh_level_matrix(hs1, l, 1)
+            np.testing.assert_array_equal(Pb.indices, Ps.indices)
+            np.testing.assert_array_equal(Pb.data, Ps.data)
