@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--profile-setup", action="store_true",
                     help="set up once, then once more between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints no bench line")
+    ap.add_argument("--profile-mlp-epoch", action="store_true",
+                    help="learned interpolation: build the samples of 20 seeded 24^3 meshes, train one epoch, "
+                         "then one more between cudaProfilerStart/Stop and exit; prints the epoch time")
     ap.add_argument("--profile-vcycles", type=int, default=0,
                     help="set up once, then run this many V-cycles between cudaProfilerStart/Stop and exit "
                          "(for ncu --profile-from-start off); prints no bench line")
@@ -474,6 +477,34 @@ def run_gpu(args, rank, world, local_rank):
         extra["fuse_restrict"] = args.fuse_restrict
     if args.interp == "constrained":
         extra["interp"] = amgh.AMGH_INTERP_CONSTRAINED
+
+    if args.profile_mlp_epoch:
+        from workloads import fields
+        m = amgh.amgh_mlp_create(0)
+        old = os.environ.get("AMGH_TUNE")
+        os.environ["AMGH_TUNE"] = "0"   # the samples need the finest P only
+        for sd in range(20):
+            pt = W.hex_problem(24, fields.log_uniform(24, 500 + sd), 1.0)
+            ht = amgh.amgh_setup(pt["A"], pt["G"])
+            amgh.amgh_mlp_add_samples(m, ht)
+            amgh.amgh_destroy(ht)
+        if old is None:
+            del os.environ["AMGH_TUNE"]
+        else:
+            os.environ["AMGH_TUNE"] = old
+        amgh.amgh_mlp_train(m, 1, 512, 1e-3, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        amgh.amgh_mlp_train(m, 2, 512, 1e-3, 2)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 2
+        torch.cuda.profiler.start()
+        amgh.amgh_mlp_train(m, 1, 512, 1e-3, 3)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print("profiled one training epoch of %d samples (batch 512); epoch %.1f ms without the profiler"
+              % (amgh.amgh_mlp_num_samples(m), 1000 * dt), flush=True)
+        return 0
 
     if args.profile_setup:
         h = amgh.amgh_setup(Ad, Gd, precision=prec, **extra)

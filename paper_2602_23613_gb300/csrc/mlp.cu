@@ -60,12 +60,51 @@ __global__ void gemm_kernel(int Mr, int N, int K, const TA* __restrict__ A, int6
     }
 }
 
+// column sums: one CTA of 256 threads per column, each thread a strided partial sum, then a
+// fixed-order tree (deterministic)
+// split-K part of C = A B: CTA (x, y, z) forms its 16 x 16 tile over k in [z ks, (z + 1) ks) into
+// part[z] (M x N); parts are then summed in z order (deterministic)
+template <class TA, class TB>
+__global__ void gemm_part_kernel(int Mr, int N, int K, int ks, const TA* __restrict__ A, int64_t a_rs, int64_t a_cs,
+                                 const TB* __restrict__ B, int64_t b_rs, int64_t b_cs, float* __restrict__ part) {
+    __shared__ float As[16][17];
+    __shared__ float Bs[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+    const int kb0 = blockIdx.z * ks, kb1 = min(K, kb0 + ks);
+    float acc = 0.f;
+    for (int k0 = kb0; k0 < kb1; k0 += 16) {
+        const int ka = k0 + tx, kb = k0 + ty;
+        As[ty][tx] = (row < Mr && ka < kb1) ? ldf(A, row * a_rs + ka * a_cs) : 0.f;
+        Bs[ty][tx] = (kb < kb1 && col < N) ? ldf(B, kb * b_rs + col * b_cs) : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    if (row < Mr && col < N) part[(int64_t)blockIdx.z * Mr * N + (int64_t)row * N + col] = acc;
+}
+
+__global__ void sum_parts_kernel(int nparts, int64_t mn, const float* __restrict__ part, float* __restrict__ C) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= mn) return;
+    float s = part[t];
+    for (int z = 1; z < nparts; ++z) s += part[z * mn + t];
+    C[t] = s;
+}
+
 __global__ void colsum_kernel(int rows, int cols, const float* __restrict__ D, float* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols) return;
+    __shared__ float red[256];
+    const int j = blockIdx.x;
     float s = 0.f;
-    for (int r = 0; r < rows; ++r) s += D[(int64_t)r * cols + j];
-    out[j] = s;
+    for (int r = threadIdx.x; r < rows; r += 256) s += D[(int64_t)r * cols + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = red[0];
 }
 
 __global__ void relu_back_kernel(int64_t n, const float* __restrict__ Z, float* __restrict__ D) {
@@ -73,12 +112,17 @@ __global__ void relu_back_kernel(int64_t n, const float* __restrict__ Z, float* 
     if (t < n && !(Z[t] > 0.f)) D[t] = 0.f;
 }
 
-// masked squared error over the batch, and dy = 2 (y - t) m / sum(m); single block, fixed order
-__global__ void loss_kernel(int64_t n, const float* __restrict__ Y, const float* __restrict__ T,
-                            const float* __restrict__ Mk, float* __restrict__ dY, double* __restrict__ out) {
-    __shared__ double sl[256], sm[256];
+// masked squared error over the batch, and dy = 2 (y - t) m / sum(m), in three steps with a
+// fixed summation order: per-CTA partial sums (FP64), their sum on one CTA, then dy elementwise
+constexpr int LOSS_BLOCKS = 152, LOSS_THREADS = 256;
+
+__global__ void __launch_bounds__(LOSS_THREADS) loss_partial_kernel(int64_t n, const float* __restrict__ Y,
+                                                                    const float* __restrict__ T,
+                                                                    const float* __restrict__ Mk,
+                                                                    double* __restrict__ part) {
+    __shared__ double sl[LOSS_THREADS], sm[LOSS_THREADS];
     double l = 0.0, m = 0.0;
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+    for (int64_t t = (int64_t)blockIdx.x * LOSS_THREADS + threadIdx.x; t < n; t += (int64_t)gridDim.x * LOSS_THREADS) {
         const double e = (double)Y[t] - (double)T[t];
         l += e * e * Mk[t];
         m += Mk[t];
@@ -86,17 +130,50 @@ __global__ void loss_kernel(int64_t n, const float* __restrict__ Y, const float*
     sl[threadIdx.x] = l;
     sm[threadIdx.x] = m;
     __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sl[threadIdx.x] += sl[threadIdx.x + s];
-            sm[threadIdx.x] += sm[threadIdx.x + s];
+    for (int o = LOSS_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sl[threadIdx.x] += sl[threadIdx.x + o];
+            sm[threadIdx.x] += sm[threadIdx.x + o];
         }
         __syncthreads();
     }
-    const double nrm = sm[0] > 0.0 ? sm[0] : 1.0;
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x)
-        dY[t] = (float)(2.0 * ((double)Y[t] - (double)T[t]) * Mk[t] / nrm);
-    if (threadIdx.x == 0) out[0] = sl[0] / nrm;
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sl[0];
+        part[2 * blockIdx.x + 1] = sm[0];
+    }
+}
+
+// out[0] = loss, out[2] = sum of the mask (the normaliser); acc[0] += loss when given
+__global__ void __launch_bounds__(LOSS_THREADS) loss_final_kernel(int nparts, const double* __restrict__ part,
+                                                                  double* __restrict__ out, double* __restrict__ acc) {
+    __shared__ double sl[LOSS_THREADS], sm[LOSS_THREADS];
+    double l = 0.0, m = 0.0;
+    for (int q = threadIdx.x; q < nparts; q += LOSS_THREADS) {
+        l += part[2 * q];
+        m += part[2 * q + 1];
+    }
+    sl[threadIdx.x] = l;
+    sm[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = LOSS_THREADS / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sl[threadIdx.x] += sl[threadIdx.x + o];
+            sm[threadIdx.x] += sm[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double nrm = sm[0] > 0.0 ? sm[0] : 1.0;
+        out[0] = sl[0] / nrm;
+        out[2] = nrm;
+        if (acc) acc[0] += sl[0] / nrm;   // the epoch's running sum (batches run in stream order)
+    }
+}
+
+__global__ void loss_grad_kernel(int64_t n, const float* __restrict__ Y, const float* __restrict__ T,
+                                 const float* __restrict__ Mk, const double* __restrict__ nrm, float* __restrict__ dY) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dY[t] = (float)(2.0 * ((double)Y[t] - (double)T[t]) * Mk[t] / nrm[0]);
 }
 
 __global__ void adam_kernel(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
@@ -198,6 +275,27 @@ void gemm(int Mr, int N, int K, const TA* A, int64_t a_rs, int64_t a_cs, const T
     AMGH_LAUNCHED();
 }
 
+// a weight gradient C (Mr x N) = A B with the batch as K: split over K in slices of 128 when the
+// batch is long enough for the plain tiles to leave most SMs idle
+constexpr int KSPLIT_MAX = 8;
+template <class TA, class TB>
+void gemm_wgrad(MlpNet& net, int Mr, int N, int K, const TA* A, int64_t a_rs, int64_t a_cs, const TB* B,
+                int64_t b_rs, int64_t b_cs, float* C, cudaStream_t s) {
+    const int nparts = std::min(KSPLIT_MAX, std::max(1, K / 128));
+    if (nparts == 1) {
+        gemm<false>(Mr, N, K, A, a_rs, a_cs, B, b_rs, b_cs, nullptr, nullptr, C, s);
+        return;
+    }
+    const int ks = ((K + nparts - 1) / nparts + 15) / 16 * 16;
+    const int nz = (K + ks - 1) / ks;
+    const int64_t mn = (int64_t)Mr * N;
+    if ((int64_t)net.kparts.n < nz * mn) net.kparts.alloc((size_t)(nz * mn));
+    dim3 blk(16, 16), grd((N + 15) / 16, (Mr + 15) / 16, nz);
+    gemm_part_kernel<TA, TB><<<grd, blk, 0, s>>>(Mr, N, K, ks, A, a_rs, a_cs, B, b_rs, b_cs, net.kparts.p);
+    sum_parts_kernel<<<(unsigned)((mn + 255) / 256), 256, 0, s>>>(nz, mn, net.kparts.p, C);
+    AMGH_LAUNCHED();
+}
+
 void to_bf16(const float* in, __nv_bfloat16* out, int64_t n, cudaStream_t s) {
     if (n == 0) return;
     to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, in, out);
@@ -229,7 +327,8 @@ void ensure_batch(MlpNet& net, int nb) {
     net.xq.alloc((size_t)nb * net.d_in);
     net.h1q.alloc((size_t)nb * net.width);
     net.h2q.alloc((size_t)nb * net.width);
-    net.lossbuf.alloc(1);
+    net.lossbuf.alloc(3);   // the last batch's loss, the epoch's running sum, the last normaliser
+    net.losspart.alloc(2 * LOSS_BLOCKS);
 }
 
 }  // namespace
@@ -305,12 +404,16 @@ void mlp_forward(MlpNet& net, const float* X, int64_t n, float* Y, cudaStream_t 
     }
 }
 
-double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M, int nb, cudaStream_t s) {
+double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M, int nb, cudaStream_t s,
+                     bool read_loss) {
     ensure_batch(net, nb);
     refresh_wq(net, s);
     forward_batch(net, X, nb, net.y.p, s);
     const int64_t ny = (int64_t)nb * net.d_out;
-    loss_kernel<<<1, 256, 0, s>>>(ny, net.y.p, T, M, net.dy.p, net.lossbuf.p);
+    loss_partial_kernel<<<LOSS_BLOCKS, LOSS_THREADS, 0, s>>>(ny, net.y.p, T, M, net.losspart.p);
+    loss_final_kernel<<<1, LOSS_THREADS, 0, s>>>(LOSS_BLOCKS, net.losspart.p, net.lossbuf.p,
+                                                 read_loss ? nullptr : net.lossbuf.p + 1);
+    loss_grad_kernel<<<(unsigned)((ny + 255) / 256), 256, 0, s>>>(ny, net.y.p, T, M, net.lossbuf.p + 2, net.dy.p);
     AMGH_LAUNCHED();
     float* G = net.grads.p;
     const float* P = net.params.p;
@@ -318,48 +421,52 @@ double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M
     if (net.bf16) {
         // the same chain with the operands as the forward pass stored them
         const __nv_bfloat16* Q = net.wq.p;
-        gemm<false>(w, net.d_out, nb, net.h2q.p, 1, w, net.dy.p, net.d_out, 1, nullptr, nullptr, G + net.off_W3(), s);
-        colsum_kernel<<<(net.d_out + 127) / 128, 128, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());
+        gemm_wgrad(net, w, net.d_out, nb, net.h2q.p, 1, w, net.dy.p, net.d_out, 1, G + net.off_W3(), s);
+        colsum_kernel<<<net.d_out, 256, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());
         AMGH_LAUNCHED();
         gemm<false>(nb, w, net.d_out, net.dy.p, net.d_out, 1, Q + net.off_W3(), 1, net.d_out, nullptr, nullptr,
                     net.dh.p, s);
         relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z2.p, net.dh.p);
         AMGH_LAUNCHED();
-        gemm<false>(w, w, nb, net.h1q.p, 1, w, net.dh.p, w, 1, nullptr, nullptr, G + net.off_W2(), s);
-        colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dh.p, G + net.off_b2());
+        gemm_wgrad(net, w, w, nb, net.h1q.p, 1, w, net.dh.p, w, 1, G + net.off_W2(), s);
+        colsum_kernel<<<w, 256, 0, s>>>(nb, w, net.dh.p, G + net.off_b2());
         AMGH_LAUNCHED();
         gemm<false>(nb, w, w, net.dh.p, w, 1, Q + net.off_W2(), 1, w, nullptr, nullptr, net.dz.p, s);
         relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z1.p, net.dz.p);
         AMGH_LAUNCHED();
-        gemm<false>(net.d_in, w, nb, net.xq.p, 1, net.d_in, net.dz.p, w, 1, nullptr, nullptr, G + net.off_W1(), s);
-        colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dz.p, G + net.off_b1());
+        gemm_wgrad(net, net.d_in, w, nb, net.xq.p, 1, net.d_in, net.dz.p, w, 1, G + net.off_W1(), s);
+        colsum_kernel<<<w, 256, 0, s>>>(nb, w, net.dz.p, G + net.off_b1());
         AMGH_LAUNCHED();
         double L = 0.0;
-        AMGH_CUDA(cudaMemcpyAsync(&L, net.lossbuf.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-        AMGH_CUDA(cudaStreamSynchronize(s));
+        if (read_loss) {
+            AMGH_CUDA(cudaMemcpyAsync(&L, net.lossbuf.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+            AMGH_CUDA(cudaStreamSynchronize(s));
+        }
         return L;
     }
     // layer 3: dW3 = h2^T dy, db3 = colsum(dy), dh2 = dy W3^T
-    gemm<false>(w, net.d_out, nb, net.h2.p, 1, w, net.dy.p, net.d_out, 1, nullptr, nullptr, G + net.off_W3(), s);
-    colsum_kernel<<<(net.d_out + 127) / 128, 128, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());
+    gemm_wgrad(net, w, net.d_out, nb, net.h2.p, 1, w, net.dy.p, net.d_out, 1, G + net.off_W3(), s);
+    colsum_kernel<<<net.d_out, 256, 0, s>>>(nb, net.d_out, net.dy.p, G + net.off_b3());
     AMGH_LAUNCHED();
     gemm<false>(nb, w, net.d_out, net.dy.p, net.d_out, 1, P + net.off_W3(), 1, net.d_out, nullptr, nullptr, net.dh.p, s);
     relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z2.p, net.dh.p);
     AMGH_LAUNCHED();
     // layer 2: dW2 = h1^T dz2, db2, dh1 = dz2 W2^T
-    gemm<false>(w, w, nb, net.h1.p, 1, w, net.dh.p, w, 1, nullptr, nullptr, G + net.off_W2(), s);
-    colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dh.p, G + net.off_b2());
+    gemm_wgrad(net, w, w, nb, net.h1.p, 1, w, net.dh.p, w, 1, G + net.off_W2(), s);
+    colsum_kernel<<<w, 256, 0, s>>>(nb, w, net.dh.p, G + net.off_b2());
     AMGH_LAUNCHED();
     gemm<false>(nb, w, w, net.dh.p, w, 1, P + net.off_W2(), 1, w, nullptr, nullptr, net.dz.p, s);
     relu_back_kernel<<<(unsigned)(((int64_t)nb * w + 255) / 256), 256, 0, s>>>((int64_t)nb * w, net.z1.p, net.dz.p);
     AMGH_LAUNCHED();
     // layer 1: dW1 = X^T dz1, db1
-    gemm<false>(net.d_in, w, nb, X, 1, net.d_in, net.dz.p, w, 1, nullptr, nullptr, G + net.off_W1(), s);
-    colsum_kernel<<<(w + 127) / 128, 128, 0, s>>>(nb, w, net.dz.p, G + net.off_b1());
+    gemm_wgrad(net, net.d_in, w, nb, X, 1, net.d_in, net.dz.p, w, 1, G + net.off_W1(), s);
+    colsum_kernel<<<w, 256, 0, s>>>(nb, w, net.dz.p, G + net.off_b1());
     AMGH_LAUNCHED();
     double L = 0.0;
-    AMGH_CUDA(cudaMemcpyAsync(&L, net.lossbuf.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    AMGH_CUDA(cudaStreamSynchronize(s));
+    if (read_loss) {
+        AMGH_CUDA(cudaMemcpyAsync(&L, net.lossbuf.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMGH_CUDA(cudaStreamSynchronize(s));
+    }
     return L;
 }
 
@@ -384,7 +491,8 @@ double mlp_epoch(MlpNet& net, int batch, float lr, uint64_t seed, cudaStream_t s
     DevArray<int32_t> dperm;
     dperm.upload(perm, s);
     ensure_batch(net, batch);
-    double tot = 0.0;
+    // the batch losses add up on the device; the host reads the sum once, after the epoch
+    AMGH_CUDA(cudaMemsetAsync(net.lossbuf.p + 1, 0, sizeof(double), s));
     int nbatches = 0;
     for (int64_t r0 = 0; r0 < N; r0 += batch) {
         const int nb = (int)std::min<int64_t>(batch, N - r0);
@@ -395,10 +503,13 @@ double mlp_epoch(MlpNet& net, int batch, float lr, uint64_t seed, cudaStream_t s
         gather_rows_kernel<<<(unsigned)(((int64_t)nb * net.d_out + 255) / 256), 256, 0, s>>>(nb, net.d_out, dperm.p + r0,
                                                                                            net.M.p, net.bm.p);
         AMGH_LAUNCHED();
-        tot += mlp_loss_grad(net, net.bx.p, net.bt.p, net.bm.p, nb, s);
+        mlp_loss_grad(net, net.bx.p, net.bt.p, net.bm.p, nb, s, false);
         mlp_adam(net, lr, s);
         nbatches++;
     }
+    double tot = 0.0;
+    AMGH_CUDA(cudaMemcpyAsync(&tot, net.lossbuf.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMGH_CUDA(cudaStreamSynchronize(s));
     return tot / nbatches;
 }
 

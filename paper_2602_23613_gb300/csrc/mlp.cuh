@@ -26,7 +26,8 @@ struct MlpNet {
     // h2q); accumulation, biases, outputs, gradients and Adam stay FP32
     bool bf16 = false;
     DevArray<__nv_bfloat16> wq, xq, h1q, h2q;
-    DevArray<double> lossbuf;
+    DevArray<double> lossbuf, losspart;
+    DevArray<float> kparts;                       // split-K parts of the weight gradients
     int64_t off_W1() const { return 0; }
     int64_t off_b1() const { return (int64_t)d_in * width; }
     int64_t off_W2() const { return off_b1() + width; }
@@ -40,8 +41,10 @@ struct MlpNet {
 void mlp_init(MlpNet& net, uint64_t seed, cudaStream_t s);
 // forward pass for n rows of X (n x d_in) into Y (n x d_out); uses the batch buffers in chunks
 void mlp_forward(MlpNet& net, const float* X, int64_t n, float* Y, cudaStream_t s);
-// loss and gradients of a batch (X, T, M device arrays of nb rows) into net.grads; returns loss
-double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M, int nb, cudaStream_t s);
+// loss and gradients of a batch (X, T, M device arrays of nb rows) into net.grads; returns the loss
+// (read_loss = false: returns 0 without waiting and adds the loss to the epoch sum, lossbuf[1])
+double mlp_loss_grad(MlpNet& net, const float* X, const float* T, const float* M, int nb, cudaStream_t s,
+                     bool read_loss = true);
 void mlp_adam(MlpNet& net, float lr, cudaStream_t s);
 // one pass over the sample set in shuffled batches (permutation from stream 7 with the epoch seed)
 double mlp_epoch(MlpNet& net, int batch, float lr, uint64_t seed, cudaStream_t s);
