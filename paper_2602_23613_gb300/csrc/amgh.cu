@@ -1943,6 +1943,8 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
             // constraint are built on a helper thread while this one builds the smoother's stars
             // and the solves run; the device then corrects the rows
             const bool commute = solved && prm.interp == AMGH_INTERP_CONSTRAINED;
+            // the finest P's fill time ends here, unless the correction still has to run
+            if (l == 0 && !commute) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             std::string comm_msg;
             std::vector<int32_t> order;
             int32_t cls_ptr[9] = {0};
@@ -2005,8 +2007,8 @@ static void setup_impl(amgh_ctx* h, const amgh_csr* Ain, const amgh_csr* Gin) {
                                     dcr_ea.p, dcr_eb.p, dcr_nptr.p, dcr_t.p, dcr_comp.p, h->errflag.p, s);
                 h->interp_used = AMGH_INTERP_CONSTRAINED;
                 cur.Pn = std::move(crow.Pn);
+                if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             }
-            if (l == 0) AMGH_CUDA(cudaEventRecord(fe.e1, s));
             if (solved) check_flag(h, "a local harmonic-extension solve or the commuting correction");
             if (l == 0) {
                 float ms = 0.f;
