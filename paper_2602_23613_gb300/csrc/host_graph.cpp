@@ -56,18 +56,6 @@ inline bool has(const HostCSR& M, int r, int c) {
     return std::binary_search(b, e, c);
 }
 
-// Build CSR from per-row sorted vectors
-HostCSR from_rows(int nrows, int ncols, const std::vector<std::vector<int32_t>>& rows) {
-    HostCSR M;
-    M.nrows = nrows;
-    M.ncols = ncols;
-    M.ptr.assign(nrows + 1, 0);
-    for (int r = 0; r < nrows; ++r) M.ptr[r + 1] = M.ptr[r] + (int32_t)rows[r].size();
-    M.idx.resize(M.ptr[nrows]);
-    for (int r = 0; r < nrows; ++r) std::copy(rows[r].begin(), rows[r].end(), M.idx.begin() + M.ptr[r]);
-    return M;
-}
-
 // Symbolic product row by row: out row r = union over t in X row r of Y row X.idx[t].
 HostCSR symbolic_rows(const HostCSR& X, const HostCSR& Y, int nthreads) {
     HostCSR M;
