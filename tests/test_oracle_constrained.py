@@ -173,3 +173,20 @@ def test_rank_of_the_row_block_is_structural():
     want = p0 + C @ y
     assert np.abs(out).max() < 10.0
     np.testing.assert_allclose(out, want, rtol=0, atol=1e-12)
+
+
+def test_every_level_of_a_hierarchy_commutes():
+    """The correction on every level of a corrected hierarchy (coarse levels come from Galerkin
+    products of corrected P, so their gradients are the coarse G_c): the relation holds to rounding
+    on each level, and each level's exterior rows are R^T."""
+    p = W.hex_problem(12, W.fields.log_uniform(12, 3, lo=-2, hi=2), 0.1)
+    H = O.setup(p["A"], p["G"], interp="constrained")
+    assert len(H) >= 3
+    for l, L in enumerate(H[:-1]):
+        cz = L["coarsening"]
+        G = sp.csr_matrix(L["G"])
+        d = defect(cz, G)
+        assert abs(d).max() <= 1e-12 * max(1.0, abs(cz["P"]).max()), (l, abs(d).max())
+        ext = np.concatenate([[e[0], e[2]] for e in cz["edges"]])
+        R = O.restriction(cz["edges"], L["A"].shape[0])
+        assert abs(sp.csr_matrix(cz["P"])[ext] - R.T.tocsr()[ext]).max() == 0, l
