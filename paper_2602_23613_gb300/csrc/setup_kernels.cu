@@ -416,7 +416,8 @@ namespace {
 
 constexpr int COMMUTE_SIZES[5] = {8, 16, 32, 64, 128};
 
-__host__ __device__ constexpr int commute_slice(int M) { return M * (M + 1) / 2 + M; }
+// a thread's slice in doubles, odd so that the threads' 8-byte accesses fall in distinct banks
+__host__ __device__ constexpr int commute_slice(int M) { return (M * (M + 1) / 2 + M) | 1; }
 // threads per CTA: two CTAs' slices (about 70-140 KB each) per SM where they fit
 __host__ __device__ constexpr int commute_threads(int M) {
     return M <= 8 ? 256 : (M <= 16 ? 64 : (M <= 32 ? 24 : (M <= 64 ? 8 : 2)));
@@ -477,7 +478,8 @@ __global__ void __launch_bounds__(commute_threads(M)) commute_rows_kernel(
             L[at(u, u)] = 1.0;
             y[u] = 0.0;
         }
-    // Cholesky L = F F^T in place, then F F^T y = r
+    // Cholesky L = F F^T in place, the diagonal holding 1 / F_jj (one division per pivot: FP64
+    // division is a long instruction sequence on this GPU), then F F^T y = r
     for (int j = 0; j < m; ++j) {
         double d = L[at(j, j)];
         for (int t = 0; t < j; ++t) d -= L[at(j, t)] * L[at(j, t)];
@@ -485,23 +487,23 @@ __global__ void __launch_bounds__(commute_threads(M)) commute_rows_kernel(
             atomicExch(err_flag, 1);
             return;
         }
-        const double f = sqrt(d);
-        L[at(j, j)] = f;
+        const double rf = 1.0 / sqrt(d);
+        L[at(j, j)] = rf;
         for (int a = j + 1; a < m; ++a) {
             double v = L[at(a, j)];
             for (int t = 0; t < j; ++t) v -= L[at(a, t)] * L[at(j, t)];
-            L[at(a, j)] = v / f;
+            L[at(a, j)] = v * rf;
         }
     }
     for (int a = 0; a < m; ++a) {
         double v = y[a];
         for (int t = 0; t < a; ++t) v -= L[at(a, t)] * y[t];
-        y[a] = v / L[at(a, a)];
+        y[a] = v * L[at(a, a)];
     }
     for (int a = m - 1; a >= 0; --a) {
         double v = y[a];
         for (int t = a + 1; t < m; ++t) v -= L[at(t, a)] * y[t];
-        y[a] = v / L[at(a, a)];
+        y[a] = v * L[at(a, a)];
     }
     for (int q = q0; q < q1; ++q) {
         const int a = ea[q], b = eb[q];
